@@ -1,0 +1,157 @@
+/*
+ * bisp.h - C ABI of the GB300 (sm_103a) estimator of the redshift-space bispectrum
+ * multipoles B_{l1 l2 L}(k1, k2) in the tri-polar spherical-harmonic (TripoSH)
+ * decomposition of Sugiyama, Saito, Beutler & Seo (arXiv:1803.02132).
+ *
+ * The library computes, on one GPU and with hand-written CUDA kernels only:
+ *   - the mass assignment of weighted galaxies and randoms onto a mesh (Sec. 4.1,
+ *     Eq. mean_n, Eq. dn, Eq. nlm; NGP/CIC/TSC, App. C) with optional interlacing;
+ *   - the forward 3D FFT and the W_mass deconvolution (Sec. 4.2);
+ *   - the y_l^{m*}(k)-filtered inverse FFTs per k shell and the y_L^{M*}(x)-weighted
+ *     density field G_L^M (Eq. nlm_bi);
+ *   - the mesh sum of F F G contracted with Wigner 3j symbols (Eq. bi_estimator_FFTs;
+ *     global line of sight: Eq. simulation_estimator);
+ *   - the four shot-noise terms (Eq. shotnoise, Eq. ShotNoise), the normalisation I
+ *     (Eq. normalization; periodic box I = Np^3/V^2, Sec. 4.4);
+ *   - the window bispectrum: the same estimator on the random catalogue alone (the
+ *     bispectrum-space counterpart of Eq. Q).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a bisp_status.  Nothing throws across the ABI.  On failure
+ *     bisp_last_error() returns a message for the calling thread (valid until the next
+ *     failing call on that thread).
+ *   - Positions are in box coordinates [0, box_len)^3, float32, interleaved x,y,z.
+ *   - A plan owns all its device memory (meshes, spectra, fields) and a CUDA stream;
+ *     the caller owns every pointer it passes, and the library only borrows it for the
+ *     duration of the call.  Calls on one plan must not overlap (one thread at a time).
+ *   - Device pointers passed in are read on the plan's stream; the call returns after
+ *     the work has completed (host outputs are written).
+ *   - Output arrays are caller-owned host FP64 arrays.
+ */
+#ifndef BISP_H
+#define BISP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bisp_plan bisp_plan; /* opaque; owns device memory and a stream */
+
+typedef enum {
+  BISP_OK = 0,
+  BISP_EINVAL = 1,      /* invalid argument (message names it) */
+  BISP_ENOMEM = 2,      /* device memory admission failed (message gives bytes needed) */
+  BISP_ECUDA = 3,       /* a CUDA runtime call failed */
+  BISP_ESTATE = 4,      /* call out of order (e.g. measure before the data catalogue) */
+  BISP_ETIMEOUT = 5,    /* a bounded device wait expired */
+  BISP_EUNSUPPORTED = 6 /* valid request outside what this build implements */
+} bisp_status;
+
+/* Line of sight: global (the z axis of the box, Sec. 4.4) or local (the direction from
+ * the observer to each object, Sec. 2 and Sec. 4.1). */
+typedef enum { BISP_LOS_GLOBAL_Z = 0, BISP_LOS_LOCAL = 1 } bisp_los;
+
+/* Mass assignment scheme; the value is the exponent p of W_mass (Sec. 4.2). */
+typedef enum { BISP_NGP = 1, BISP_CIC = 2, BISP_TSC = 3 } bisp_mas;
+
+typedef enum { BISP_DATA = 0, BISP_RANDOMS = 1 } bisp_catalog;
+
+typedef struct {
+  int nmesh;               /* N, a power of two, 16..1024 */
+  double box_len;          /* L [Mpc/h]; the mesh covers [0, L)^3 */
+  const double* k_edges;   /* nbins+1 ascending edges [h/Mpc]; bin b = [e_b, e_{b+1}).
+                              Modes on a Nyquist plane are in no bin. Copied. */
+  int nbins;
+  const int* ells;         /* 3*n_mult ints (l1, l2, L), each satisfying the selection
+                              rules of Table 1 (l1 >= l2, L even, triangle rule,
+                              l1+l2+L even), l1, l2, L <= 4. Copied. */
+  int n_mult;
+  int los;                 /* bisp_los */
+  double observer[3];      /* BISP_LOS_LOCAL only: origin of the lines of sight */
+  int mas;                 /* bisp_mas */
+  int interlace;           /* 0/1: second mesh shifted by half a cell (reading of Sec. 4.2) */
+  double fkp_P0;           /* > 0: FKP weight w/(1 + nbar P0) when nbar is given (Sec. 5.2) */
+  size_t max_device_bytes; /* 0: free device memory minus a reserve; else the admission cap */
+  int want_window;         /* 1: also the randoms-only window bispectrum (needs randoms) */
+} bisp_params;
+
+/* Create a plan.  Validates params (BISP_EINVAL names the offending field), computes the
+ * bin thresholds, the 3j tables and the per-multipole contraction recipes in FP64, and
+ * reserves device memory for the meshes and fields (BISP_ENOMEM with the bytes needed).
+ * stream: a cudaStream_t to run on, or NULL for a stream the plan creates and owns. */
+bisp_status bisp_plan_create(bisp_plan** out, const bisp_params* p, void* stream);
+
+/* Assign a catalogue (Sec. 4.1): weights w_i (NULL: 1) times the FKP weight when nbar
+ * (expected number density at each object, NULL: none) is given and fkp_P0 > 0; the
+ * local-LOS channels y_L^{M*}(x_hat) w and y_L^M(x_hat) w^2; deterministic sort-by-cell
+ * scatter onto the mesh (no float atomics); forward FFT; interlacing; deconvolution.
+ * xyz: 3*n floats; w, nbar: n floats or NULL; ptr_is_device: 1 if the three pointers
+ * are device pointers, 0 if host pointers (copied in by the call).
+ * Errors: BISP_EINVAL for n < 0, NULL xyz with n > 0, non-finite or out-of-box
+ * positions (the message gives the count), non-positive total weight. Re-assigning a
+ * catalogue replaces it. */
+bisp_status bisp_assign(bisp_plan* plan, int which, const float* xyz, const float* w,
+                        const float* nbar, int64_t n, int ptr_is_device);
+
+/* Measure every multipole of the plan.  All outputs are host FP64 arrays of n_mult *
+ * nbins * nbins values laid out [mult][b1][b2] (or NULL to skip):
+ *   B            shot-noise-subtracted bispectrum multipoles B_{l1 l2 L}(k_b1, k_b2)
+ *   shot         the subtracted shot noise (sum of the four terms of Eq. shotnoise)
+ *   window       window bispectrum (randoms only), shot noise subtracted; needs
+ *                want_window
+ *   window_shot  the window's shot noise
+ *   nmodes       nbins values: the number of Fourier modes in each shell
+ * Needs the data catalogue (BISP_ESTATE otherwise) and, for the local line of sight or
+ * the window, the random catalogue. */
+bisp_status bisp_measure(bisp_plan* plan, double* B, double* shot, double* window,
+                         double* window_shot, double* nmodes);
+
+/* Free every resource of the plan (NULL is accepted). */
+bisp_status bisp_plan_destroy(bisp_plan* plan);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* bisp_last_error(void);
+
+/* Sizes and bookkeeping of a plan, for callers and tests. */
+typedef struct {
+  int nmesh, nbins, n_mult, n_dchan, n_nchan, n_fcomp;
+  double alpha;            /* sum w_gal / sum w_ran, 0 before both are assigned */
+  double norm_I;           /* normalisation I of Eq. normalization */
+  int64_t n_data, n_randoms;
+  size_t device_bytes;     /* device memory held by the plan */
+  int kernel_launches;     /* kernels launched by the last bisp_assign + bisp_measure */
+  double ms_assign_data, ms_assign_randoms, ms_measure; /* device time of the last calls */
+  double ms_pair;          /* device time of the pair-reduction kernels in the last measure */
+  double pair_bytes;       /* algorithmic bytes read by those pair reductions */
+  int pair_launches;
+} bisp_plan_info;
+
+bisp_status bisp_plan_query(const bisp_plan* plan, bisp_plan_info* info);
+
+/* Stable ordering of particles by their home mesh node (Sec. 4.2 mass assignment; the
+ * node is floor(x/H) for CIC and floor(x/H + 1/2) for NGP/TSC, with H = box_len/nmesh,
+ * computed in FP64).  keys_out[i] = (hx*N + hy)*N + hz of particle order_out[i]; ties
+ * keep input order.  xyz (3*n floats), keys_out and order_out (n uint32 each) are device
+ * pointers; stream is a cudaStream_t or NULL.  Scratch is allocated by the call.
+ * Errors: BISP_EINVAL for bad sizes, non-finite or out-of-box positions. */
+bisp_status bisp_cell_order(int nmesh, double box_len, int mas, const float* xyz, int64_t n,
+                            uint32_t* keys_out, uint32_t* order_out, void* stream);
+
+/* Copy an internal array of the plan to host memory (tests):
+ *   what = BISP_DBG_SPECTRUM: the deconvolved half spectrum of channel `index` of
+ *          catalogue `which`, complex64 [N][N][N/2] (nz < N/2), 8*N*N*N/2 bytes;
+ *   what = BISP_DBG_MESH: the real mesh of channel `index` (non-shifted) of catalogue
+ *          `which` as assigned, float32 [N][N][N]; kept only if the plan was created
+ *          with BISP_DEBUG_KEEP_MESH in the environment variable BISP_DEBUG.
+ * bytes must equal the array size. */
+enum { BISP_DBG_SPECTRUM = 0, BISP_DBG_MESH = 1 };
+bisp_status bisp_debug_fetch(const bisp_plan* plan, int what, int which, int index,
+                             void* host_out, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BISP_H */

@@ -1,0 +1,215 @@
+"""Python binding of libbisp (include/bisp.h): argument marshalling only.
+
+Every step of the estimator runs in the library's CUDA kernels.  Device inputs are
+torch CUDA tensors (PyTorch supplies device memory and streams); host inputs are numpy
+arrays.  If the compiled library is missing, importing this package builds it with nvcc;
+if that fails, the import raises - there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libbisp.so")
+_HEADER = os.path.join(os.path.dirname(_HERE), "include", "bisp.h")
+
+BISP_OK, BISP_EINVAL, BISP_ENOMEM, BISP_ECUDA, BISP_ESTATE, BISP_ETIMEOUT, BISP_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["BISP_OK", "BISP_EINVAL", "BISP_ENOMEM", "BISP_ECUDA", "BISP_ESTATE", "BISP_ETIMEOUT",
+                "BISP_EUNSUPPORTED"]
+LOS = {"global": 0, "local": 1}
+MAS = {"NGP": 1, "CIC": 2, "TSC": 3, 1: 1, 2: 2, 3: 3}
+DATA, RANDOMS = 0, 1
+
+
+class BispError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+        self.status = status
+
+
+class _Params(C.Structure):
+    _fields_ = [("nmesh", C.c_int), ("box_len", C.c_double), ("k_edges", C.POINTER(C.c_double)),
+                ("nbins", C.c_int), ("ells", C.POINTER(C.c_int)), ("n_mult", C.c_int), ("los", C.c_int),
+                ("observer", C.c_double * 3), ("mas", C.c_int), ("interlace", C.c_int), ("fkp_P0", C.c_double),
+                ("max_device_bytes", C.c_size_t), ("want_window", C.c_int)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("nmesh", C.c_int), ("nbins", C.c_int), ("n_mult", C.c_int), ("n_dchan", C.c_int),
+                ("n_nchan", C.c_int), ("n_fcomp", C.c_int), ("alpha", C.c_double), ("norm_I", C.c_double),
+                ("n_data", C.c_int64), ("n_randoms", C.c_int64), ("device_bytes", C.c_size_t),
+                ("kernel_launches", C.c_int), ("ms_assign_data", C.c_double), ("ms_assign_randoms", C.c_double),
+                ("ms_measure", C.c_double), ("ms_pair", C.c_double), ("pair_bytes", C.c_double),
+                ("pair_launches", C.c_int)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        from . import build as _b
+        _b.build()
+    lib = C.CDLL(_LIB_PATH)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    lib.bisp_plan_create.argtypes = [C.POINTER(vp), C.POINTER(_Params), vp]
+    lib.bisp_assign.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int64, C.c_int]
+    lib.bisp_measure.argtypes = [vp, dp, dp, dp, dp, dp]
+    lib.bisp_plan_destroy.argtypes = [vp]
+    lib.bisp_last_error.restype = C.c_char_p
+    lib.bisp_plan_query.argtypes = [vp, C.POINTER(_Info)]
+    lib.bisp_cell_order.argtypes = [C.c_int, C.c_double, C.c_int, vp, C.c_int64, vp, vp, vp]
+    lib.bisp_debug_fetch.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, C.c_size_t]
+    for f in ("bisp_plan_create", "bisp_assign", "bisp_measure", "bisp_plan_destroy", "bisp_plan_query",
+              "bisp_cell_order", "bisp_debug_fetch"):
+        getattr(lib, f).restype = C.c_int
+    return lib
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libbisp (built on first use)."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def header_functions():
+    """Names of the functions declared in include/bisp.h."""
+    txt = open(_HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:bisp_status|const char\*)\s+(bisp_\w+)\s*\(", txt, re.M)))
+
+
+def _check(st):
+    if st != BISP_OK:
+        raise BispError(st, lib().bisp_last_error().decode())
+
+
+def _ptr(a):
+    """(pointer, is_device) of a torch CUDA tensor or a numpy array (kept alive by caller)."""
+    if a is None:
+        return None, None
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        assert a.is_contiguous()
+        return C.c_void_p(a.data_ptr()), 1
+    arr = np.ascontiguousarray(a)
+    return C.c_void_p(arr.ctypes.data), 0
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Plan:
+    """A measurement plan: mesh, bins, multipoles, line of sight, assignment scheme."""
+
+    def __init__(self, nmesh, box_len, k_edges, ells, los="global", observer=(0.0, 0.0, 0.0), mas="TSC",
+                 interlace=False, fkp_P0=0.0, want_window=False, max_device_bytes=0, stream=None):
+        self._edges = np.ascontiguousarray(k_edges, dtype=np.float64)
+        self._ells = np.ascontiguousarray(np.asarray(ells, dtype=np.int32).reshape(-1))
+        p = _Params()
+        p.nmesh = int(nmesh)
+        p.box_len = float(box_len)
+        p.k_edges = self._edges.ctypes.data_as(C.POINTER(C.c_double))
+        p.nbins = len(self._edges) - 1
+        p.ells = self._ells.ctypes.data_as(C.POINTER(C.c_int))
+        p.n_mult = len(self._ells) // 3
+        p.los = LOS[los] if isinstance(los, str) else int(los)
+        p.observer = (C.c_double * 3)(*[float(v) for v in observer])
+        p.mas = MAS[mas]
+        p.interlace = 1 if interlace else 0
+        p.fkp_P0 = float(fkp_P0)
+        p.max_device_bytes = int(max_device_bytes)
+        p.want_window = 1 if want_window else 0
+        self.nbins = p.nbins
+        self.want_window = bool(want_window)
+        self.n_mult = p.n_mult
+        self.nmesh = p.nmesh
+        self._h = C.c_void_p()
+        _check(lib().bisp_plan_create(C.byref(self._h), C.byref(p), _stream_handle(stream)))
+
+    def assign(self, which, xyz, w=None, nbar=None):
+        """Assign a catalogue: xyz (n, 3) float32, optional w and nbar (n,) float32, either
+        all torch CUDA tensors or all host arrays."""
+        keep = []
+        for a in (xyz, w, nbar):
+            if a is not None and not (hasattr(a, "is_cuda") and a.is_cuda):
+                a = np.ascontiguousarray(a, dtype=np.float32)
+            keep.append(a)
+        px, dev = _ptr(keep[0])
+        pw, _ = _ptr(keep[1])
+        pn, _ = _ptr(keep[2])
+        n = int(keep[0].shape[0]) if keep[0] is not None else 0
+        _check(lib().bisp_assign(self._h, int(which), px, pw, pn, n, int(dev or 0)))
+
+    def measure(self):
+        """Dict of FP64 arrays [n_mult, nbins, nbins]: B, shot, window, window_shot; nmodes [nbins]."""
+        shape = (self.n_mult, self.nbins, self.nbins)
+        out = {k: np.zeros(shape) for k in ("B", "shot", "window", "window_shot")}
+        out["nmodes"] = np.zeros(self.nbins)
+        dp = C.POINTER(C.c_double)
+        info = self.info()
+        args = [out[k].ctypes.data_as(dp) for k in ("B", "shot")]
+        if info["n_randoms"] > 0 and self.want_window:
+            args += [out[k].ctypes.data_as(dp) for k in ("window", "window_shot")]
+        else:
+            args += [None, None]
+            del out["window"], out["window_shot"]
+        args.append(out["nmodes"].ctypes.data_as(dp))
+        _check(lib().bisp_measure(self._h, *args))
+        return out
+
+    def info(self):
+        i = _Info()
+        _check(lib().bisp_plan_query(self._h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+    def fetch_spectrum(self, which, chan):
+        """Deconvolved half spectrum of a channel: complex64 [N, N, N/2]."""
+        N = self.nmesh
+        a = np.empty((N, N, N // 2), dtype=np.complex64)
+        _check(lib().bisp_debug_fetch(self._h, 0, int(which), int(chan), C.c_void_p(a.ctypes.data), a.nbytes))
+        return a
+
+    def fetch_mesh(self, which, chan):
+        """Assigned real mesh of a channel (needs BISP_DEBUG=BISP_DEBUG_KEEP_MESH at plan creation)."""
+        N = self.nmesh
+        a = np.empty((N, N, N), dtype=np.float32)
+        _check(lib().bisp_debug_fetch(self._h, 1, int(which), int(chan), C.c_void_p(a.ctypes.data), a.nbytes))
+        return a
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().bisp_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def cell_order(nmesh, box_len, mas, xyz, stream=None):
+    """(keys, order) of a torch CUDA float32 (n, 3) tensor: stable order by home mesh node."""
+    import torch
+    assert xyz.is_cuda and xyz.dtype == torch.float32 and xyz.is_contiguous()
+    n = xyz.shape[0]
+    keys = torch.empty(n, dtype=torch.int32, device=xyz.device)
+    order = torch.empty(n, dtype=torch.int32, device=xyz.device)
+    s = _stream_handle(stream if stream is not None else torch.cuda.current_stream())
+    _check(lib().bisp_cell_order(int(nmesh), float(box_len), MAS[mas], C.c_void_p(xyz.data_ptr()), n,
+                                 C.c_void_p(keys.data_ptr()), C.c_void_p(order.data_ptr()), s))
+    return keys, order

@@ -1,0 +1,466 @@
+// Mass assignment (Sec. 4.1 Eq. mean_n, Eq. dn, Eq. nlm; Sec. 4.2; App. C):
+// per-particle weights and line-of-sight channels, a stable LSD radix sort of the
+// particles by home mesh node, cell starts, and a gather deposit in which every mesh
+// node sums the particles around it in a fixed order (no float atomics, so the meshes
+// are bit-reproducible run to run).
+#include "common.cuh"
+#include "internal.h"
+
+namespace bisp {
+
+// =====================================================================================
+// prep: FP64 cell keys, FP32 offsets, weights, channel values, FP64 partial sums
+// =====================================================================================
+constexpr int PREP_THREADS = 256;
+constexpr int PREP_MAXBLK = 4096;
+
+int prep_blocks(int64_t n) {
+  int64_t b = (n + PREP_THREADS - 1) / PREP_THREADS;
+  if (b < 1) b = 1;
+  if (b > PREP_MAXBLK) b = PREP_MAXBLK;
+  return (int)b;
+}
+
+__constant__ PrepArgs c_prep;
+
+__global__ void __launch_bounds__(PREP_THREADS) k_prep() {
+  const PrepArgs& a = c_prep;
+  constexpr int NSMAX = 34;
+  double acc[NSMAX];
+#pragma unroll
+  for (int q = 0; q < NSMAX; ++q) acc[q] = 0.0;
+  const int N = a.N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = a.xyz[3 * i], y = a.xyz[3 * i + 1], z = a.xyz[3 * i + 2];
+    const bool ok = isfinite(x) && isfinite(y) && isfinite(z) && x >= 0.f && y >= 0.f && z >= 0.f &&
+                    (double)x < a.box && (double)y < a.box && (double)z < a.box;
+    if (!ok) {
+      atomicAdd(a.bad, 1);
+      a.keys[i] = 0;
+      a.idx[i] = (uint32_t)i;
+      a.frac[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int c = 0; c < a.nchan; ++c) a.vals[(size_t)c * a.n + i] = 0.f;
+      continue;
+    }
+    // u = x / H in FP64; home node floor(u) (CIC) or floor(u + 1/2) (NGP, TSC)
+    const double ux = (double)x / a.H, uy = (double)y / a.H, uz = (double)z / a.H;
+    double hx, hy, hz;
+    if (a.mas == 2) {
+      hx = floor(ux); hy = floor(uy); hz = floor(uz);
+    } else {
+      hx = floor(ux + 0.5); hy = floor(uy + 0.5); hz = floor(uz + 0.5);
+    }
+    const int ix = ((int)hx) & (N - 1), iy = ((int)hy) & (N - 1), iz = ((int)hz) & (N - 1);
+    a.keys[i] = ((uint32_t)ix * (uint32_t)N + (uint32_t)iy) * (uint32_t)N + (uint32_t)iz;
+    a.idx[i] = (uint32_t)i;
+    a.frac[i] = make_float4((float)(ux - hx), (float)(uy - hy), (float)(uz - hz), 0.f);
+    // weight: w / (1 + nbar P0)
+    double wd = a.w ? (double)a.w[i] : 1.0;
+    if (a.nbar && a.P0 > 0.f) wd = wd / (1.0 + (double)a.nbar[i] * (double)a.P0);
+    const float wf = (float)wd;
+    // line-of-sight harmonics
+    float2 yl[(BISP_LMAX + 1) * (BISP_LMAX + 2) / 2];
+    if (a.local) {
+      ylm_all<BISP_LMAX>(x - a.obs[0], y - a.obs[1], z - a.obs[2], a.ynorm, yl);
+    } else {
+      ylm_all<BISP_LMAX>(0.f, 0.f, 1.f, a.ynorm, yl);
+    }
+    acc[0] += wd;
+    const double w3 = wd * wd * wd;
+    int q = 1;
+    for (int c = 0; c < a.nchan; ++c) {
+      const Chan ch = a.chan[c];
+      const int am = ch.M < 0 ? -ch.M : ch.M;
+      float2 yv = yl[ch.L * (ch.L + 1) / 2 + am];
+      if (ch.M < 0) {  // y_l^{-m} = (-1)^m conj(y_l^m)
+        yv = cconj(yv);
+        if (am & 1) yv = make_float2(-yv.x, -yv.y);
+      }
+      if (ch.conj) yv = cconj(yv);
+      const float pv = ch.part ? yv.y : yv.x;
+      const float wp = ch.power == 2 ? wf * wf : wf;
+      a.vals[(size_t)c * a.n + i] = wp * pv;
+      if (ch.power == 1 && q < a.nsum && q < NSMAX) {
+        acc[q] += w3 * (double)pv;
+        ++q;
+      }
+    }
+  }
+  // deterministic block reduction of the FP64 sums
+  __shared__ double red[PREP_THREADS / 32];
+  for (int q = 0; q < a.nsum && q < NSMAX; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int wv = 0; wv < PREP_THREADS / 32; ++wv) s += red[wv];
+      a.partials[(size_t)blockIdx.x * a.nsum + q] = s;
+    }
+    __syncthreads();
+  }
+}
+
+void launch_prep(const PrepArgs& a, cudaStream_t s) {
+  BISP_CUDA(cudaMemcpyToSymbolAsync(c_prep, &a, sizeof(PrepArgs), 0, cudaMemcpyHostToDevice, s));
+  k_prep<<<prep_blocks(a.n), PREP_THREADS, 0, s>>>();
+  BISP_CHECK_LAUNCH();
+}
+
+// =====================================================================================
+// exclusive scan of uint32 (three phases, recursive on the block sums)
+// =====================================================================================
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t ws[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t t = lane < SCAN_THREADS / 32 ? ws[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < SCAN_THREADS / 32) ws[lane] = t;
+  }
+  __syncthreads();
+  const uint32_t wpre = wid ? ws[wid - 1] : 0u;
+  if (total) *total = ws[SCAN_THREADS / 32 - 1];
+  __syncthreads();
+  return wpre + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const uint32_t* in, uint32_t* out, int64_t n,
+                                                              uint32_t* sums) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  uint32_t tsum = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    tsum += v[k];
+  }
+  uint32_t total;
+  uint32_t pre = block_exclusive_scan(tsum, &total);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(uint32_t* out, int64_t n, const uint32_t* offs) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  const uint32_t o = offs[blockIdx.x];
+  for (int k = threadIdx.x; k < SCAN_TILE; k += blockDim.x)
+    if (base + k < n) out[base + k] += o;
+}
+
+static int64_t ntiles(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
+
+size_t scan_scratch_bytes(int64_t n) {
+  size_t b = 0;
+  int64_t m = n;
+  while (m > 1) {
+    m = ntiles(m);
+    b += 2 * (size_t)(m + 1) * sizeof(uint32_t);
+  }
+  return b + 64;
+}
+
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* scratch, cudaStream_t s,
+                        int* launches) {
+  if (n <= 0) return;
+  const int64_t nt = ntiles(n);
+  uint32_t* sums = (uint32_t*)scratch;
+  uint32_t* offs = sums + nt + 1;
+  k_scan_tiles<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, out, n, sums);
+  BISP_CHECK_LAUNCH();
+  if (launches) ++*launches;
+  if (nt > 1) {
+    exclusive_scan_u32(sums, offs, nt, offs + nt + 1, s, launches);
+    k_scan_add<<<(unsigned)nt, 256, 0, s>>>(out, n, offs);
+    BISP_CHECK_LAUNCH();
+    if (launches) ++*launches;
+  }
+}
+
+// =====================================================================================
+// stable LSD radix sort, 8-bit digits
+// =====================================================================================
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;
+constexpr int RS_BINS = 256;
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* keys, int64_t n, int shift,
+                                                        uint32_t* hist, int64_t nt) {
+  __shared__ uint32_t h[RS_BINS];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const int64_t i = base + r * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & (RS_BINS - 1)], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin, const uint32_t* vin, int64_t n,
+                                                           int shift, const uint32_t* offs, int64_t nt,
+                                                           uint32_t* kout, uint32_t* vout) {
+  constexpr int NW = RS_THREADS / 32;
+  __shared__ uint32_t wc[NW][RS_BINS];
+  __shared__ uint32_t base[RS_BINS];
+  __shared__ uint32_t tot[RS_BINS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  base[threadIdx.x] = offs[(int64_t)threadIdx.x * nt + blockIdx.x];
+  const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) wc[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = t0 + r * RS_THREADS + threadIdx.x;
+    const bool valid = i < n;
+    uint32_t k = 0, v = 0, d = RS_BINS;  // invalid items take a digit no one uses
+    if (valid) {
+      k = kin[i];
+      v = vin[i];
+      d = (k >> shift) & (RS_BINS - 1);
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt);
+    if (valid && rank == 0) wc[wid][d] = __popc(peers);
+    __syncthreads();
+    {  // per-digit prefix over warps (thread = digit)
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t c = wc[w][threadIdx.x];
+        wc[w][threadIdx.x] = run;
+        run += c;
+      }
+      tot[threadIdx.x] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = base[d] + wc[wid][d] + rank;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+    base[threadIdx.x] += tot[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+size_t radix_sort_scratch_bytes(int64_t n) {
+  const int64_t nt = (n + RS_TILE - 1) / RS_TILE;
+  const int64_t nh = nt * RS_BINS;
+  return 2 * (size_t)n * sizeof(uint32_t) + 2 * (size_t)nh * sizeof(uint32_t) + scan_scratch_bytes(nh) + 256;
+}
+
+void radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_out, uint32_t* vals_out, int64_t n, int bits,
+                void* scratch, cudaStream_t s, int* launches) {
+  if (n <= 0) return;
+  const int64_t nt = (n + RS_TILE - 1) / RS_TILE;
+  const int64_t nh = nt * RS_BINS;
+  uint32_t* tk = (uint32_t*)scratch;
+  uint32_t* tv = tk + n;
+  uint32_t* hist = tv + n;
+  uint32_t* offs = hist + nh;
+  void* sscr = offs + nh;
+  int npass = (bits + 7) / 8;
+  if (npass < 1) npass = 1;
+  // ping-pong so that the last pass writes keys_out/vals_out
+  const uint32_t* kin = keys;
+  const uint32_t* vin = vals;
+  for (int p = 0; p < npass; ++p) {
+    const bool last = p == npass - 1;
+    // even distance from the end -> out, odd -> temp
+    const bool to_out = ((npass - 1 - p) % 2) == 0;
+    uint32_t* ko = to_out ? keys_out : tk;
+    uint32_t* vo = to_out ? vals_out : tv;
+    (void)last;
+    k_rs_hist<<<(unsigned)nt, RS_THREADS, 0, s>>>(kin, n, 8 * p, hist, nt);
+    BISP_CHECK_LAUNCH();
+    exclusive_scan_u32(hist, offs, nh, sscr, s, launches);
+    k_rs_scatter<<<(unsigned)nt, RS_THREADS, 0, s>>>(kin, vin, n, 8 * p, offs, nt, ko, vo);
+    BISP_CHECK_LAUNCH();
+    if (launches) *launches += 2;
+    kin = ko;
+    vin = vo;
+  }
+}
+
+// =====================================================================================
+// cell counts, particle gather, deposit
+// =====================================================================================
+__global__ void k_count_cells(const uint32_t* keys, int64_t n, uint32_t* counts) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&counts[keys[i]], 1u);
+}
+
+void launch_count_cells(const uint32_t* keys, int64_t n, uint32_t* counts, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t b = (n + 255) / 256;
+  if (b > 65536) b = 65536;
+  k_count_cells<<<(unsigned)b, 256, 0, s>>>(keys, n, counts);
+  BISP_CHECK_LAUNCH();
+}
+
+__global__ void k_gather_particles(const uint32_t* perm, int64_t n, const float4* frac_in, const float* vals_in,
+                                   int nchan, float4* frac_out, float* vals_out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = perm[i];
+    frac_out[i] = frac_in[p];
+    for (int c = 0; c < nchan; ++c) vals_out[(size_t)c * n + i] = vals_in[(size_t)c * n + p];
+  }
+}
+
+void launch_gather_particles(const uint32_t* perm, int64_t n, const float4* frac_in, const float* vals_in,
+                             int nchan, float4* frac_out, float* vals_out, cudaStream_t s) {
+  if (n <= 0) return;
+  int64_t b = (n + 255) / 256;
+  if (b > 65536) b = 65536;
+  k_gather_particles<<<(unsigned)b, 256, 0, s>>>(perm, n, frac_in, vals_in, nchan, frac_out, vals_out);
+  BISP_CHECK_LAUNCH();
+}
+
+// 1D assignment kernel as a function of the distance t between particle and node
+template <int P>
+__device__ __forceinline__ float wker(float t) {
+  if (P == 1) return (t >= -0.5f && t < 0.5f) ? 1.f : 0.f;
+  const float a = fabsf(t);
+  if (P == 2) return a < 1.f ? 1.f - a : 0.f;
+  if (a < 0.5f) return 0.75f - t * t;
+  if (a < 1.5f) {
+    const float b = 1.5f - a;
+    return 0.5f * b * b;
+  }
+  return 0.f;
+}
+
+constexpr int DEP_CG = 4;  // channels per deposit pass
+
+// One thread per mesh node c.  It visits the home nodes h = c + o, o in [OLO, OHI]^3 (z
+// innermost), and every particle of each home node in sorted order, so the sum order is
+// fixed.  Node positions: mesh 0 at c H, mesh 1 (interlaced) at (c + 1/2) H.
+template <int P, int ILV>
+__global__ void __launch_bounds__(256) k_deposit(const uint32_t* __restrict__ cell_start,
+                                                 const float4* __restrict__ frac, const float* __restrict__ vals,
+                                                 int64_t n, int N, int nchan, float* mesh0, float* mesh1) {
+  // home-node offsets o = h - c that can reach node c
+  constexpr int OLO = (P == 2) ? -1 : (P == 1 ? 0 : -1);
+  constexpr int OHI = ILV ? (P == 2 ? 1 : (P == 1 ? 1 : 2)) : (P == 2 ? 0 : (P == 1 ? 0 : 1));
+  const int64_t Ng = (int64_t)N * N * N;
+  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= Ng) return;
+  const int c0 = blockIdx.y * DEP_CG;
+  const int nc = min(DEP_CG, nchan - c0);
+  const int cz = (int)(cell % N), cy = (int)((cell / N) % N), cx = (int)(cell / ((int64_t)N * N));
+  float a0[DEP_CG], a1[DEP_CG];
+#pragma unroll
+  for (int k = 0; k < DEP_CG; ++k) a0[k] = a1[k] = 0.f;
+  for (int ox = OLO; ox <= OHI; ++ox) {
+    const int hx = (cx + ox) & (N - 1);
+    for (int oy = OLO; oy <= OHI; ++oy) {
+      const int hy = (cy + oy) & (N - 1);
+      const uint32_t rowkey = ((uint32_t)hx * N + (uint32_t)hy) * (uint32_t)N;
+      for (int oz = OLO; oz <= OHI; ++oz) {
+        const int hz = (cz + oz) & (N - 1);
+        const uint32_t key = rowkey + (uint32_t)hz;
+        const uint32_t p0 = cell_start[key], p1 = cell_start[key + 1];
+        for (uint32_t p = p0; p < p1; ++p) {
+          const float4 d = frac[p];
+          // distance particle - node along each axis: (h - c) + d
+          const float tx = (float)ox + d.x, ty = (float)oy + d.y, tz = (float)oz + d.z;
+          const float w0 = wker<P>(tx) * wker<P>(ty) * wker<P>(tz);
+          float w1 = 0.f;
+          if (ILV) w1 = wker<P>(tx - 0.5f) * wker<P>(ty - 0.5f) * wker<P>(tz - 0.5f);
+#pragma unroll
+          for (int k = 0; k < DEP_CG; ++k) {
+            if (k < nc) {
+              const float v = vals[(size_t)(c0 + k) * n + p];
+              a0[k] = fmaf(w0, v, a0[k]);
+              if (ILV) a1[k] = fmaf(w1, v, a1[k]);
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < DEP_CG; ++k) {
+    if (k < nc) {
+      mesh0[(size_t)(c0 + k) * Ng + cell] = a0[k];
+      if (ILV) mesh1[(size_t)(c0 + k) * Ng + cell] = a1[k];
+    }
+  }
+}
+
+void launch_deposit(const DepositArgs& a, cudaStream_t s, int* launches) {
+  const int64_t Ng = (int64_t)a.N * a.N * a.N;
+  dim3 grid((unsigned)((Ng + 255) / 256), (unsigned)((a.nchan + DEP_CG - 1) / DEP_CG));
+#define BISP_DEP(P_, I_) \
+  k_deposit<P_, I_><<<grid, 256, 0, s>>>(a.cell_start, a.frac, a.vals, a.n, a.N, a.nchan, a.mesh0, a.mesh1)
+  if (a.interlace) {
+    if (a.mas == 1) BISP_DEP(1, 1);
+    else if (a.mas == 2) BISP_DEP(2, 1);
+    else BISP_DEP(3, 1);
+  } else {
+    if (a.mas == 1) BISP_DEP(1, 0);
+    else if (a.mas == 2) BISP_DEP(2, 0);
+    else BISP_DEP(3, 0);
+  }
+#undef BISP_DEP
+  BISP_CHECK_LAUNCH();
+  if (launches) ++*launches;
+}
+
+// =====================================================================================
+// sum of cubes of a mesh (normalisation I from the random catalogue), FP64 partials
+// =====================================================================================
+__global__ void __launch_bounds__(256) k_sum_cubes(const float* m, int64_t ncell, double* partials) {
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncell; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)m[i];
+    acc += v * v * v;
+  }
+  __shared__ double red[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+int launch_sum_cubes(const float* mesh, int64_t ncell, double* partials, cudaStream_t s) {
+  const int nb = 1024;
+  k_sum_cubes<<<nb, 256, 0, s>>>(mesh, ncell, partials);
+  BISP_CHECK_LAUNCH();
+  return nb;
+}
+
+}  // namespace bisp

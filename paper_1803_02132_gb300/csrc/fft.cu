@@ -1,0 +1,414 @@
+// Hand-written batched 3D FFTs of the estimator (Sec. 4.2, Eq. nlm_bi):
+//  * forward: real meshes -> deconvolved half spectra, three shared-memory passes
+//    (z: real-to-complex, y, x).  The x pass also combines the interlaced pair and
+//    divides by W_mass(k);
+//  * inverse: half spectra -> real fields, pruned to the box |n_i| <= P that holds the
+//    non-zero modes.  The first pass (x) builds the spectrum on the fly: a plain channel,
+//    the shot-noise product Q = A conj(B) - Sbar C/W^2, or a k shell times
+//    (-i)^l Re/Im y_l^{m*}(k) / N_mode (times the density or 1).
+// Layout: real mesh [x][y][z] (z fastest); half spectrum [nx][ny][nz], nz < N/2 (the
+// nz = N/2 plane is dropped: every spectrum is zero on the Nyquist planes).
+#include "common.cuh"
+#include "internal.h"
+
+namespace bisp {
+
+template <int N>
+struct Geo {
+  static constexpr int NH = N / 2;
+  static constexpr int LB = (N >= 1024 || N < 32) ? 8 : 16;   // lines per CTA, strided passes
+  static constexpr int LBZ = (N >= 1024 || N < 32) ? 8 : 16;  // rows per CTA, z passes
+  static constexpr int TS = LB * N / 8;                       // threads, strided passes
+  static constexpr int TZ = LBZ * NH / 8;                     // threads, z passes
+};
+
+__device__ __forceinline__ int sgn_idx(int j, int N) { return j < N / 2 ? j : j - N; }
+
+// ------------------------------------------------------------------------------------
+// forward z pass: rows of N reals -> N/2 complex (X[0] real, Nyquist dropped), in place
+// ------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::TZ) k_fwd_z(float* data, const float2* __restrict__ tw) {
+  constexpr int NH = N / 2, LBZ = Geo<N>::LBZ, LD = LBZ + 1;
+  __shared__ float2 s[NH * LD];
+  float2* rows = reinterpret_cast<float2*>(data) + (size_t)blockIdx.x * LBZ * NH;
+  for (int i = threadIdx.x; i < LBZ * NH; i += blockDim.x) {
+    const int l = i / NH, e = i % NH;
+    s[e * LD + l] = rows[(size_t)l * NH + e];
+  }
+  __syncthreads();
+  fft_smem<NH, LBZ, -1>(s, tw, LD);
+  // X[k] = (Z[k] + Z*[NH-k])/2 - i w^k (Z[k] - Z*[NH-k])/2,  w = e^{-2 pi i / N}
+  for (int i = threadIdx.x; i < LBZ * (NH / 2 + 1); i += blockDim.x) {
+    const int l = i % LBZ, k = i / LBZ;
+    if (k == 0) {
+      const float2 z0 = s[l];
+      s[l] = make_float2(z0.x + z0.y, 0.f);
+    } else {
+      const int kp = NH - k;
+      const float2 a = s[k * LD + l], b = s[kp * LD + l];
+      const float2 wk = tw[k * (BISP_TWN / N)];
+      const float2 wkp = tw[kp * (BISP_TWN / N)];
+      // X[k]
+      float2 sp = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));      // (a + b*)/2
+      float2 dm = make_float2(0.5f * (a.x - b.x), 0.5f * (a.y + b.y));      // (a - b*)/2
+      float2 t = cmul(wk, dm);
+      const float2 xk = make_float2(sp.x + t.y, sp.y - t.x);                // sp - i t
+      // X[kp]
+      float2 sp2 = make_float2(0.5f * (b.x + a.x), 0.5f * (b.y - a.y));
+      float2 dm2 = make_float2(0.5f * (b.x - a.x), 0.5f * (b.y + a.y));
+      float2 t2 = cmul(wkp, dm2);
+      const float2 xkp = make_float2(sp2.x + t2.y, sp2.y - t2.x);
+      s[k * LD + l] = xk;
+      if (kp != k) s[kp * LD + l] = xkp;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < LBZ * NH; i += blockDim.x) {
+    const int l = i / NH, e = i % NH;
+    rows[(size_t)l * NH + e] = s[e * LD + l];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// forward y pass: complex lines along y, in place.  data: [cnt][N][N][NH]
+// ------------------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::TS) k_fwd_y(float2* data, const float2* __restrict__ tw) {
+  constexpr int NH = N / 2, LB = Geo<N>::LB;
+  extern __shared__ float2 s[];
+  const int nz0 = blockIdx.x * LB, x = blockIdx.y, mesh = blockIdx.z;
+  float2* base = data + (((size_t)mesh * N + x) * N) * NH + nz0;
+  for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+    const int l = i % LB, e = i / LB;
+    s[i] = base[(size_t)e * NH + l];
+  }
+  __syncthreads();
+  fft_smem<N, LB, -1>(s, tw);
+  for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+    const int l = i % LB, e = i / LB;
+    base[(size_t)e * NH + l] = s[i];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// forward x pass + interlacing + deconvolution, written over mesh0.
+//   D = [ (D0 + e^{-i pi (nx+ny+nz)/N} D1) / 2 ] / W(k)   (ILV)   or   D0 / W(k)
+// winv[j] = 1 / sinc(pi n_j / N)^p for the signed frequency of index j.
+// ------------------------------------------------------------------------------------
+template <int N, int ILV>
+__global__ void __launch_bounds__(Geo<N>::TS) k_fwd_x(float2* m0, const float2* m1, const float2* __restrict__ tw,
+                                                      const float* __restrict__ winv) {
+  constexpr int NH = N / 2, LB = Geo<N>::LB;
+  extern __shared__ float2 sm[];  // dynamic: (1 + ILV) * N * LB
+  float2* s0 = sm;
+  float2* s1 = sm + N * LB;
+  const int nz0 = blockIdx.x * LB, ny = blockIdx.y, mesh = blockIdx.z;
+  const size_t moff = (size_t)mesh * N * N * NH;
+  float2* b0 = m0 + moff + (size_t)ny * NH + nz0;
+  const float2* b1 = ILV ? m1 + moff + (size_t)ny * NH + nz0 : nullptr;
+  for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+    const int l = i % LB, e = i / LB;
+    s0[i] = b0[(size_t)e * N * NH + l];
+    if (ILV) s1[i] = b1[(size_t)e * N * NH + l];
+  }
+  __syncthreads();
+  fft_smem<N, LB, -1>(s0, tw);
+  if (ILV) fft_smem<N, LB, -1>(s1, tw);
+  const int sy = sgn_idx(ny, N);
+  const float wy = winv[ny];
+  for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+    const int l = i % LB, e = i / LB;
+    const int nz = nz0 + l;
+    float2 v = s0[i];
+    if (ILV) {
+      const int ph = (sgn_idx(e, N) + sy + nz) * (BISP_TWN / (2 * N));
+      const float2 p = tw[ph & (BISP_TWN - 1)];
+      const float2 d1 = cmul(p, s1[i]);
+      v = make_float2(0.5f * (v.x + d1.x), 0.5f * (v.y + d1.y));
+    }
+    const float wi = winv[e] * wy * winv[nz];
+    v = make_float2(v.x * wi, v.y * wi);
+    if (e == NH || ny == NH) v = make_float2(0.f, 0.f);
+    b0[(size_t)e * N * NH + l] = v;
+  }
+}
+
+template <typename K>
+static void smem_attr(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    BISP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+template <int N>
+static void fwd_impl(float* mesh0, float* mesh1, int count, int mas, const float2* tw, const float* winv,
+                     cudaStream_t s, int* launches) {
+  using G = Geo<N>;
+  const int rows = count * N * N;
+  k_fwd_z<N><<<rows / G::LBZ, G::TZ, 0, s>>>(mesh0, tw);
+  BISP_CHECK_LAUNCH();
+  if (mesh1) {
+    k_fwd_z<N><<<rows / G::LBZ, G::TZ, 0, s>>>(mesh1, tw);
+    BISP_CHECK_LAUNCH();
+  }
+  dim3 gy(G::NH / G::LB, N, count);
+  const size_t s1 = (size_t)N * G::LB * sizeof(float2);
+  smem_attr(k_fwd_y<N>, s1);
+  k_fwd_y<N><<<gy, G::TS, s1, s>>>(reinterpret_cast<float2*>(mesh0), tw);
+  BISP_CHECK_LAUNCH();
+  if (mesh1) {
+    k_fwd_y<N><<<gy, G::TS, s1, s>>>(reinterpret_cast<float2*>(mesh1), tw);
+    BISP_CHECK_LAUNCH();
+  }
+  const size_t sh = (mesh1 ? 2 : 1) * (size_t)N * G::LB * sizeof(float2);
+  if (mesh1) {
+    smem_attr(k_fwd_x<N, 1>, sh);
+    k_fwd_x<N, 1><<<gy, G::TS, sh, s>>>(reinterpret_cast<float2*>(mesh0), reinterpret_cast<const float2*>(mesh1),
+                                          tw, winv);
+  } else {
+    smem_attr(k_fwd_x<N, 0>, sh);
+    k_fwd_x<N, 0><<<gy, G::TS, sh, s>>>(reinterpret_cast<float2*>(mesh0), nullptr, tw, winv);
+  }
+  BISP_CHECK_LAUNCH();
+  if (launches) *launches += mesh1 ? 5 : 3;
+  (void)mas;
+}
+
+void forward_fft(float* mesh0, float* mesh1, int count, int N, int mas, const float2* tw, const float* winv,
+                 cudaStream_t s, int* launches) {
+  switch (N) {
+    case 16: fwd_impl<16>(mesh0, mesh1, count, mas, tw, winv, s, launches); break;
+    case 32: fwd_impl<32>(mesh0, mesh1, count, mas, tw, winv, s, launches); break;
+    case 64: fwd_impl<64>(mesh0, mesh1, count, mas, tw, winv, s, launches); break;
+    case 128: fwd_impl<128>(mesh0, mesh1, count, mas, tw, winv, s, launches); break;
+    case 256: fwd_impl<256>(mesh0, mesh1, count, mas, tw, winv, s, launches); break;
+    case 512: fwd_impl<512>(mesh0, mesh1, count, mas, tw, winv, s, launches); break;
+    case 1024: fwd_impl<1024>(mesh0, mesh1, count, mas, tw, winv, s, launches); break;
+    default: throw Error{1, "unsupported mesh size"};
+  }
+}
+
+// ====================================================================================
+// inverse, pruned
+// ====================================================================================
+__constant__ InvBatch c_inv;
+
+// y_l^m(n) for one (l, m >= 0) by the associated-Legendre recurrence (see common.cuh)
+__device__ __forceinline__ float2 ylm_one(int l, int m, float x, float y, float z, const float* ynorm) {
+  const float r2 = x * x + y * y + z * z;
+  if (r2 == 0.f) return l == 0 ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
+  const float rinv = rsqrtf(r2);
+  const float mu = z * rinv;
+  float pmm = 1.f;
+  for (int k = 1; k <= m; ++k) pmm *= -(2.f * k - 1.f);
+  float p = pmm;
+  if (l > m) {
+    float pm2 = pmm, pm1 = (2.f * m + 1.f) * mu * pmm;
+    p = pm1;
+    for (int ll = m + 2; ll <= l; ++ll) {
+      p = ((2.f * ll - 1.f) * mu * pm1 - (float)(ll + m - 1) * pm2) / (float)(ll - m);
+      pm2 = pm1;
+      pm1 = p;
+    }
+  }
+  float2 e = make_float2(1.f, 0.f);
+  const float2 e1 = make_float2(x * rinv, y * rinv);
+  for (int k = 0; k < m; ++k) e = cmul(e, e1);
+  const float a = ynorm[l * (BISP_LMAX + 1) + m] * p;
+  return make_float2(a * e.x, a * e.y);
+}
+
+__device__ __forceinline__ float cw2_val(const float* t, int N, int ix, int iy, int iz, int interlace) {
+  // t = [e1 (N), o1 (N)] with e1 = E/W^2, o1 = O/W^2 per axis
+  float v = t[ix] * t[iy] * t[iz];
+  if (interlace) v = 0.5f * (v + t[N + ix] * t[N + iy] * t[N + iz]);
+  return v;
+}
+
+// scratch layout per field: T1 [N][2P+1][Pz], T2 [N][N][Pz]
+struct InvGeo {
+  int N, P, Pz, ny;
+  size_t t1, t2;
+};
+__host__ __device__ __forceinline__ InvGeo inv_geo(int N, int P, int LB) {
+  InvGeo g;
+  g.N = N;
+  g.P = P;
+  g.Pz = ((P + 1 + LB - 1) / LB) * LB;
+  g.ny = 2 * P + 1;
+  g.t1 = (size_t)N * g.ny * g.Pz;
+  g.t2 = (size_t)N * N * g.Pz;
+  return g;
+}
+
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(float2* t1all, const float2* __restrict__ tw) {
+  constexpr int NH = N / 2, LB = Geo<N>::LB;
+  extern __shared__ float2 s[];
+  const InvBatch& B = c_inv;
+  const InvGeo g = inv_geo(N, B.P, LB);
+  const int nz0 = blockIdx.x * LB, iy = blockIdx.y;
+  const int sy = iy - g.P;
+  const int jy = sy & (N - 1);
+  for (int f = 0; f < B.nf; ++f) {
+    const InvField& F = B.f[f];
+    for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+      const int l = i % LB, e = i / LB;
+      const int nz = nz0 + l;
+      const int sx = sgn_idx(e, N);
+      float2 v = make_float2(0.f, 0.f);
+      if (sx <= g.P && sx >= -g.P && nz <= g.P) {
+        const size_t gi = ((size_t)e * N + jy) * NH + nz;
+        if (F.kind == SRC_PLAIN) {
+          v = cscale(F.A[gi], F.scale);
+        } else if (F.kind == SRC_QSHOT) {
+          const float2 a = F.A[gi], b = F.B[gi];
+          v = cmul(a, cconj(b));
+          const float c = F.sbar * cw2_val(B.cw2_1d, N, e, jy, nz, B.interlace);
+          v = make_float2((v.x - c) * F.scale, v.y * F.scale);
+        } else {
+          const long long q = (long long)sx * sx + (long long)sy * sy + (long long)nz * nz;
+          if (q >= B.qlo && q < B.qhi) {
+            const float2 y = ylm_one(F.l, F.m, (float)sx, (float)sy, (float)nz, B.ynorm);
+            // part of y_l^{m*}: Re y or -Im y
+            float c = (F.part ? -y.y : y.x) * B.inv_nmodes;
+            float2 a = F.unit ? make_float2(1.f, 0.f) : F.A[gi];
+            // times (-i)^l
+            float2 t = make_float2(a.x * c, a.y * c);
+            switch (F.l & 3) {
+              case 0: v = t; break;
+              case 1: v = make_float2(t.y, -t.x); break;
+              case 2: v = make_float2(-t.x, -t.y); break;
+              default: v = make_float2(-t.y, t.x); break;
+            }
+          }
+        }
+      }
+      s[i] = v;
+    }
+    __syncthreads();
+    fft_smem<N, LB, +1>(s, tw);
+    float2* t1 = t1all + (size_t)f * g.t1;
+    for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+      const int l = i % LB, e = i / LB;
+      t1[((size_t)e * g.ny + iy) * g.Pz + nz0 + l] = s[i];
+    }
+    __syncthreads();
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::TS) k_inv_y(const float2* t1all, float2* t2all,
+                                                      const float2* __restrict__ tw) {
+  constexpr int LB = Geo<N>::LB;
+  extern __shared__ float2 s[];
+  const InvBatch& B = c_inv;
+  const InvGeo g = inv_geo(N, B.P, LB);
+  const int nz0 = blockIdx.x * LB, x = blockIdx.y, f = blockIdx.z;
+  const float2* t1 = t1all + (size_t)f * g.t1;
+  for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+    const int l = i % LB, e = i / LB;
+    const int sy = sgn_idx(e, N);
+    float2 v = make_float2(0.f, 0.f);
+    if (sy >= -g.P && sy <= g.P) v = t1[((size_t)x * g.ny + (sy + g.P)) * g.Pz + nz0 + l];
+    s[i] = v;
+  }
+  __syncthreads();
+  fft_smem<N, LB, +1>(s, tw);
+  float2* t2 = t2all + (size_t)f * g.t2;
+  for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+    const int l = i % LB, e = i / LB;
+    t2[((size_t)x * N + e) * g.Pz + nz0 + l] = s[i];
+  }
+}
+
+// c2r along z: X[k], k <= P (Pz stored, zero above P), Nyquist zero.
+//   Z[k] = (X[k] + X*[NH-k]) + i (X[k] - X*[NH-k]) e^{2 pi i k / N};  z = IDFT_NH(Z)
+//   x[2j] = Re z[j], x[2j+1] = Im z[j]
+template <int N>
+__global__ void __launch_bounds__(Geo<N>::TZ) k_inv_z(const float2* t2all, const float2* __restrict__ tw) {
+  constexpr int NH = N / 2, LBZ = Geo<N>::LBZ, LD = LBZ + 1;
+  __shared__ float2 s[NH * LD];
+  const InvBatch& B = c_inv;
+  const InvGeo g = inv_geo(N, B.P, Geo<N>::LB);
+  const int f = blockIdx.y;
+  const size_t r0 = (size_t)blockIdx.x * LBZ;
+  const float2* t2 = t2all + (size_t)f * g.t2 + r0 * g.Pz;
+  for (int i = threadIdx.x; i < LBZ * NH; i += blockDim.x) {
+    const int l = i / NH, e = i % NH;
+    s[e * LD + l] = e < g.Pz ? t2[(size_t)l * g.Pz + e] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < LBZ * (NH / 2 + 1); i += blockDim.x) {
+    const int l = i % LBZ, k = i / LBZ;
+    if (k == 0) {
+      const float a = s[l].x;
+      s[l] = make_float2(a, a);
+    } else {
+      const int kp = NH - k;
+      const float2 a = s[k * LD + l], b = s[kp * LD + l];
+      const float2 wk = cconj(tw[k * (BISP_TWN / N)]);
+      const float2 wkp = cconj(tw[kp * (BISP_TWN / N)]);
+      const float2 sp = make_float2(a.x + b.x, a.y - b.y);   // a + b*
+      const float2 dm = make_float2(a.x - b.x, a.y + b.y);   // a - b*
+      const float2 t = cmul(dm, wk);
+      const float2 zk = make_float2(sp.x - t.y, sp.y + t.x);  // sp + i t
+      const float2 sp2 = make_float2(b.x + a.x, b.y - a.y);
+      const float2 dm2 = make_float2(b.x - a.x, b.y + a.y);
+      const float2 t2v = cmul(dm2, wkp);
+      const float2 zkp = make_float2(sp2.x - t2v.y, sp2.y + t2v.x);
+      s[k * LD + l] = zk;
+      if (kp != k) s[kp * LD + l] = zkp;
+    }
+  }
+  __syncthreads();
+  fft_smem<NH, LBZ, +1>(s, tw, LD);
+  float* out = B.f[f].out + r0 * N;
+  float2* o2 = reinterpret_cast<float2*>(out);
+  for (int i = threadIdx.x; i < LBZ * NH; i += blockDim.x) {
+    const int l = i / NH, e = i % NH;
+    o2[(size_t)l * NH + e] = s[e * LD + l];
+  }
+}
+
+template <int N>
+static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStream_t s, int* launches) {
+  using G = Geo<N>;
+  const InvGeo g = inv_geo(N, b.P, G::LB);
+  float2* t1 = reinterpret_cast<float2*>(scratch);
+  float2* t2 = t1 + (size_t)b.nf * g.t1;
+  BISP_CUDA(cudaMemcpyToSymbolAsync(c_inv, &b, sizeof(InvBatch), 0, cudaMemcpyHostToDevice, s));
+  const size_t s1 = (size_t)N * G::LB * sizeof(float2);
+  smem_attr(k_inv_x<N>, s1);
+  smem_attr(k_inv_y<N>, s1);
+  k_inv_x<N><<<dim3(g.Pz / G::LB, g.ny), G::TS, s1, s>>>(t1, tw);
+  BISP_CHECK_LAUNCH();
+  k_inv_y<N><<<dim3(g.Pz / G::LB, N, b.nf), G::TS, s1, s>>>(t1, t2, tw);
+  BISP_CHECK_LAUNCH();
+  k_inv_z<N><<<dim3(N * N / G::LBZ, b.nf), G::TZ, 0, s>>>(t2, tw);
+  BISP_CHECK_LAUNCH();
+  if (launches) *launches += 3;
+}
+
+size_t inverse_scratch_bytes(int N, int P, int nf) {
+  const int LB = (N >= 1024 || N < 32) ? 8 : 16;
+  const InvGeo g = inv_geo(N, P, LB);
+  return (size_t)nf * (g.t1 + g.t2) * sizeof(float2);
+}
+
+void inverse_fft(const InvBatch& b, const float2* tw, void* scratch, cudaStream_t s, int* launches) {
+  if (b.nf <= 0) return;
+  if (b.P < 0 || b.P > b.N / 2 - 1) throw Error{1, "inverse_fft: bad prune extent"};
+  switch (b.N) {
+    case 16: inv_impl<16>(b, tw, scratch, s, launches); break;
+    case 32: inv_impl<32>(b, tw, scratch, s, launches); break;
+    case 64: inv_impl<64>(b, tw, scratch, s, launches); break;
+    case 128: inv_impl<128>(b, tw, scratch, s, launches); break;
+    case 256: inv_impl<256>(b, tw, scratch, s, launches); break;
+    case 512: inv_impl<512>(b, tw, scratch, s, launches); break;
+    case 1024: inv_impl<1024>(b, tw, scratch, s, launches); break;
+    default: throw Error{1, "unsupported mesh size"};
+  }
+}
+
+}  // namespace bisp

@@ -1,0 +1,160 @@
+// Host-side declarations shared by the .cu files of the library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace bisp {
+
+// ---- error handling -------------------------------------------------------------
+struct Error {
+  int status;
+  std::string msg;
+};
+#define BISP_CUDA(call)                                                                   \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::bisp::Error{3, std::string(#call) + ": " + cudaGetErrorString(e_)};         \
+  } while (0)
+#define BISP_CHECK_LAUNCH() BISP_CUDA(cudaGetLastError())
+
+// ---- channel descriptors --------------------------------------------------------
+// A channel is one real mesh: weight^power * (Re or Im)(y_L^M(x_hat) or its conjugate).
+struct Chan {
+  int L, M, part;  // part 0: real part, 1: imaginary part
+  int power;       // 1: delta n channels (w y*), 2: N channels (w^2 y)
+  int conj;        // 1: y_L^{M*}, 0: y_L^M
+};
+
+// device-side prep parameters
+struct PrepArgs {
+  const float* xyz;
+  const float* w;      // or nullptr
+  const float* nbar;   // or nullptr
+  int64_t n;
+  int N;
+  double H, box;
+  int mas;
+  float P0;            // FKP P0 (0: off)
+  int local;
+  float obs[3];
+  int nchan;
+  Chan chan[32];
+  const float* ynorm;  // (BISP_LMAX+1)^2 table
+  // outputs
+  uint32_t* keys;
+  uint32_t* idx;
+  float4* frac;        // dx, dy, dz, unused
+  float* vals;         // [nchan][n]
+  double* partials;    // [blocks][nsum]  sums: w, then w^3 * Re/Im y* for each D channel
+  int nsum;
+  int* bad;            // count of non-finite / out-of-box positions
+};
+
+// launches (defined in assign.cu)
+int prep_blocks(int64_t n);
+void launch_prep(const PrepArgs& a, cudaStream_t s);
+size_t radix_sort_scratch_bytes(int64_t n);
+// Stable sort of (keys, vals) by the low `bits` bits of keys.  Results in keys_out/vals_out.
+void radix_sort(uint32_t* keys, uint32_t* vals, uint32_t* keys_out, uint32_t* vals_out, int64_t n,
+                int bits, void* scratch, cudaStream_t s, int* launches);
+size_t scan_scratch_bytes(int64_t n);
+void exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* scratch, cudaStream_t s,
+                        int* launches);
+void launch_count_cells(const uint32_t* keys, int64_t n, uint32_t* counts, cudaStream_t s);
+void launch_gather_particles(const uint32_t* perm, int64_t n, const float4* frac_in, const float* vals_in,
+                             int nchan, float4* frac_out, float* vals_out, cudaStream_t s);
+struct DepositArgs {
+  const uint32_t* cell_start;  // N^3 + 1
+  const float4* frac;          // sorted
+  const float* vals;           // sorted [nchan][n]
+  int64_t n;
+  int N, mas, interlace, nchan;
+  float* mesh0;                // [nchan][N^3]
+  float* mesh1;                // [nchan][N^3] (interlaced) or nullptr
+};
+void launch_deposit(const DepositArgs& a, cudaStream_t s, int* launches);
+// sum_c m(c)^3 over a real mesh, FP64 partials per block (deterministic), returns #blocks
+int launch_sum_cubes(const float* mesh, int64_t ncell, double* partials, cudaStream_t s);
+
+// ---- FFT (fft.cu) ---------------------------------------------------------------
+// Forward r2c 3D FFT of `count` channel meshes held as [count][N][N][N] floats; if
+// mesh1 != nullptr the interlaced pair is combined.  Output: deconvolved half spectra,
+// complex [N][N][N/2] (nz < N/2, Nyquist planes zero), written over mesh0.
+void forward_fft(float* mesh0, float* mesh1, int count, int N, int mas, const float2* tw,
+                 const float* winv1d, cudaStream_t s, int* launches);
+
+// Inverse transforms from half spectra to real fields, pruned to |n_i| <= P.
+enum SrcKind { SRC_PLAIN = 0, SRC_QSHOT = 1, SRC_SHELL = 2 };
+struct InvField {
+  // SRC_PLAIN:  spec(k) = scale * A(k)
+  // SRC_QSHOT:  spec(k) = scale * (A(k) conj(B(k)) - sbar * cw2(k))
+  // SRC_SHELL:  spec(k) = mask_b(k)/Nm * (-i)^l * part(y_l^{m*}(k)) * (A(k) or 1)
+  int kind;
+  const float2* A;
+  const float2* B;
+  float sbar;
+  float scale;
+  int l, m, part, unit;   // SRC_SHELL
+  float* out;             // real field [N][N][N]
+};
+struct InvBatch {
+  int N, P;               // prune extent: modes with |nx|,|ny|,nz <= P
+  int nf;                 // number of fields (<= 32)
+  InvField f[32];
+  // shell geometry (SRC_SHELL)
+  long long qlo, qhi;     // |n|^2 in [qlo, qhi)
+  float inv_nmodes;
+  const float* ynorm;
+  const float* cw2_1d;    // QSHOT: per-axis tables (E, O, W) packed, see fft.cu
+  int interlace;
+};
+size_t inverse_scratch_bytes(int N, int P, int nf);
+void inverse_fft(const InvBatch& b, const float2* tw, void* scratch, cudaStream_t s, int* launches);
+
+// ---- shell sums and pair reduction (measure.cu) -----------------------------------
+void launch_axpby(float2* out, const float2* x, double a, const float2* y, double b, size_t n,
+                  int zero_k0, cudaStream_t s);
+
+struct ZsumArgs {
+  const float2* D00;      // delta n spectrum
+  const float2* NR;       // N_L^M real-part channel spectrum
+  const float2* NI;       // imaginary-part channel or nullptr (M = 0)
+  double sbar_re, sbar_im;
+  int N, P;
+  int nbins;
+  const long long* qlo;   // [nbins]
+  const long long* qhi;
+  const float* cw2_1d;
+  int interlace;
+  int nlm;                // number of (l, m) pairs, m >= 0
+  int lm[16][2];
+  const float* ynorm;
+  double* partials;       // [nbins][nblk][nlm][2]
+  int nblk;
+};
+void launch_zsum(const ZsumArgs& a, cudaStream_t s);
+
+struct PairRecipe { int comp, g; float coef; };
+struct PairTermDesc { int xoff, xcnt, yoff, ycnt; };
+struct PairJob {
+  const float* fields;    // component field (b, c) at fields + (b*ncomp + c) * Ng
+  const float* gfields;   // g field i at gfields + i * Ng
+  int64_t Ng;
+  int nb, ncomp, ng;
+  int nout;               // outputs (multipole x G-set)
+  int out_term_off[33];   // terms of output o: [off[o], off[o+1])
+  int nterm;
+  PairTermDesc term[64];
+  int nrec;
+  PairRecipe rec[512];
+};
+// Result: out[o][b1][b2] = sum_x sum_{t in o} X_t(x;b1) Y_t(x;b2)   (FP64)
+void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scratch_bytes,
+                 cudaStream_t s, int* launches);
+size_t pair_scratch_bytes(const PairJob& job);
+
+}  // namespace bisp

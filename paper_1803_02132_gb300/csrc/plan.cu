@@ -1,0 +1,1268 @@
+// Host side of the library: plan (validation, k-shell thresholds, channels, Wigner 3j
+// contraction recipes in FP64), orchestration of bisp_assign / bisp_measure, and the
+// C ABI declared in include/bisp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/bisp.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace bisp;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct Fail {
+  int status;
+  std::string msg;
+};
+[[noreturn]] void fail(int st, const std::string& m) { throw Fail{st, m}; }
+
+// ---------------------------------------------------------------------------------
+// FP64 helpers: Wigner 3j (Racah's formula), y_l^m normalisation, y_l^{m*}
+// ---------------------------------------------------------------------------------
+double lfact(int n) { return std::lgamma((double)n + 1.0); }
+
+double wigner3j(int j1, int j2, int j3, int m1, int m2, int m3) {
+  if (m1 + m2 + m3 != 0) return 0.0;
+  if (std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(m3) > j3) return 0.0;
+  if (j3 < std::abs(j1 - j2) || j3 > j1 + j2) return 0.0;
+  // exact integer factorials up to 20! fit in double mantissa only approximately; use
+  // long double products of small integers (arguments here are <= 12)
+  auto f = [](int n) {
+    long double r = 1.0L;
+    for (int i = 2; i <= n; ++i) r *= (long double)i;
+    return r;
+  };
+  const long double tri = f(j1 + j2 - j3) * f(j1 - j2 + j3) * f(-j1 + j2 + j3) / f(j1 + j2 + j3 + 1);
+  const long double pref = std::sqrt(tri * f(j1 + m1) * f(j1 - m1) * f(j2 + m2) * f(j2 - m2) * f(j3 + m3) * f(j3 - m3));
+  const int tmin = std::max({0, j2 - j3 - m1, j1 - j3 + m2});
+  const int tmax = std::min({j1 + j2 - j3, j1 - m1, j2 + m2});
+  long double s = 0.0L;
+  for (int t = tmin; t <= tmax; ++t) {
+    const long double den =
+        f(t) * f(j3 - j2 + t + m1) * f(j3 - j1 + t - m2) * f(j1 + j2 - j3 - t) * f(j1 - t - m1) * f(j2 - t + m2);
+    s += ((t & 1) ? -1.0L : 1.0L) / den;
+  }
+  const double sign = ((j1 - j2 - m3) & 1) ? -1.0 : 1.0;
+  return sign * (double)(pref * s);
+}
+
+// y_l^m (m >= 0) of the direction (x, y, z), FP64, Condon-Shortley phase
+void ylm_host(int l, int m, double x, double y, double z, double* re, double* im) {
+  const double r = std::sqrt(x * x + y * y + z * z);
+  if (r == 0.0) {
+    *re = l == 0 ? 1.0 : 0.0;
+    *im = 0.0;
+    return;
+  }
+  const double mu = z / r;
+  double pmm = 1.0;
+  for (int k = 1; k <= m; ++k) pmm *= -(2.0 * k - 1.0);
+  double p = pmm;
+  if (l > m) {
+    double pm2 = pmm, pm1 = (2.0 * m + 1.0) * mu * pmm;
+    p = pm1;
+    for (int ll = m + 2; ll <= l; ++ll) {
+      p = ((2.0 * ll - 1.0) * mu * pm1 - (double)(ll + m - 1) * pm2) / (double)(ll - m);
+      pm2 = pm1;
+      pm1 = p;
+    }
+  }
+  double er = 1.0, ei = 0.0;
+  const double cx = x / r, cy = y / r;
+  for (int k = 0; k < m; ++k) {
+    const double t = er * cx - ei * cy;
+    ei = er * cy + ei * cx;
+    er = t;
+  }
+  static const std::vector<double> ntab = [] {
+    std::vector<double> t((BISP_LMAX + 1) * (BISP_LMAX + 1));
+    for (int a = 0; a <= BISP_LMAX; ++a)
+      for (int b = 0; b <= a; ++b) t[a * (BISP_LMAX + 1) + b] = std::exp(0.5 * (lfact(a - b) - lfact(a + b)));
+    return t;
+  }();
+  const double norm = ntab[l * (BISP_LMAX + 1) + m];
+  *re = norm * p * er;
+  *im = norm * p * ei;
+}
+
+// y_l^{m*} for signed m
+void ystar_host(int l, int m, double x, double y, double z, double* re, double* im) {
+  const int am = std::abs(m);
+  double a, b;
+  ylm_host(l, am, x, y, z, &a, &b);
+  if (m >= 0) {
+    *re = a;
+    *im = -b;
+  } else {  // y_l^{-m*} = (-1)^m y_l^m
+    const double s = (am & 1) ? -1.0 : 1.0;
+    *re = s * a;
+    *im = s * b;
+  }
+}
+
+struct cplx {
+  double r = 0, i = 0;
+};
+cplx cm(cplx a, cplx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+cplx cc(cplx a) { return {a.r, -a.i}; }
+
+// ---------------------------------------------------------------------------------
+// device buffer cache
+// ---------------------------------------------------------------------------------
+struct DBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  void ensure(size_t bytes, size_t* total) {
+    if (bytes <= n) return;
+    release(total);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      char buf[160];
+      snprintf(buf, sizeof buf, "device allocation of %.3f GB failed (%s)", bytes / 1e9, cudaGetErrorString(e));
+      fail(BISP_ENOMEM, buf);
+    }
+    n = bytes;
+    *total += bytes;
+  }
+  void release(size_t* total) {
+    if (p) {
+      cudaFree(p);
+      *total -= n;
+    }
+    p = nullptr;
+    n = 0;
+  }
+  template <class T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+struct Comp {
+  int l, m, part;
+};
+
+struct Catalog {
+  bool assigned = false;
+  int64_t n = 0;
+  bool unit_w = true;   // N channels alias the D channels (no weights)
+  int nspec = 0;
+  DBuf spec;            // [nspec][Nk] float2
+  double sumw = 0.0;
+  std::vector<double> sbar;  // per D channel: sum w^3 part(y*)
+  double sumR3 = 0.0;
+  DBuf dbg_mesh;
+  int launches = 0;
+  double ms = 0.0;
+};
+
+}  // namespace
+
+struct bisp_plan {
+  // parameters
+  int N = 0, NH = 0, nb = 0, nmult = 0, los = 0, mas = 2, interlace = 0, want_window = 0;
+  double L = 0, H = 0, kF = 0, V = 0, P0 = 0, obs[3] = {0, 0, 0};
+  size_t max_bytes = 0;
+  int64_t Ng = 0, Nk = 0;
+  std::vector<double> edges;
+  std::vector<std::array<int, 3>> ells;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool debug_mesh = false;
+  // channels
+  std::vector<Chan> dch, nch;
+  std::vector<int> Ls, ls;
+  int d00 = 0, n00 = 0;
+  // shells
+  std::vector<long long> qlo, qhi;
+  std::vector<int> Pb;
+  std::vector<double> nmodes;
+  std::vector<Comp> comps;
+  std::map<std::tuple<int, int, int>, int> comp_index;  // (l, m, part) -> index
+  std::vector<std::vector<cplx>> Y;                     // [b][lm index (l, m signed)]
+  // contraction recipes per multipole (pair-kernel terms with g indices into a G set)
+  struct Term {
+    std::vector<PairRecipe> x, y;
+  };
+  std::vector<std::vector<Term>> terms;
+  // device constants
+  DBuf tw, winv, ynorm, cw2, qlo_d, qhi_d;
+  Catalog cat[2];
+  // measurement buffers
+  DBuf pass_spec[2], gf[2], qf, pool, invscr, pairscr, pairout, zpart;
+  size_t bytes = 0;
+  // bookkeeping
+  double alpha = 0.0, normI = 0.0;
+  int launches_measure = 0, pair_launches = 0;
+  double ms_measure = 0.0, ms_pair = 0.0, pair_bytes = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  int lm_index(int l, int m) const {  // index of (l, m) in the Y table: l^2 + (m + l)
+    return l * l + (m + l);
+  }
+  int dchan(int L_, int M_, int part) const {
+    for (size_t c = 0; c < dch.size(); ++c)
+      if (dch[c].L == L_ && dch[c].M == M_ && dch[c].part == part) return (int)c;
+    return -1;
+  }
+  int nchan(int L_, int M_, int part) const {
+    for (size_t c = 0; c < nch.size(); ++c)
+      if (nch[c].L == L_ && nch[c].M == M_ && nch[c].part == part) return (int)c;
+    return -1;
+  }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------------
+// plan construction
+// ---------------------------------------------------------------------------------
+void validate(const bisp_params* p) {
+  if (!p) fail(BISP_EINVAL, "params is NULL");
+  const int N = p->nmesh;
+  if (N < 16 || N > BISP_NMAX || (N & (N - 1))) fail(BISP_EINVAL, "nmesh must be a power of two in [16, 1024]");
+  if (!(p->box_len > 0.0) || !std::isfinite(p->box_len)) fail(BISP_EINVAL, "box_len must be positive");
+  if (p->nbins < 1 || !p->k_edges) fail(BISP_EINVAL, "need nbins >= 1 and k_edges");
+  for (int b = 0; b <= p->nbins; ++b) {
+    if (!(p->k_edges[b] > 0.0) || !std::isfinite(p->k_edges[b])) fail(BISP_EINVAL, "k_edges must be positive and finite");
+    if (b && !(p->k_edges[b] > p->k_edges[b - 1])) fail(BISP_EINVAL, "k_edges must be ascending");
+  }
+  if (p->n_mult < 1 || !p->ells) fail(BISP_EINVAL, "need n_mult >= 1 and ells");
+  for (int i = 0; i < p->n_mult; ++i) {
+    const int l1 = p->ells[3 * i], l2 = p->ells[3 * i + 1], L = p->ells[3 * i + 2];
+    const bool ok = l1 >= l2 && l2 >= 0 && L % 2 == 0 && L >= std::abs(l1 - l2) && L <= l1 + l2 &&
+                    (l1 + l2 + L) % 2 == 0;
+    if (!ok) {
+      char buf[128];
+      snprintf(buf, sizeof buf, "multipole (%d,%d,%d) violates the selection rules", l1, l2, L);
+      fail(BISP_EINVAL, buf);
+    }
+    if (l1 > BISP_LMAX || L > BISP_LMAX) fail(BISP_EUNSUPPORTED, "l and L above 4 are not built");
+  }
+  if (p->los != BISP_LOS_GLOBAL_Z && p->los != BISP_LOS_LOCAL) fail(BISP_EINVAL, "los");
+  if (p->mas < 1 || p->mas > 3) fail(BISP_EINVAL, "mas must be 1 (NGP), 2 (CIC) or 3 (TSC)");
+  if (!std::isfinite(p->fkp_P0) || p->fkp_P0 < 0) fail(BISP_EINVAL, "fkp_P0");
+  if (p->los == BISP_LOS_LOCAL)
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(p->observer[k])) fail(BISP_EINVAL, "observer");
+}
+
+void build_channels(bisp_plan* P) {
+  std::vector<int> Ls = {0}, ls;
+  for (auto& e : P->ells) {
+    Ls.push_back(e[2]);
+    ls.push_back(e[0]);
+    ls.push_back(e[1]);
+  }
+  std::sort(Ls.begin(), Ls.end());
+  Ls.erase(std::unique(Ls.begin(), Ls.end()), Ls.end());
+  std::sort(ls.begin(), ls.end());
+  ls.erase(std::unique(ls.begin(), ls.end()), ls.end());
+  P->Ls = Ls;
+  P->ls = ls;
+  P->dch.clear();
+  P->nch.clear();
+  if (P->los == BISP_LOS_GLOBAL_Z) {
+    P->dch.push_back({0, 0, 0, 1, 1});
+    P->nch.push_back({0, 0, 0, 2, 0});
+  } else {
+    for (int L : Ls)
+      for (int M = 0; M <= L; ++M)
+        for (int part = 0; part < (M ? 2 : 1); ++part) {
+          P->dch.push_back({L, M, part, 1, 1});
+          P->nch.push_back({L, M, part, 2, 0});
+        }
+  }
+  P->d00 = P->dchan(0, 0, 0);
+  P->n00 = P->nchan(0, 0, 0);
+  P->comps.clear();
+  P->comp_index.clear();
+  for (int l : ls)
+    for (int m = 0; m <= l; ++m)
+      for (int part = 0; part < (m ? 2 : 1); ++part) {
+        P->comp_index[{l, m, part}] = (int)P->comps.size();
+        P->comps.push_back({l, m, part});
+      }
+  if ((int)P->comps.size() > 32) fail(BISP_EUNSUPPORTED, "too many field components");
+}
+
+void build_shells(bisp_plan* P) {
+  const int N = P->N, nb = P->nb;
+  const long long qmax = 3LL * (N / 2) * (N / 2);
+  P->qlo.assign(nb, -1);
+  P->qhi.assign(nb, -1);
+  // bin of q: e_b <= kF sqrt(q) < e_{b+1}, FP64
+  std::vector<int> binq(qmax + 1, -1);
+  for (long long q = 1; q <= qmax; ++q) {
+    const double k = P->kF * std::sqrt((double)q);
+    const auto it = std::upper_bound(P->edges.begin(), P->edges.end(), k);
+    const int b = (int)(it - P->edges.begin()) - 1;
+    if (b >= 0 && b < nb) binq[q] = b;
+  }
+  for (int b = 0; b < nb; ++b) {
+    for (long long q = 1; q <= qmax; ++q)
+      if (binq[q] == b) {
+        if (P->qlo[b] < 0) P->qlo[b] = q;
+        P->qhi[b] = q + 1;
+      }
+    if (P->qlo[b] < 0) P->qlo[b] = P->qhi[b] = 1;  // empty bin
+  }
+  P->Pb.assign(nb, 0);
+  for (int b = 0; b < nb; ++b) {
+    int pb = (int)std::floor(std::sqrt((double)(P->qhi[b] - 1)));
+    while ((long long)(pb + 1) * (pb + 1) <= P->qhi[b] - 1) ++pb;
+    while ((long long)pb * pb > P->qhi[b] - 1) --pb;
+    P->Pb[b] = std::min(pb, N / 2 - 1);
+  }
+  // mode counts and shell averages of y_l^{m*} over the full cube (Nyquist planes out)
+  const int Pm = *std::max_element(P->Pb.begin(), P->Pb.end());
+  const int lmax = P->ls.empty() ? 0 : P->ls.back();
+  const int nlm = (lmax + 1) * (lmax + 1);
+  std::vector<std::vector<cplx>> S(nb, std::vector<cplx>(nlm));
+  std::vector<double> cnt(nb, 0.0);
+  for (int x = -Pm; x <= Pm; ++x)
+    for (int y = -Pm; y <= Pm; ++y)
+      for (int z = -Pm; z <= Pm; ++z) {
+        const long long q = (long long)x * x + (long long)y * y + (long long)z * z;
+        if (q == 0 || q > qmax) continue;
+        const int b = binq[q];
+        if (b < 0 || std::abs(x) > P->Pb[b] || std::abs(y) > P->Pb[b] || std::abs(z) > P->Pb[b]) continue;
+        cnt[b] += 1.0;
+        for (int l : P->ls)
+          for (int m = -l; m <= l; ++m) {
+            double re, im;
+            ystar_host(l, m, x, y, z, &re, &im);
+            cplx& s = S[b][P->lm_index(l, m)];
+            s.r += re;
+            s.i += im;
+          }
+      }
+  P->nmodes = cnt;
+  P->Y.assign(nb, std::vector<cplx>(nlm));
+  for (int b = 0; b < nb; ++b)
+    for (int i = 0; i < nlm; ++i)
+      if (cnt[b] > 0) P->Y[b][i] = {S[b][i].r / cnt[b], S[b][i].i / cnt[b]};
+}
+
+// Real-component expansion of Re sum_{m1 m2 M} 3j F_{l1}^{m1} F_{l2}^{m2} G_L^M with
+//   F_l^m = i^l (A + i B),  F_l^{-m} = (-1)^m i^l (A - i B),
+//   G_L^M = R + i I,        G_L^{-M} = (-1)^M (R - i I)   (global LOS: G_L^M = delta_M0 G)
+// grouped into pair-kernel terms on the side with fewer components.
+void build_recipes(bisp_plan* P) {
+  P->terms.clear();
+  const bool glob = P->los == BISP_LOS_GLOBAL_Z;
+  for (auto& e : P->ells) {
+    const int l1 = e[0], l2 = e[1], L = e[2];
+    std::map<std::tuple<int, int, int>, double> tri;  // (c1, c2, g) -> coef
+    const double il = (((l1 + l2) / 2) & 1) ? -1.0 : 1.0;  // i^{l1+l2}
+    for (int m1 = -l1; m1 <= l1; ++m1)
+      for (int m2 = -l2; m2 <= l2; ++m2) {
+        const int M = -m1 - m2;
+        if (std::abs(M) > L || (glob && M != 0)) continue;
+        const double w = wigner3j(l1, l2, L, m1, m2, M);
+        if (w == 0.0) continue;
+        const int a1 = std::abs(m1), a2 = std::abs(m2), aM = std::abs(M);
+        const double k1 = (m1 < 0 && (a1 & 1)) ? -1.0 : 1.0;
+        const double k2 = (m2 < 0 && (a2 & 1)) ? -1.0 : 1.0;
+        const double s1 = m1 < 0 ? -1.0 : 1.0, s2 = m2 < 0 ? -1.0 : 1.0;
+        const int A1 = P->comp_index.at({l1, a1, 0}), B1 = a1 ? P->comp_index.at({l1, a1, 1}) : -1;
+        const int A2 = P->comp_index.at({l2, a2, 0}), B2 = a2 ? P->comp_index.at({l2, a2, 1}) : -1;
+        int R, I;
+        double kG, sG;
+        if (glob) {
+          R = P->d00;
+          I = -1;
+          kG = 1.0;
+          sG = 1.0;
+        } else {
+          R = P->dchan(L, aM, 0);
+          I = aM ? P->dchan(L, aM, 1) : -1;
+          kG = (M < 0 && (aM & 1)) ? -1.0 : 1.0;
+          sG = M < 0 ? -1.0 : 1.0;
+        }
+        const double kap = w * il * k1 * k2 * kG;
+        tri[{A1, A2, R}] += kap;
+        if (B1 >= 0 && B2 >= 0) tri[{B1, B2, R}] += -kap * s1 * s2;
+        if (B1 >= 0 && I >= 0) tri[{B1, A2, I}] += -kap * s1 * sG;
+        if (B2 >= 0 && I >= 0) tri[{A1, B2, I}] += -kap * s2 * sG;
+      }
+    double mx = 0.0;
+    for (auto& kv : tri) mx = std::max(mx, std::fabs(kv.second));
+    std::map<int, std::vector<std::tuple<int, int, double>>> by1, by2;
+    for (auto& kv : tri) {
+      if (std::fabs(kv.second) <= 1e-13 * mx) continue;
+      const int c1 = std::get<0>(kv.first), c2 = std::get<1>(kv.first), g = std::get<2>(kv.first);
+      by1[c1].push_back({c2, g, kv.second});
+      by2[c2].push_back({c1, g, kv.second});
+    }
+    std::vector<bisp_plan::Term> ts;
+    if (by2.size() <= by1.size()) {
+      for (auto& kv : by2) {
+        bisp_plan::Term t;
+        for (auto& r : kv.second) t.x.push_back({std::get<0>(r), std::get<1>(r), (float)std::get<2>(r)});
+        t.y.push_back({kv.first, -1, 1.0f});
+        ts.push_back(t);
+      }
+    } else {
+      for (auto& kv : by1) {
+        bisp_plan::Term t;
+        t.x.push_back({kv.first, -1, 1.0f});
+        for (auto& r : kv.second) t.y.push_back({std::get<0>(r), std::get<1>(r), (float)std::get<2>(r)});
+        ts.push_back(t);
+      }
+    }
+    P->terms.push_back(ts);
+  }
+}
+
+void upload_tables(bisp_plan* P) {
+  const int N = P->N;
+  std::vector<float2> tw(BISP_TWN);
+  for (int j = 0; j < BISP_TWN; ++j) {
+    const double a = -2.0 * M_PI * (double)j / BISP_TWN;
+    tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  // deconvolution 1/W per axis, alias-sum tables C/W^2 (even and alternating images)
+  std::vector<float> winv(N), cw2(2 * N);
+  const int p = P->mas;
+  for (int j = 0; j < N; ++j) {
+    const int n = j < N / 2 ? j : j - N;
+    const double x = M_PI * n / N;
+    const double sc = n == 0 ? 1.0 : std::sin(x) / x;
+    const double w = std::pow(sc, p);
+    winv[j] = (float)(1.0 / w);
+    const double s2 = std::sin(x) * std::sin(x), c = std::cos(x), c2 = c * c;
+    double E, O;  // sum_m sinc^{2p}(x + pi m), sum_m (-1)^m sinc^{2p}(x + pi m)
+    if (p == 1) {
+      E = 1.0;
+      O = c;
+    } else if (p == 2) {
+      E = 1.0 - 2.0 / 3.0 * s2;
+      O = c * (5.0 + c2) / 6.0;
+    } else {
+      E = 1.0 - s2 + 2.0 / 15.0 * s2 * s2;
+      O = c * (61.0 + 58.0 * c2 + c2 * c2) / 120.0;
+    }
+    cw2[j] = (float)(E / (w * w));
+    cw2[N + j] = (float)(O / (w * w));
+  }
+  std::vector<float> yn((BISP_LMAX + 1) * (BISP_LMAX + 1), 0.f);
+  for (int l = 0; l <= BISP_LMAX; ++l)
+    for (int m = 0; m <= l; ++m) yn[l * (BISP_LMAX + 1) + m] = (float)std::exp(0.5 * (lfact(l - m) - lfact(l + m)));
+  P->tw.ensure(tw.size() * sizeof(float2), &P->bytes);
+  P->winv.ensure(winv.size() * sizeof(float), &P->bytes);
+  P->cw2.ensure(cw2.size() * sizeof(float), &P->bytes);
+  P->ynorm.ensure(yn.size() * sizeof(float), &P->bytes);
+  P->qlo_d.ensure(P->nb * sizeof(long long), &P->bytes);
+  P->qhi_d.ensure(P->nb * sizeof(long long), &P->bytes);
+  BISP_CUDA(cudaMemcpy(P->tw.p, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  BISP_CUDA(cudaMemcpy(P->winv.p, winv.data(), winv.size() * sizeof(float), cudaMemcpyHostToDevice));
+  BISP_CUDA(cudaMemcpy(P->cw2.p, cw2.data(), cw2.size() * sizeof(float), cudaMemcpyHostToDevice));
+  BISP_CUDA(cudaMemcpy(P->ynorm.p, yn.data(), yn.size() * sizeof(float), cudaMemcpyHostToDevice));
+  BISP_CUDA(cudaMemcpy(P->qlo_d.p, P->qlo.data(), P->nb * sizeof(long long), cudaMemcpyHostToDevice));
+  BISP_CUDA(cudaMemcpy(P->qhi_d.p, P->qhi.data(), P->nb * sizeof(long long), cudaMemcpyHostToDevice));
+}
+
+void admit(bisp_plan* P, size_t extra) {
+  size_t fre = 0, tot = 0;
+  BISP_CUDA(cudaMemGetInfo(&fre, &tot));
+  const size_t reserve = (size_t)2 << 30;
+  size_t cap = fre > reserve ? fre - reserve : 0;
+  if (P->max_bytes && P->bytes + extra > P->max_bytes) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "admission: needs %.3f GB, cap max_device_bytes = %.3f GB", (P->bytes + extra) / 1e9,
+             P->max_bytes / 1e9);
+    fail(BISP_ENOMEM, buf);
+  }
+  if (extra > cap) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "admission: needs %.3f GB more device memory, %.3f GB free", extra / 1e9, fre / 1e9);
+    fail(BISP_ENOMEM, buf);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// assign
+// ---------------------------------------------------------------------------------
+void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const float* nbar, int64_t n,
+               int ptr_is_device) {
+  if (which != BISP_DATA && which != BISP_RANDOMS) fail(BISP_EINVAL, "which must be BISP_DATA or BISP_RANDOMS");
+  if (n < 0) fail(BISP_EINVAL, "n < 0");
+  if (n > 0 && !xyz) fail(BISP_EINVAL, "xyz is NULL");
+  if (n >= (int64_t)0xffffffffLL) fail(BISP_EUNSUPPORTED, "more than 2^32-1 particles");
+  Catalog& C = P->cat[which];
+  cudaStream_t s = P->stream;
+  int launches = 0;
+  BISP_CUDA(cudaEventRecord(P->ev0, s));
+  const int N = P->N;
+  const int64_t Ng = P->Ng;
+  const bool unit_w = !w && !(nbar && P->P0 > 0);
+  // channels assigned for this catalogue: D channels, plus N channels unless aliased
+  std::vector<Chan> ch = P->dch;
+  if (!unit_w)
+    for (auto& c : P->nch) ch.push_back(c);
+  const int nchan = (int)ch.size();
+  if (nchan > 32) fail(BISP_EUNSUPPORTED, "too many channels");
+  const int ilv = P->interlace ? 1 : 0;
+  // temporaries
+  size_t tb = 0;
+  DBuf din, keys, idx, frac, vals, skeys, perm, sfrac, svals, sortscr, cells, scanscr, part, bad, mesh1;
+  const size_t sortb = radix_sort_scratch_bytes(n);
+  const size_t need = (ptr_is_device ? 0 : (size_t)n * 20) + (size_t)n * (4 * 4 + 16 * 2 + 8 * nchan) + sortb +
+                      (size_t)(Ng + 2) * 8 + scan_scratch_bytes(Ng + 1) + (size_t)nchan * Ng * 4 * (1 + ilv);
+  admit(P, need > C.spec.n ? need - C.spec.n : 0);
+  const float *dxyz = xyz, *dw = w, *dnb = nbar;
+  if (!ptr_is_device && n > 0) {
+    din.ensure((size_t)n * 4 * (3 + (w ? 1 : 0) + (nbar ? 1 : 0)), &tb);
+    float* q = din.as<float>();
+    BISP_CUDA(cudaMemcpyAsync(q, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, s));
+    dxyz = q;
+    q += 3 * n;
+    if (w) {
+      BISP_CUDA(cudaMemcpyAsync(q, w, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+      dw = q;
+      q += n;
+    }
+    if (nbar) {
+      BISP_CUDA(cudaMemcpyAsync(q, nbar, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+      dnb = q;
+    }
+  }
+  const int64_t nn = std::max<int64_t>(n, 1);
+  keys.ensure(nn * 4, &tb);
+  idx.ensure(nn * 4, &tb);
+  frac.ensure(nn * 16, &tb);
+  vals.ensure((size_t)nn * 4 * nchan, &tb);
+  const int nsum = 1 + (int)P->dch.size();
+  const int pblk = prep_blocks(n);
+  part.ensure((size_t)pblk * nsum * 8, &tb);
+  bad.ensure(64, &tb);
+  BISP_CUDA(cudaMemsetAsync(bad.p, 0, 64, s));
+  PrepArgs a{};
+  a.xyz = dxyz;
+  a.w = dw;
+  a.nbar = dnb;
+  a.n = n;
+  a.N = N;
+  a.H = P->H;
+  a.box = P->L;
+  a.mas = P->mas;
+  a.P0 = (float)P->P0;
+  a.local = P->los == BISP_LOS_LOCAL;
+  for (int k = 0; k < 3; ++k) a.obs[k] = (float)P->obs[k];
+  a.nchan = nchan;
+  for (int c = 0; c < nchan; ++c) a.chan[c] = ch[c];
+  a.ynorm = P->ynorm.as<float>();
+  a.keys = keys.as<uint32_t>();
+  a.idx = idx.as<uint32_t>();
+  a.frac = frac.as<float4>();
+  a.vals = vals.as<float>();
+  a.partials = part.as<double>();
+  a.nsum = nsum;
+  a.bad = bad.as<int>();
+  if (n > 0) {
+    launch_prep(a, s);
+    ++launches;
+  }
+  int nbad = 0;
+  std::vector<double> hp((size_t)pblk * nsum, 0.0);
+  if (n > 0) {
+    BISP_CUDA(cudaMemcpyAsync(&nbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BISP_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * 8, cudaMemcpyDeviceToHost, s));
+    BISP_CUDA(cudaStreamSynchronize(s));
+  }
+  if (nbad) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%d particles have non-finite or out-of-box positions", nbad);
+    fail(BISP_EINVAL, buf);
+  }
+  std::vector<double> sums(nsum, 0.0);
+  for (int b = 0; b < pblk; ++b)
+    for (int q = 0; q < nsum; ++q) sums[q] += hp[(size_t)b * nsum + q];
+  if (n > 0 && !(sums[0] > 0.0)) fail(BISP_EINVAL, "total weight must be positive");
+  // sort by home cell
+  int bits = 0;
+  while ((1LL << bits) < Ng) ++bits;
+  skeys.ensure(nn * 4, &tb);
+  perm.ensure(nn * 4, &tb);
+  sortscr.ensure(sortb, &tb);
+  radix_sort(keys.as<uint32_t>(), idx.as<uint32_t>(), skeys.as<uint32_t>(), perm.as<uint32_t>(), n, bits, sortscr.p,
+             s, &launches);
+  // cell starts
+  cells.ensure((size_t)(Ng + 1) * 4 * 2, &tb);
+  uint32_t* counts = cells.as<uint32_t>();
+  uint32_t* cstart = counts + (Ng + 1);
+  BISP_CUDA(cudaMemsetAsync(counts, 0, (size_t)(Ng + 1) * 4, s));
+  launch_count_cells(skeys.as<uint32_t>(), n, counts, s);
+  ++launches;
+  scanscr.ensure(scan_scratch_bytes(Ng + 1), &tb);
+  exclusive_scan_u32(counts, cstart, Ng + 1, scanscr.p, s, &launches);
+  // particles in sorted order
+  sfrac.ensure(nn * 16, &tb);
+  svals.ensure((size_t)nn * 4 * nchan, &tb);
+  launch_gather_particles(perm.as<uint32_t>(), n, frac.as<float4>(), vals.as<float>(), nchan, sfrac.as<float4>(),
+                          svals.as<float>(), s);
+  ++launches;
+  keys.release(&tb);
+  idx.release(&tb);
+  frac.release(&tb);
+  vals.release(&tb);
+  sortscr.release(&tb);
+  din.release(&tb);
+  // deposit onto the meshes; mesh 0 becomes the spectrum storage
+  C.spec.ensure((size_t)nchan * Ng * 4, &P->bytes);
+  if (ilv) mesh1.ensure((size_t)nchan * Ng * 4, &tb);
+  DepositArgs da{};
+  da.cell_start = cstart;
+  da.frac = sfrac.as<float4>();
+  da.vals = svals.as<float>();
+  da.n = n;
+  da.N = N;
+  da.mas = P->mas;
+  da.interlace = ilv;
+  da.nchan = nchan;
+  da.mesh0 = C.spec.as<float>();
+  da.mesh1 = ilv ? mesh1.as<float>() : nullptr;
+  launch_deposit(da, s, &launches);
+  sfrac.release(&tb);
+  svals.release(&tb);
+  cells.release(&tb);
+  scanscr.release(&tb);
+  skeys.release(&tb);
+  perm.release(&tb);
+  if (P->debug_mesh) {
+    C.dbg_mesh.ensure((size_t)nchan * Ng * 4, &P->bytes);
+    BISP_CUDA(cudaMemcpyAsync(C.dbg_mesh.p, C.spec.p, (size_t)nchan * Ng * 4, cudaMemcpyDeviceToDevice, s));
+  }
+  C.sumR3 = 0.0;
+  if (which == BISP_RANDOMS) {
+    part.ensure(1024 * 8, &tb);
+    const int nbk = launch_sum_cubes(C.spec.as<float>() + (size_t)P->d00 * Ng, Ng, part.as<double>(), s);
+    ++launches;
+    std::vector<double> hr(nbk);
+    BISP_CUDA(cudaMemcpyAsync(hr.data(), part.p, nbk * 8, cudaMemcpyDeviceToHost, s));
+    BISP_CUDA(cudaStreamSynchronize(s));
+    for (double v : hr) C.sumR3 += v;
+  }
+  forward_fft(C.spec.as<float>(), ilv ? mesh1.as<float>() : nullptr, nchan, N, P->mas, P->tw.as<float2>(),
+              P->winv.as<float>(), s, &launches);
+  BISP_CUDA(cudaEventRecord(P->ev1, s));
+  BISP_CUDA(cudaStreamSynchronize(s));
+  mesh1.release(&tb);
+  part.release(&tb);
+  bad.release(&tb);
+  float ms = 0.f;
+  BISP_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+  C.ms = ms;
+  C.launches = launches;
+  C.assigned = true;
+  C.n = n;
+  C.unit_w = unit_w;
+  C.nspec = nchan;
+  C.sumw = sums[0];
+  C.sbar.assign(sums.begin() + 1, sums.end());
+}
+
+// pointer + sign of the N channel c of a catalogue (aliases the D channel when unit weights)
+std::pair<const float2*, double> nspec_of(const bisp_plan* P, const Catalog& C, int c) {
+  const Chan& n = P->nch[c];
+  if (C.unit_w) {
+    const int d = P->dchan(n.L, n.M, n.part);
+    return {C.spec.as<float2>() + (size_t)d * P->Nk, n.part ? -1.0 : 1.0};
+  }
+  return {C.spec.as<float2>() + (size_t)(P->dch.size() + c) * P->Nk, 1.0};
+}
+
+// ---------------------------------------------------------------------------------
+// measure
+// ---------------------------------------------------------------------------------
+struct PassState {
+  std::map<std::pair<int, int>, cplx> sbar;  // (L, M>=0) -> Sbar_L^M
+  // Z[(l, m, L, M)] per bin
+  std::map<std::tuple<int, int, int, int>, std::vector<cplx>> Z;
+};
+
+void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstride, const float* gbase,
+              std::vector<double>& out, int* launches) {
+  // build a pair job with nout = mults.size() * gsets outputs
+  PairJob J{};
+  J.fields = P->pool.as<float>();
+  J.gfields = gbase;
+  J.Ng = P->Ng;
+  J.nb = P->nb;
+  J.ncomp = (int)P->comps.size();
+  J.ng = gsets * gstride;
+  J.nout = (int)mults.size() * gsets;
+  int t = 0, r = 0;
+  for (int gs = 0; gs < gsets; ++gs)
+    for (size_t i = 0; i < mults.size(); ++i) {
+      const int o = gs * (int)mults.size() + (int)i;
+      J.out_term_off[o] = t;
+      for (auto& term : P->terms[mults[i]]) {
+        if (t >= 64 || r + (int)(term.x.size() + term.y.size()) > 512) fail(BISP_EUNSUPPORTED, "too many pair terms");
+        J.term[t].xoff = r;
+        J.term[t].xcnt = (int)term.x.size();
+        for (auto e : term.x) {
+          if (e.g >= 0) e.g += gs * gstride;
+          J.rec[r++] = e;
+        }
+        J.term[t].yoff = r;
+        J.term[t].ycnt = (int)term.y.size();
+        for (auto e : term.y) {
+          if (e.g >= 0) e.g += gs * gstride;
+          J.rec[r++] = e;
+        }
+        ++t;
+      }
+    }
+  J.out_term_off[J.nout] = t;
+  J.nterm = t;
+  J.nrec = r;
+  const size_t sb = pair_scratch_bytes(J);
+  admit(P, sb > P->pairscr.n ? sb - P->pairscr.n : 0);
+  P->pairscr.ensure(sb, &P->bytes);
+  const size_t ob = (size_t)J.nout * P->nb * P->nb * 8;
+  P->pairout.ensure(ob, &P->bytes);
+  cudaEvent_t e0, e1;
+  BISP_CUDA(cudaEventCreate(&e0));
+  BISP_CUDA(cudaEventCreate(&e1));
+  BISP_CUDA(cudaEventRecord(e0, P->stream));
+  pair_reduce(J, P->pairout.as<double>(), P->pairscr.p, P->pairscr.n, P->stream, launches);
+  BISP_CUDA(cudaEventRecord(e1, P->stream));
+  out.resize((size_t)J.nout * P->nb * P->nb);
+  BISP_CUDA(cudaMemcpyAsync(out.data(), P->pairout.p, ob, cudaMemcpyDeviceToHost, P->stream));
+  BISP_CUDA(cudaStreamSynchronize(P->stream));
+  float ms = 0.f;
+  BISP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->ms_pair += ms;
+  P->pair_launches += 1;
+  P->pair_bytes += (double)(J.nb * J.ncomp + J.ng) * (double)P->Ng * 4.0;
+}
+
+// inverse-transform a batch of fields (shared prune extent)
+void run_inverse(bisp_plan* P, InvBatch& b, int* launches) {
+  b.N = P->N;
+  b.ynorm = P->ynorm.as<float>();
+  b.cw2_1d = P->cw2.as<float>();
+  b.interlace = P->interlace;
+  const size_t need = inverse_scratch_bytes(P->N, b.P, b.nf);
+  if (need > P->invscr.n) {
+    admit(P, need - P->invscr.n);
+    P->invscr.ensure(need, &P->bytes);
+  }
+  inverse_fft(b, P->tw.as<float2>(), P->invscr.p, P->stream, launches);
+}
+
+void shell_fields(bisp_plan* P, const float2* D00, bool unit, int* launches) {
+  const int nc = (int)P->comps.size();
+  for (int b = 0; b < P->nb; ++b) {
+    InvBatch B{};
+    B.P = P->Pb[b];
+    B.nf = nc;
+    B.qlo = P->qlo[b];
+    B.qhi = P->qhi[b];
+    B.inv_nmodes = P->nmodes[b] > 0 ? (float)(1.0 / P->nmodes[b]) : 0.f;
+    for (int c = 0; c < nc; ++c) {
+      InvField& f = B.f[c];
+      f.kind = SRC_SHELL;
+      f.A = D00;
+      f.l = P->comps[c].l;
+      f.m = P->comps[c].m;
+      f.part = P->comps[c].part;
+      f.unit = unit ? 1 : 0;
+      f.scale = 1.f;
+      f.out = P->pool.as<float>() + ((size_t)b * nc + c) * P->Ng;
+    }
+    run_inverse(P, B, launches);
+  }
+}
+
+void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, double* outWS, double* outNm) {
+  Catalog& G = P->cat[BISP_DATA];
+  Catalog& R = P->cat[BISP_RANDOMS];
+  if (!G.assigned) fail(BISP_ESTATE, "measure before the data catalogue was assigned");
+  const bool local = P->los == BISP_LOS_LOCAL;
+  if ((local || P->want_window) && !R.assigned) fail(BISP_ESTATE, "this plan needs the random catalogue");
+  if (P->want_window && (outW || outWS) && !R.assigned) fail(BISP_ESTATE, "window needs randoms");
+  cudaStream_t s = P->stream;
+  int launches = 0;
+  P->ms_pair = 0.0;
+  P->pair_launches = 0;
+  P->pair_bytes = 0.0;
+  BISP_CUDA(cudaEventRecord(P->ev0, s));
+  const int nD = (int)P->dch.size(), nN = (int)P->nch.size();
+  const int64_t Ng = P->Ng, Nk = P->Nk;
+  const bool have_r = R.assigned;
+  const double alpha = have_r ? G.sumw / R.sumw : 0.0;
+  P->alpha = alpha;
+  // normalisation I (Eq. normalization): alpha^3 sum R^3 / H^6, or Np^3 / V^2 for a box
+  if (have_r) P->normI = alpha * alpha * alpha * R.sumR3 / std::pow(P->H, 6);
+  else P->normI = G.sumw * G.sumw * G.sumw / (P->V * P->V);
+  const int npass = (P->want_window && have_r) ? 2 : 1;
+  const int nb = P->nb, nmult = P->nmult;
+  // memory admission for the measurement buffers
+  {
+    size_t need = 0;
+    auto add = [&](DBuf& d, size_t b) { need += b > d.n ? b - d.n : 0; };
+    for (int k = 0; k < npass; ++k) {
+      add(P->pass_spec[k], (size_t)(nD + nN) * Nk * 8);
+      add(P->gf[k], (size_t)nD * Ng * 4);
+    }
+    add(P->qf, (size_t)npass * nD * Ng * 4);
+    add(P->pool, (size_t)nb * P->comps.size() * Ng * 4);
+    admit(P, need);
+  }
+  PassState ps[2];
+  for (int k = 0; k < npass; ++k) {
+    const bool win = k == 1;
+    P->pass_spec[k].ensure((size_t)(nD + nN) * Nk * 8, &P->bytes);
+    float2* Dp = P->pass_spec[k].as<float2>();
+    float2* Np = Dp + (size_t)nD * Nk;
+    const float2* Dg = G.spec.as<float2>();
+    const float2* Dr = have_r ? R.spec.as<float2>() : nullptr;
+    for (int c = 0; c < nD; ++c) {
+      if (!win) {
+        if (have_r)
+          launch_axpby(Dp + c * Nk, Dg + c * Nk, 1.0, Dr + c * Nk, -alpha, Nk, 1, s);
+        else
+          launch_axpby(Dp + c * Nk, Dg + c * Nk, 1.0, nullptr, 0.0, Nk, 1, s);
+      } else {
+        launch_axpby(Dp + c * Nk, Dr + c * Nk, alpha, nullptr, 0.0, Nk, 0, s);
+      }
+      ++launches;
+    }
+    for (int c = 0; c < nN; ++c) {
+      auto ng = nspec_of(P, G, c);
+      if (!win) {
+        if (have_r) {
+          auto nr = nspec_of(P, R, c);
+          launch_axpby(Np + c * Nk, ng.first, ng.second, nr.first, alpha * alpha * nr.second, Nk, 0, s);
+        } else {
+          launch_axpby(Np + c * Nk, ng.first, ng.second, nullptr, 0.0, Nk, 0, s);
+        }
+      } else {
+        auto nr = nspec_of(P, R, c);
+        launch_axpby(Np + c * Nk, nr.first, alpha * alpha * nr.second, nullptr, 0.0, Nk, 0, s);
+      }
+      ++launches;
+    }
+    // Sbar_L^M per (L, M >= 0)
+    for (int L : P->Ls)
+      for (int M = 0; M <= L; ++M) {
+        if (!local && (L > 0 || M > 0)) continue;
+        const int cr = P->dchan(L, M, 0), ci = M ? P->dchan(L, M, 1) : -1;
+        auto sb = [&](const Catalog& C) {
+          return cplx{C.sbar[cr], ci >= 0 ? C.sbar[ci] : 0.0};
+        };
+        cplx v;
+        if (!win) {
+          v = sb(G);
+          if (have_r) {
+            const cplx r = sb(R);
+            v.r -= alpha * alpha * alpha * r.r;
+            v.i -= alpha * alpha * alpha * r.i;
+          }
+        } else {
+          const cplx r = sb(R);
+          v = {alpha * alpha * alpha * r.r, alpha * alpha * alpha * r.i};
+        }
+        ps[k].sbar[{L, M}] = v;
+      }
+    // G fields: c2r of each delta n channel
+    P->gf[k].ensure((size_t)nD * Ng * 4, &P->bytes);
+    P->qf.ensure((size_t)npass * nD * Ng * 4, &P->bytes);
+    {
+      InvBatch B{};
+      B.P = P->N / 2 - 1;
+      B.nf = nD;
+      for (int c = 0; c < nD; ++c) {
+        B.f[c].kind = SRC_PLAIN;
+        B.f[c].A = Dp + c * Nk;
+        B.f[c].scale = 1.f;
+        B.f[c].out = P->gf[k].as<float>() + (size_t)c * Ng;
+      }
+      run_inverse(P, B, &launches);
+      // q fields: c2r of D_c conj(N_00) - Sbar_part C/W^2
+      InvBatch Q{};
+      Q.P = P->N / 2 - 1;
+      Q.nf = nD;
+      for (int c = 0; c < nD; ++c) {
+        const Chan& ch = P->dch[c];
+        const cplx sbv = ps[k].sbar.at({local ? ch.L : 0, local ? ch.M : 0});
+        Q.f[c].kind = SRC_QSHOT;
+        Q.f[c].A = Dp + c * Nk;
+        Q.f[c].B = Np + (size_t)P->n00 * Nk;
+        Q.f[c].sbar = (float)(ch.part ? sbv.i : sbv.r);
+        Q.f[c].scale = 1.f;
+        Q.f[c].out = P->qf.as<float>() + ((size_t)k * nD + c) * Ng;
+      }
+      run_inverse(P, Q, &launches);
+    }
+    // shell sums Z(b; l, m, L, M) for M >= 0 (FP64)
+    {
+      std::vector<std::pair<int, int>> lm;
+      for (int l : P->ls)
+        for (int m = -l; m <= l; ++m) lm.push_back({l, m});
+      const int nblk = 64;
+      for (int L : P->Ls)
+        for (int M = 0; M <= L; ++M) {
+          if (!local && (L > 0 || M > 0)) continue;
+          const cplx sbv = ps[k].sbar.at({L, M});
+          for (size_t g0 = 0; g0 < lm.size(); g0 += 9) {
+            const int cnt = (int)std::min<size_t>(9, lm.size() - g0);
+            ZsumArgs z{};
+            z.D00 = Dp + (size_t)P->d00 * Nk;
+            const int cr = P->nchan(L, M, 0), ci = M ? P->nchan(L, M, 1) : -1;
+            z.NR = Np + (size_t)cr * Nk;
+            z.NI = ci >= 0 ? Np + (size_t)ci * Nk : nullptr;
+            z.sbar_re = sbv.r;
+            z.sbar_im = sbv.i;
+            z.N = P->N;
+            z.nbins = nb;
+            z.qlo = P->qlo_d.as<long long>();
+            z.qhi = P->qhi_d.as<long long>();
+            z.cw2_1d = P->cw2.as<float>();
+            z.interlace = P->interlace;
+            z.nlm = cnt;
+            for (int t = 0; t < cnt; ++t) {
+              z.lm[t][0] = lm[g0 + t].first;
+              z.lm[t][1] = lm[g0 + t].second;
+            }
+            z.ynorm = P->ynorm.as<float>();
+            z.nblk = nblk;
+            const size_t zb = (size_t)nb * nblk * cnt * 2 * 8;
+            P->zpart.ensure(zb, &P->bytes);
+            z.partials = P->zpart.as<double>();
+            launch_zsum(z, s);
+            ++launches;
+            std::vector<double> hz((size_t)nb * nblk * cnt * 2);
+            BISP_CUDA(cudaMemcpyAsync(hz.data(), P->zpart.p, zb, cudaMemcpyDeviceToHost, s));
+            BISP_CUDA(cudaStreamSynchronize(s));
+            for (int t = 0; t < cnt; ++t) {
+              std::vector<cplx> zz(nb);
+              for (int b = 0; b < nb; ++b) {
+                double re = 0, im = 0;
+                for (int q = 0; q < nblk; ++q) {
+                  re += hz[(((size_t)b * nblk + q) * cnt + t) * 2];
+                  im += hz[(((size_t)b * nblk + q) * cnt + t) * 2 + 1];
+                }
+                if (P->nmodes[b] > 0) zz[b] = {re / P->nmodes[b], im / P->nmodes[b]};
+              }
+              ps[k].Z[{lm[g0 + t].first, lm[g0 + t].second, L, M}] = zz;
+            }
+          }
+        }
+    }
+  }
+  // pair reductions
+  P->pool.ensure((size_t)nb * P->comps.size() * Ng * 4, &P->bytes);
+  std::vector<int> all(nmult);
+  for (int i = 0; i < nmult; ++i) all[i] = i;
+  std::vector<double> cU, cD, cW;
+  // i = j != k shot term: unit shells, q fields of every pass
+  shell_fields(P, nullptr, true, &launches);
+  run_pair(P, all, npass, nD, P->qf.as<float>(), cU, &launches);
+  // data
+  shell_fields(P, P->pass_spec[0].as<float2>() + (size_t)P->d00 * Nk, false, &launches);
+  run_pair(P, all, 1, nD, P->gf[0].as<float>(), cD, &launches);
+  if (npass == 2) {
+    shell_fields(P, P->pass_spec[1].as<float2>() + (size_t)P->d00 * Nk, false, &launches);
+    run_pair(P, all, 1, nD, P->gf[1].as<float>(), cW, &launches);
+  }
+  BISP_CUDA(cudaEventRecord(P->ev1, s));
+  BISP_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  BISP_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+  P->ms_measure = ms;
+  P->launches_measure = launches;
+  // host FP64: normalisation, 3j-contracted shell terms, subtraction
+  const double Ngd = (double)Ng;
+  for (int k = 0; k < npass; ++k) {
+    const std::vector<double>& raw = k == 0 ? cD : cW;
+    double* oB = k == 0 ? outB : outW;
+    double* oS = k == 0 ? outShot : outWS;
+    for (int mu = 0; mu < nmult; ++mu) {
+      const int l1 = P->ells[mu][0], l2 = P->ells[mu][1], L = P->ells[mu][2];
+      const double pref = (double)((2 * l1 + 1) * (2 * l2 + 1) * (2 * L + 1)) * wigner3j(l1, l2, L, 0, 0, 0) / P->normI;
+      for (int b1 = 0; b1 < nb; ++b1)
+        for (int b2 = 0; b2 < nb; ++b2) {
+          cplx sh;
+          for (int m1 = -l1; m1 <= l1; ++m1)
+            for (int m2 = -l2; m2 <= l2; ++m2) {
+              const int M = -m1 - m2;
+              if (std::abs(M) > L || (!local && M != 0)) continue;
+              const double w = wigner3j(l1, l2, L, m1, m2, M);
+              if (w == 0.0) continue;
+              const int Lz = local ? L : 0;
+              const cplx Y1 = P->Y[b1][P->lm_index(l1, m1)], Y2 = P->Y[b2][P->lm_index(l2, m2)];
+              // Sbar_L^M and Z for signed M via Z(l,m,L,-M) = (-1)^{m+M+l} conj Z(l,-m,L,M)
+              auto sbar_at = [&](int MM) {
+                const cplx v = ps[k].sbar.at({Lz, std::abs(MM)});
+                if (MM >= 0) return v;
+                const double sg = (std::abs(MM) & 1) ? -1.0 : 1.0;
+                return cplx{sg * v.r, -sg * v.i};
+              };
+              auto z_at = [&](int l, int m, int MM, int b) {
+                if (MM >= 0) return ps[k].Z.at({l, m, Lz, MM})[b];
+                const cplx v = ps[k].Z.at({l, -m, Lz, -MM})[b];
+                const double sg = ((m + MM + l) & 1) ? -1.0 : 1.0;
+                return cplx{sg * v.r, -sg * v.i};
+              };
+              const cplx S = sbar_at(M);
+              const cplx Z1 = z_at(l1, m1, M, b1), Z2 = z_at(l2, m2, M, b2);
+              const cplx iii = cm(S, cm(Y1, Y2));
+              const cplx ijj = cm(Z1, Y2);
+              const cplx iji = cm(Y1, Z2);
+              sh.r += w * (iii.r + ijj.r + iji.r);
+            }
+          const size_t o = ((size_t)mu * nb + b1) * nb + b2;
+          const double iij = cU[(size_t)(k * nmult + mu) * nb * nb + b1 * nb + b2] / Ngd;
+          const double shot = pref * (sh.r + iij);
+          const double braw = pref * raw[(size_t)mu * nb * nb + b1 * nb + b2] / Ngd;
+          if (oB) oB[o] = braw - shot;
+          if (oS) oS[o] = shot;
+        }
+    }
+  }
+  if (outNm)
+    for (int b = 0; b < nb; ++b) outNm[b] = P->nmodes[b];
+}
+
+void destroy(bisp_plan* P) {
+  if (!P) return;
+  size_t* t = &P->bytes;
+  for (auto* d : {&P->tw, &P->winv, &P->ynorm, &P->cw2, &P->qlo_d, &P->qhi_d, &P->pool, &P->invscr, &P->pairscr,
+                  &P->pairout, &P->zpart})
+    d->release(t);
+  for (int k = 0; k < 2; ++k) {
+    P->cat[k].spec.release(t);
+    P->cat[k].dbg_mesh.release(t);
+    P->pass_spec[k].release(t);
+    P->gf[k].release(t);
+  }
+  P->qf.release(t);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
+  delete P;
+}
+
+template <class F>
+bisp_status guarded(F&& f) {
+  try {
+    f();
+    return BISP_OK;
+  } catch (const Fail& e) {
+    g_err = e.msg;
+    return (bisp_status)e.status;
+  } catch (const Error& e) {
+    g_err = e.msg;
+    return (bisp_status)e.status;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return BISP_EINVAL;
+  }
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+bisp_status bisp_plan_create(bisp_plan** out, const bisp_params* p, void* stream) {
+  if (!out) {
+    g_err = "out is NULL";
+    return BISP_EINVAL;
+  }
+  *out = nullptr;
+  bisp_plan* P = new bisp_plan();
+  bisp_status st = guarded([&] {
+    validate(p);
+    P->N = p->nmesh;
+    P->NH = P->N / 2;
+    P->L = p->box_len;
+    P->H = P->L / P->N;
+    P->kF = 2.0 * M_PI / P->L;
+    P->V = P->L * P->L * P->L;
+    P->Ng = (int64_t)P->N * P->N * P->N;
+    P->Nk = (int64_t)P->N * P->N * (P->N / 2);
+    P->nb = p->nbins;
+    P->edges.assign(p->k_edges, p->k_edges + p->nbins + 1);
+    P->nmult = p->n_mult;
+    for (int i = 0; i < p->n_mult; ++i) P->ells.push_back({p->ells[3 * i], p->ells[3 * i + 1], p->ells[3 * i + 2]});
+    P->los = p->los;
+    for (int k = 0; k < 3; ++k) P->obs[k] = p->observer[k];
+    P->mas = p->mas;
+    P->interlace = p->interlace ? 1 : 0;
+    P->P0 = p->fkp_P0;
+    P->max_bytes = p->max_device_bytes;
+    P->want_window = p->want_window ? 1 : 0;
+    const char* dbg = std::getenv("BISP_DEBUG");
+    P->debug_mesh = dbg && std::strstr(dbg, "BISP_DEBUG_KEEP_MESH");
+    int dev = 0;
+    BISP_CUDA(cudaGetDevice(&dev));
+    if (stream) {
+      P->stream = (cudaStream_t)stream;
+    } else {
+      BISP_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+      P->own_stream = true;
+    }
+    BISP_CUDA(cudaEventCreate(&P->ev0));
+    BISP_CUDA(cudaEventCreate(&P->ev1));
+    build_channels(P);
+    build_shells(P);
+    build_recipes(P);
+    upload_tables(P);
+  });
+  if (st != BISP_OK) {
+    destroy(P);
+    return st;
+  }
+  *out = P;
+  return BISP_OK;
+}
+
+bisp_status bisp_assign(bisp_plan* plan, int which, const float* xyz, const float* w, const float* nbar, int64_t n,
+                        int ptr_is_device) {
+  if (!plan) {
+    g_err = "plan is NULL";
+    return BISP_EINVAL;
+  }
+  return guarded([&] { do_assign(plan, which, xyz, w, nbar, n, ptr_is_device); });
+}
+
+bisp_status bisp_measure(bisp_plan* plan, double* B, double* shot, double* window, double* window_shot,
+                         double* nmodes) {
+  if (!plan) {
+    g_err = "plan is NULL";
+    return BISP_EINVAL;
+  }
+  return guarded([&] { do_measure(plan, B, shot, window, window_shot, nmodes); });
+}
+
+bisp_status bisp_plan_destroy(bisp_plan* plan) {
+  destroy(plan);
+  return BISP_OK;
+}
+
+const char* bisp_last_error(void) { return g_err.c_str(); }
+
+bisp_status bisp_plan_query(const bisp_plan* P, bisp_plan_info* info) {
+  if (!P || !info) {
+    g_err = "NULL argument";
+    return BISP_EINVAL;
+  }
+  std::memset(info, 0, sizeof(*info));
+  info->nmesh = P->N;
+  info->nbins = P->nb;
+  info->n_mult = P->nmult;
+  info->n_dchan = (int)P->dch.size();
+  info->n_nchan = (int)P->nch.size();
+  info->n_fcomp = (int)P->comps.size();
+  info->alpha = P->alpha;
+  info->norm_I = P->normI;
+  info->n_data = P->cat[0].n;
+  info->n_randoms = P->cat[1].n;
+  info->device_bytes = P->bytes;
+  info->kernel_launches = P->cat[0].launches + P->cat[1].launches + P->launches_measure;
+  info->ms_assign_data = P->cat[0].ms;
+  info->ms_assign_randoms = P->cat[1].ms;
+  info->ms_measure = P->ms_measure;
+  info->ms_pair = P->ms_pair;
+  info->pair_bytes = P->pair_bytes;
+  info->pair_launches = P->pair_launches;
+  return BISP_OK;
+}
+
+bisp_status bisp_cell_order(int nmesh, double box_len, int mas, const float* xyz, int64_t n, uint32_t* keys_out,
+                            uint32_t* order_out, void* stream) {
+  return guarded([&] {
+    if (nmesh < 16 || nmesh > BISP_NMAX || (nmesh & (nmesh - 1))) fail(BISP_EINVAL, "nmesh");
+    if (!(box_len > 0)) fail(BISP_EINVAL, "box_len");
+    if (mas < 1 || mas > 3) fail(BISP_EINVAL, "mas");
+    if (n < 0 || (n > 0 && (!xyz || !keys_out || !order_out))) fail(BISP_EINVAL, "bad pointers or size");
+    if (n == 0) return;
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t tb = 0;
+    DBuf keys, idx, frac, part, bad, scr;
+    keys.ensure(n * 4, &tb);
+    idx.ensure(n * 4, &tb);
+    frac.ensure(n * 16, &tb);
+    part.ensure((size_t)prep_blocks(n) * 8, &tb);
+    bad.ensure(64, &tb);
+    BISP_CUDA(cudaMemsetAsync(bad.p, 0, 64, s));
+    PrepArgs a{};
+    a.xyz = xyz;
+    a.n = n;
+    a.N = nmesh;
+    a.H = box_len / nmesh;
+    a.box = box_len;
+    a.mas = mas;
+    a.nchan = 0;
+    a.keys = keys.as<uint32_t>();
+    a.idx = idx.as<uint32_t>();
+    a.frac = frac.as<float4>();
+    a.vals = nullptr;
+    a.partials = part.as<double>();
+    a.nsum = 1;
+    a.bad = bad.as<int>();
+    std::vector<float> yn((BISP_LMAX + 1) * (BISP_LMAX + 1), 1.f);
+    DBuf ynd;
+    ynd.ensure(yn.size() * 4, &tb);
+    BISP_CUDA(cudaMemcpyAsync(ynd.p, yn.data(), yn.size() * 4, cudaMemcpyHostToDevice, s));
+    a.ynorm = ynd.as<float>();
+    launch_prep(a, s);
+    int nbad = 0;
+    BISP_CUDA(cudaMemcpyAsync(&nbad, bad.p, 4, cudaMemcpyDeviceToHost, s));
+    BISP_CUDA(cudaStreamSynchronize(s));
+    if (nbad) fail(BISP_EINVAL, std::to_string(nbad) + " particles have non-finite or out-of-box positions");
+    int bits = 0;
+    while ((1LL << bits) < (int64_t)nmesh * nmesh * nmesh) ++bits;
+    scr.ensure(radix_sort_scratch_bytes(n), &tb);
+    radix_sort(keys.as<uint32_t>(), idx.as<uint32_t>(), keys_out, order_out, n, bits, scr.p, s, nullptr);
+    BISP_CUDA(cudaStreamSynchronize(s));
+    for (DBuf* d : {&keys, &idx, &frac, &part, &bad, &scr, &ynd}) d->release(&tb);
+  });
+}
+
+bisp_status bisp_debug_fetch(const bisp_plan* P, int what, int which, int index, void* host_out, size_t bytes) {
+  return guarded([&] {
+    if (!P || !host_out) fail(BISP_EINVAL, "NULL argument");
+    if (which != 0 && which != 1) fail(BISP_EINVAL, "which");
+    const Catalog& C = P->cat[which];
+    if (!C.assigned) fail(BISP_ESTATE, "catalogue not assigned");
+    if (index < 0 || index >= C.nspec) fail(BISP_EINVAL, "channel index");
+    if (what == BISP_DBG_SPECTRUM) {
+      const size_t b = (size_t)P->Nk * 8;
+      if (bytes != b) fail(BISP_EINVAL, "bytes");
+      BISP_CUDA(cudaMemcpy(host_out, C.spec.as<float2>() + (size_t)index * P->Nk, b, cudaMemcpyDeviceToHost));
+    } else if (what == BISP_DBG_MESH) {
+      if (!C.dbg_mesh.p) fail(BISP_ESTATE, "mesh not kept (set BISP_DEBUG=BISP_DEBUG_KEEP_MESH)");
+      const size_t b = (size_t)P->Ng * 4;
+      if (bytes != b) fail(BISP_EINVAL, "bytes");
+      BISP_CUDA(cudaMemcpy(host_out, C.dbg_mesh.as<float>() + (size_t)index * P->Ng, b, cudaMemcpyDeviceToHost));
+    } else {
+      fail(BISP_EINVAL, "what");
+    }
+  });
+}
+
+}  // extern "C"

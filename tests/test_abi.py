@@ -1,0 +1,51 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function that
+include/bisp.h declares (no GPU needed: nothing here calls into CUDA)."""
+import os
+import re
+
+import pytest
+
+import paper_1803_02132_gb300 as bisp
+
+
+def test_library_exports_every_header_function():
+    names = bisp.header_functions()
+    assert {"bisp_plan_create", "bisp_assign", "bisp_measure", "bisp_plan_destroy", "bisp_last_error"} <= set(names)
+    lib = bisp.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_header_is_plain_c():
+    txt = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "bisp.h")).read()
+    assert 'extern "C"' in txt
+    assert "torch" not in txt and "at::" not in txt
+    # every declared function is documented by a comment block just above it
+    for m in re.finditer(r"^(?:bisp_status|const char\*)\s+(bisp_\w+)\s*\(", txt, re.M):
+        before = txt[: m.start()].rstrip().splitlines()[-1]
+        assert before.strip().endswith("*/") or before.strip().startswith("enum") or "}" in before, m.group(1)
+
+
+def test_plan_create_rejects_bad_params_without_touching_the_gpu():
+    # validation happens before any CUDA call: these fail with BISP_EINVAL even without a GPU
+    with pytest.raises(bisp.BispError) as e:
+        bisp.Plan(nmesh=48, box_len=1000.0, k_edges=[0.01, 0.02], ells=[(0, 0, 0)])
+    assert e.value.status == bisp.BISP_EINVAL
+    with pytest.raises(bisp.BispError) as e:
+        bisp.Plan(nmesh=64, box_len=1000.0, k_edges=[0.02, 0.01], ells=[(0, 0, 0)])
+    assert e.value.status == bisp.BISP_EINVAL
+    with pytest.raises(bisp.BispError) as e:
+        bisp.Plan(nmesh=64, box_len=1000.0, k_edges=[0.01, 0.02], ells=[(2, 1, 2)])
+    assert e.value.status == bisp.BISP_EINVAL and "selection rules" in str(e.value)
+    with pytest.raises(bisp.BispError) as e:
+        bisp.Plan(nmesh=64, box_len=-1.0, k_edges=[0.01, 0.02], ells=[(0, 0, 0)])
+    assert e.value.status == bisp.BISP_EINVAL
+
+
+def test_oracle_is_not_imported_by_the_product():
+    src_dir = os.path.dirname(bisp.__file__)
+    for root, _, files in os.walk(src_dir):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(root, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f

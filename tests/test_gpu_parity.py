@@ -1,0 +1,176 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1803_02132_gb300 as bisp  # noqa: E402
+import synthcat  # noqa: E402
+from oracle import estimator as E  # noqa: E402
+
+# the benchmark spec tolerance: per multipole, max relative error <= 1e-4 over bins with
+# |B| > 1% of the multipole's maximum |B|
+TOL = 1e-4
+
+
+def rel_err(gpu, ref):
+    """max relative error over bins above 1% of the multipole's max |ref|, per multipole."""
+    out = []
+    for g, r in zip(gpu, ref):
+        m = np.abs(r) > 0.01 * np.abs(r).max()
+        out.append(float(np.max(np.abs(g[m] - r[m]) / np.abs(r[m]))) if m.any() else 0.0)
+    return out
+
+
+def assert_close(gpu, ref, tol=TOL, what=""):
+    errs = rel_err(gpu, ref)
+    assert max(errs) <= tol, f"{what}: max rel err per multipole {errs}"
+
+
+def _plan(p, **kw):
+    return bisp.Plan(nmesh=p.N, box_len=p.L, k_edges=p.edges, ells=p.ells, los=p.los, observer=p.observer,
+                     mas=p.mas, interlace=p.interlace, fkp_P0=p.P0, want_window=p.window, **kw)
+
+
+def _assign(plan, which, cat, device=True):
+    xyz = cat["xyz"]
+    w = cat.get("w")
+    nb = cat.get("nbar")
+    if device:
+        t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+        plan.assign(which, t(xyz), t(w), t(nb))
+    else:
+        plan.assign(which, xyz, w, nb)
+
+
+# ----------------------------------------------------------------------------------
+def test_cell_order_bit_exact():
+    N, L = 64, 1000.0
+    rng = np.random.default_rng(11)
+    xyz = (rng.random((100_000, 3)) * L).astype(np.float32)
+    xyz[:2000] = np.round(xyz[:2000] / (L / N)) * np.float32(L / N)  # on nodes
+    xyz[2000:4000] = (np.floor(xyz[2000:4000] / (L / N)) + 0.5) * np.float32(L / N)  # half-cell ties
+    xyz = np.mod(xyz, np.float32(L)).astype(np.float32)
+    xyz[xyz >= L] = 0
+    xyz[4000:6000] = xyz[6000:8000]  # duplicate positions: stability
+    xd = torch.from_numpy(xyz).cuda()
+    for mas in (1, 2, 3):
+        keys, order = bisp.cell_order(N, L, mas, xd)
+        ok = E.cell_keys(xyz, N, L, mas)
+        oo = np.argsort(ok, kind="stable")
+        assert np.array_equal(order.cpu().numpy().astype(np.int64), oo)
+        assert np.array_equal(keys.cpu().numpy().astype(np.int64), ok[oo])
+
+
+def test_cell_order_empty_and_ragged():
+    for n in (0, 1, 4095, 4097):
+        xyz = (np.random.default_rng(n).random((n, 3)) * 100.0).astype(np.float32)
+        if n == 0:
+            continue
+        keys, order = bisp.cell_order(16, 100.0, 3, torch.from_numpy(xyz).cuda())
+        ok = E.cell_keys(xyz, 16, 100.0, 3)
+        assert np.array_equal(order.cpu().numpy(), np.argsort(ok, kind="stable"))
+
+
+@pytest.mark.parametrize("mas,interlace", [(1, False), (2, False), (3, True)])
+def test_mesh_and_spectrum_parity(mas, interlace, monkeypatch):
+    monkeypatch.setenv("BISP_DEBUG", "BISP_DEBUG_KEEP_MESH")
+    N, L = 32, 500.0
+    rng = np.random.default_rng(3)
+    xyz = (rng.random((20_000, 3)) * L).astype(np.float32)
+    w = (0.5 + rng.random(20_000)).astype(np.float32)
+    p = E.Params(N=N, L=L, edges=[0.02, 0.05], ells=[(0, 0, 0)], mas=mas, interlace=interlace)
+    with _plan(p) as plan:
+        _assign(plan, 0, {"xyz": xyz, "w": w})
+        mesh = plan.fetch_mesh(0, 0)
+        ref = E.assign(xyz, w.astype(np.float64), N, L, mas, 0.0)
+        assert np.max(np.abs(mesh - ref)) <= 2e-6 * np.max(np.abs(ref))
+        spec = plan.fetch_spectrum(0, 0)
+        refk = E.spectrum(p, xyz, w.astype(np.float64))[:, :, : N // 2]
+        assert np.max(np.abs(spec - refk)) <= 1e-5 * np.max(np.abs(refk))
+
+
+def _survey(seed, N, L, ngal, nran, P0=1e4):
+    obs = (0.5 * L, 0.5 * L, -0.3 * L)
+    gal, ran = synthcat.survey_catalogs(N, L, obs, ngal, nran, seed, r_min=0.35 * L, r_max=1.25 * L,
+                                        half_angle_deg=40.0, r_mean=0.8 * L, sigma=0.2 * L)
+    return gal, ran, obs
+
+
+CASES = {
+    "box_cic": dict(N=32, L=1000.0, mas=2, interlace=False, los="global", np_=30_000,
+                    ells=[(0, 0, 0), (2, 0, 2), (1, 1, 0), (2, 2, 2)]),
+    "box_tsc_ilv": dict(N=32, L=1000.0, mas=3, interlace=True, los="global", np_=30_000,
+                        ells=[(0, 0, 0), (1, 1, 0), (2, 2, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2)]),
+    "survey_local": dict(N=32, L=2000.0, mas=3, interlace=True, los="local", np_=20_000,
+                         ells=[(0, 0, 0), (2, 0, 2), (1, 1, 2)]),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_estimator_parity_small(case):
+    c = CASES[case]
+    N, L = c["N"], c["L"]
+    kf = 2 * np.pi / L
+    edges = kf * np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5, 11.0, 15.5])  # 7 bins, last one ragged
+    if c["los"] == "global":
+        gal = {"xyz": synthcat.periodic_catalog(N, L, c["np_"], seed=100 + N)}
+        ran = None
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="global", mas=c["mas"], interlace=c["interlace"])
+    else:
+        gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="local", observer=obs, mas=c["mas"],
+                     interlace=c["interlace"], P0=1e4, window=True)
+    ref = E.measure(p, gal, ran)
+    with _plan(p) as plan:
+        _assign(plan, 0, gal)
+        if ran is not None:
+            _assign(plan, 1, ran)
+        out = plan.measure()
+        out2 = plan.measure()
+        info = plan.info()
+    assert info["norm_I"] == pytest.approx(ref["I"], rel=1e-6)
+    assert np.array_equal(out["nmodes"], ref["nmodes"])
+    assert_close(out["B"], ref["B"], what="B")
+    assert_close(out["shot"], ref["shot"], what="shot")
+    assert np.array_equal(out["B"], out2["B"])  # bitwise reproducible
+    if ran is not None:
+        assert_close(out["window"], ref["window"], what="window")
+        assert_close(out["window_shot"], ref["window_shot"], what="window shot")
+
+
+def test_cfg1_box_64_cic_fp():
+    # 1000 Mpc/h box, 64^3, 2e5 particles, CIC, no interlacing, global LOS, B000 and B202 on
+    # 10 bins with edges 0.01..0.21 h/Mpc
+    N, L = 64, 1000.0
+    gal = {"xyz": synthcat.periodic_catalog(N, L, 200_000, seed=1000)}
+    edges = np.linspace(0.01, 0.21, 11)
+    p = E.Params(N=N, L=L, edges=edges, ells=[(0, 0, 0), (2, 0, 2)], los="global", mas=2, interlace=False)
+    ref = E.measure(p, gal, None)
+    with _plan(p) as plan:
+        _assign(plan, 0, gal, device=False)   # host pointers through the C ABI
+        out = plan.measure()
+    assert_close(out["B"], ref["B"], what="B")
+    assert_close(out["shot"], ref["shot"], what="shot")
+
+
+def test_errors_are_reported():
+    p = E.Params(N=16, L=100.0, edges=[0.1, 0.3], ells=[(0, 0, 0)], los="local", mas=3)
+    with _plan(p) as plan:
+        with pytest.raises(bisp.BispError) as e:
+            plan.measure()
+        assert e.value.status == bisp.BISP_ESTATE
+        bad = np.array([[1.0, 2.0, 3.0], [np.nan, 1.0, 1.0], [150.0, 1.0, 1.0]], np.float32)
+        with pytest.raises(bisp.BispError) as e:
+            plan.assign(0, bad)
+        assert e.value.status == bisp.BISP_EINVAL and "2 particles" in str(e.value)
+        plan.assign(0, np.array([[1.0, 2.0, 3.0]], np.float32))
+        with pytest.raises(bisp.BispError) as e:  # local LOS needs randoms
+            plan.measure()
+        assert e.value.status == bisp.BISP_ESTATE
