@@ -1,0 +1,301 @@
+"""Benchmark: bispectrum multipoles B_{l1 l2 L}(k1, k2) per second.
+
+Default workload (the 512^3 configuration the metric is quoted on): a survey-like
+catalogue with a local line of sight - 3000 Mpc/h box, 512^3 mesh, observer at
+(1500, 1500, -300) Mpc/h, 1e6 galaxies in a 1000-1700 Mpc/h shell inside a 60x60 degree
+cap with a Gaussian n(r) (mean 1350, sigma 200 Mpc/h), 5e7 randoms with the same n(r),
+FKP weights with P0 = 1e4, TSC with interlacing; B000, B202 and B112 on 25 bins of width
+0.01 h/Mpc from 0.01 h/Mpc, plus the window bispectrum from the randoms.  A step is one
+pass of the whole path: assign galaxies, assign randoms, measure (data, shot noise,
+window).  Inputs are synthetic (synthcat, seeded) and far larger than L2.
+
+`--impl reference` times the FP64 oracle (the CPU reference of this project) on a
+bounded sample on the host cores.  For N > 1 (torchrun) every rank measures its own
+independent realisation (replicas; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "survey512": dict(kind="survey", N=512, L=3000.0, n_gen=256, observer=(1500.0, 1500.0, -300.0),
+                      n_gal=1_000_000, n_ran=50_000_000, edges=list(np.round(np.linspace(0.01, 0.26, 26), 6)),
+                      ells=[(0, 0, 0), (2, 0, 2), (1, 1, 2)], mas="TSC", interlace=True, P0=1e4, window=True),
+    "box256": dict(kind="box", N=256, L=1000.0, n_gen=256, n_p=4_000_000,
+                   edges=list(np.round(np.linspace(0.01, 0.21, 21), 6)),
+                   ells=[(0, 0, 0), (1, 1, 0), (2, 2, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2)], mas="TSC",
+                   interlace=True, P0=0.0, window=False),
+    "box128": dict(kind="box", N=128, L=1000.0, n_gen=128, n_p=500_000,
+                   edges=list(np.round(np.linspace(0.01, 0.21, 21), 6)),
+                   ells=[(0, 0, 0), (1, 1, 0), (2, 2, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2)], mas="TSC",
+                   interlace=True, P0=0.0, window=False),
+    "box64": dict(kind="box", N=64, L=1000.0, n_gen=64, n_p=200_000, edges=list(np.round(np.linspace(0.01, 0.21, 11), 6)),
+                  ells=[(0, 0, 0), (2, 0, 2)], mas="CIC", interlace=False, P0=0.0, window=False),
+}
+
+
+def n_bins_output(w):
+    """Distinct outputs: k1 <= k2 when l1 = l2, all pairs otherwise; twice with the window."""
+    nb = len(w["edges"]) - 1
+    n = sum(nb * (nb + 1) // 2 if l1 == l2 else nb * nb for (l1, l2, _) in w["ells"])
+    return n * (2 if w["window"] else 1)
+
+
+def make_inputs(w, seed):
+    import synthcat
+
+    if w["kind"] == "survey":
+        gal, ran = synthcat.survey_catalogs(w["n_gen"], w["L"], w["observer"], w["n_gal"], w["n_ran"], seed)
+        return gal, ran
+    return {"xyz": synthcat.periodic_catalog(w["n_gen"], w["L"], w["n_p"], seed)}, None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 7]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0])]
+        mx = [num(r[1]) for r in rows if num(r[1])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu(args, w, rank, world):
+    import torch
+
+    import paper_1803_02132_gb300 as bisp
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+    gal, ran = make_inputs(w, seed=1002 + rank)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    g_dev = {k: t(v) for k, v in gal.items()}
+    r_dev = {k: t(v) for k, v in ran.items()} if ran is not None else None
+    stream = torch.cuda.Stream()
+    plan = bisp.Plan(w["N"], w["L"], w["edges"], w["ells"], los="local" if w["kind"] == "survey" else "global",
+                     observer=w.get("observer", (0, 0, 0)), mas=w["mas"], interlace=w["interlace"],
+                     fkp_P0=w["P0"], want_window=w["window"], stream=stream)
+
+    def step(dev_inputs=True):
+        if dev_inputs:
+            plan.assign(bisp.DATA, g_dev["xyz"], None, g_dev.get("nbar"))
+            if r_dev is not None:
+                plan.assign(bisp.RANDOMS, r_dev["xyz"], None, r_dev.get("nbar"))
+        else:
+            plan.assign(bisp.DATA, gal["xyz"], None, gal.get("nbar"))
+            if ran is not None:
+                plan.assign(bisp.RANDOMS, ran["xyz"], None, ran.get("nbar"))
+        return plan.measure()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ms_pair = []
+    pair_launches = 0
+    pair_bytes = 0.0
+    launches = 0
+    for _ in range(args.steps):
+        step()
+        inf = plan.info()
+        ms_pair.append(inf["ms_pair"])
+        pair_launches += inf["pair_launches"]
+        pair_bytes += inf["pair_bytes"]
+        launches += inf["kernel_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    # end to end through the public API with host buffers (H2D and D2H inside)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(dev_inputs=False)
+    torch.cuda.synchronize()
+    ms_e2e = (time.perf_counter() - t0) * 1e3
+    if dist:
+        tt = torch.tensor([ms, ms_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = tt.tolist()
+    info = plan.info()
+    plan.close()
+    nbins = n_bins_output(w)
+    ms_step = ms / args.steps
+    value = world * nbins / (ms_step / 1e3)
+    h2d = sum(v.nbytes for v in gal.values()) + (sum(v.nbytes for v in ran.values()) if ran else 0)
+    d2h = (4 if w["window"] else 2) * len(w["ells"]) * (len(w["edges"]) - 1) ** 2 * 8 + (len(w["edges"]) - 1) * 8
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    pair_ms_avg = sum(ms_pair) / max(pair_launches, 1)
+    pair_gbs = (pair_bytes / max(pair_launches, 1)) / (pair_ms_avg / 1e3) / 1e9 if pair_ms_avg > 0 else None
+    out = {
+        "metric": "B_l1l2L(k1,k2) bins/s at 512^3 (local LOS, B000+B202+B112 + window)"
+        if w["N"] == 512 else f"B_l1l2L(k1,k2) bins/s at {w['N']}^3",
+        "value": value, "unit": "bins/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64 accumulation)", "data": "synthetic",
+        "config": {"workload": args.workload, "nmesh": w["N"], "box_len": w["L"], "nbins": len(w["edges"]) - 1,
+                   "ells": w["ells"], "n_gal": w.get("n_gal", w.get("n_p")), "n_ran": w.get("n_ran", 0),
+                   "bins_per_step": nbins, "los": "local" if w["kind"] == "survey" else "global",
+                   "mas": w["mas"], "interlace": w["interlace"], "window": w["window"],
+                   "l2": "inputs larger than L2 (meshes and fields of 0.5 GB each)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": world * nbins / (ms_e2e / args.steps / 1e3), "unit": "bins/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": "k_pair (mesh sum of F F G)", "achieved": pair_gbs,
+                     "peak": hbm, "unit": "GB/s", "frac": (pair_gbs / hbm) if pair_gbs else None,
+                     "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+                     else "fallback 6800 GB/s"},
+        "stages_ms": {"assign_data": info["ms_assign_data"], "assign_randoms": info["ms_assign_randoms"],
+                      "measure": info["ms_measure"], "pair": info["ms_pair"]},
+        "clocks": clk,
+    }
+    return out
+
+
+def cpu_baseline(args, w):
+    """The FP64 oracle on a bounded sample of the workload, timed on the host cores."""
+    from oracle import estimator as E
+
+    import synthcat
+
+    # sample: the same recipe scaled down to a 64^3 mesh in the same box (1/512 of the cells,
+    # particles in proportion), on the bins below that mesh's Nyquist frequency
+    N = 64
+    L = w["L"]
+    kN = np.pi * N / L
+    edges = [e for e in w["edges"] if e < 0.9 * kN]
+    if len(edges) < 3:
+        edges = list(np.linspace(w["edges"][0], 0.9 * kN, 4))
+    frac = (N / w["N"]) ** 3
+    if w["kind"] == "survey":
+        gal, ran = synthcat.survey_catalogs(N, L, w["observer"], int(w["n_gal"] * frac), int(w["n_ran"] * frac), 7)
+        p = E.Params(N=N, L=L, edges=edges, ells=w["ells"], los="local", observer=w["observer"],
+                     mas={"NGP": 1, "CIC": 2, "TSC": 3}[w["mas"]], interlace=w["interlace"], P0=w["P0"],
+                     window=w["window"])
+    else:
+        gal, ran = {"xyz": synthcat.periodic_catalog(N, L, int(w["n_p"] * frac), 7)}, None
+        p = E.Params(N=N, L=L, edges=edges, ells=w["ells"], los="global",
+                     mas={"NGP": 1, "CIC": 2, "TSC": 3}[w["mas"]], interlace=w["interlace"])
+    t0 = time.perf_counter()
+    E.measure(p, gal, ran)
+    dt = time.perf_counter() - t0
+    nb = len(edges) - 1
+    nbins = sum(nb * (nb + 1) // 2 if l1 == l2 else nb * nb for (l1, l2, _) in w["ells"]) * (2 if w["window"] else 1)
+    cores = 1
+    try:
+        import threadpoolctl
+        cores = max(1, max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1)
+    except Exception:
+        pass
+    return {"value": nbins / dt, "unit": "bins/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle on the same recipe at {N}^3 (1/{int(round(1 / frac))} of the cells and particles), "
+                      f"{nb} bins below that mesh's Nyquist, {nbins} bins in {dt:.1f} s",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="survey512", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        vals = []
+        for i in range(args.warmup + args.steps):
+            cb = cpu_baseline(args, w)
+            if i >= args.warmup:
+                vals.append(cb)
+        v = float(np.mean([c["value"] for c in vals]))
+        cb = dict(vals[-1])
+        cb["value"] = v
+        print(json.dumps({"impl": "reference", "metric": "B_l1l2L(k1,k2) bins/s (FP64 CPU oracle, bounded sample)",
+                          "value": v, "unit": "bins/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "config": {"workload": args.workload}, "cpu_baseline": cb,
+                          "e2e": {"value": v, "unit": "bins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                          "seconds": time.perf_counter() - t0}))
+        return
+    out = run_gpu(args, w, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args, w)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

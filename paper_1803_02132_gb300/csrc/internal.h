@@ -139,7 +139,11 @@ struct ZsumArgs {
 void launch_zsum(const ZsumArgs& a, cudaStream_t s);
 
 struct PairRecipe { int comp, g; float coef; };
-struct PairTermDesc { int xoff, xcnt, yoff, ycnt; };
+struct PairTermDesc {
+  int xoff, xcnt, yoff, ycnt;  // recipe entries of the two sides
+  int xdir, ydir;              // side is a bare component field (index), or -1
+  int xslot, yslot;            // shared-memory slot of a side built per chunk, or -1
+};
 struct PairJob {
   const float* fields;    // component field (b, c) at fields + (b*ncomp + c) * Ng
   const float* gfields;   // g field i at gfields + i * Ng
@@ -148,7 +152,16 @@ struct PairJob {
   int nout;               // outputs (multipole x G-set)
   int out_term_off[33];   // terms of output o: [off[o], off[o+1])
   int nterm;
+  int nslot;              // sides built per chunk
+  int term_out[64];       // output of each term
   PairTermDesc term[64];
+  // built sides: side s = sum over its entries (c, h) of P_c(b, x) H_h(x), where
+  // H_h(x) = sum over its entries (g, coef) of coef G_g(x) (g < 0: the constant coef)
+  int nh;
+  int h_off[129];         // entries of H row h: [h_off[h], h_off[h+1]) in h_ent
+  PairRecipe h_ent[512];  // (comp unused, g, coef)
+  int s_off[65];          // entries of side s: [s_off[s], s_off[s+1]) in s_ent
+  int s_ent[512][2];      // (c, h)
   int nrec;
   PairRecipe rec[512];
 };

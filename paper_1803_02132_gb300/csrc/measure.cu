@@ -8,6 +8,8 @@
 //    small combination of filtered fields and G fields prepared per x chunk in shared
 //    memory.  FP32 products in 4x4 register tiles, FP32 partials over at most 1024
 //    cells, FP64 above that; per-CTA partials are reduced in a fixed order.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -158,179 +160,342 @@ void launch_zsum(const ZsumArgs& a, cudaStream_t s) {
 
 // ------------------------------------------------------------------------------------
 // pair reduction
+//   out[o][b1][b2] = sum_x sum_{t in o} X_t(x; b1) Y_t(x; b2)
+// Each CTA streams chunks of PR_CH cells.  All component fields and G fields of a chunk
+// are copied to shared memory with 16-byte cp.async, PR_NSTAGE chunks in flight.  Sides
+// that are combinations of fields are built in shared memory; bare component sides are
+// read in place.  One warp owns one (term, x slice): its 32 lanes form a 4 x 8 grid and
+// each lane holds a TM x TN register tile of (b1, b2), so the warp covers 4TM x 8TN bins.
+// FP32 partials over at most PR_FLUSH chunks are added to lane-owned FP64 slots in global
+// memory; a second kernel reduces the slots in a fixed order.
 // ------------------------------------------------------------------------------------
 __constant__ PairJob c_pj;
-constexpr int PR_THREADS = 256;
 constexpr int PR_CH = 32;          // cells per chunk
 constexpr int PR_LD = PR_CH + 4;   // padded row (bank spread for 16-byte loads)
 constexpr int PR_FLUSH = 32;       // chunks per FP32 partial (<= 1024 cells)
-constexpr int PR_IPT = 2;          // work items per thread
+constexpr int PR_NSTAGE = 3;       // chunks staged ahead
+constexpr int PR_MAXWARP = 16;
 
 struct PairLaunch {
-  int nbp;      // nb rounded up to 4
-  int ntile;    // nbp / 4
-  int units;    // nout * ntile^2
-  int ksplit;   // x slices per chunk
-  int items;    // units * ksplit (<= PR_IPT * PR_THREADS)
-  int nblk;
+  int TM, TN, nbp, ksplit, warps, nblk, rows;
   size_t smem;
 };
 
+static void pick_tile(int nb, int* TM, int* TN) {
+  static const int tab[][2] = {{1, 1}, {2, 1}, {3, 2}, {4, 2}, {5, 3}, {6, 3}, {7, 4}, {8, 4}, {10, 5}};
+  for (auto& t : tab)
+    if (4 * t[0] >= nb && 8 * t[1] >= nb) {
+      *TM = t[0];
+      *TN = t[1];
+      return;
+    }
+  throw Error{6, "pair reduction: more than 40 bins"};
+}
+
 static PairLaunch pair_launch_cfg(const PairJob& j) {
   PairLaunch c;
-  c.nbp = (j.nb + 3) / 4 * 4;
-  c.ntile = c.nbp / 4;
-  c.units = j.nout * c.ntile * c.ntile;
+  pick_tile(j.nb, &c.TM, &c.TN);
+  c.nbp = std::max(4 * c.TM, 8 * c.TN);
+  if (j.nterm > 2 * PR_MAXWARP || (j.nterm > PR_MAXWARP && c.TM * c.TN > 18))
+    throw Error{6, "pair reduction: too many terms for one CTA"};
   c.ksplit = 1;
-  while (c.ksplit < 8 && c.units * c.ksplit * 2 <= PR_IPT * PR_THREADS) c.ksplit *= 2;
-  c.items = c.units * c.ksplit;
-  if (c.items > PR_IPT * PR_THREADS) throw Error{6, "pair reduction: too many outputs for one CTA"};
-  c.nblk = 2 * 152;
-  c.smem = ((size_t)2 * j.nterm * c.nbp * PR_LD + (size_t)(j.nb * j.ncomp + j.ng) * PR_CH) * sizeof(float);
+  while (c.ksplit < 8 && j.nterm * c.ksplit * 2 <= PR_MAXWARP) c.ksplit *= 2;
+  c.warps = j.nterm * c.ksplit;
+  c.rows = c.nbp * j.ncomp + j.ng;
+  c.smem = ((size_t)PR_NSTAGE * c.rows * PR_LD + (size_t)j.nslot * c.nbp * PR_LD + (size_t)j.nh * PR_CH) *
+           sizeof(float);
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  c.nblk = nsm;
   return c;
 }
 
-size_t pair_scratch_bytes(const PairJob& j) {
-  const PairLaunch c = pair_launch_cfg(j);
-  return (size_t)c.nblk * c.items * 16 * sizeof(double);
+// classify the sides of every term: bare component field (read in place) or built
+static PairJob classify(const PairJob& job) {
+  PairJob j = job;
+  j.nslot = 0;
+  for (int t = 0; t < j.nterm; ++t) {
+    PairTermDesc& T = j.term[t];
+    auto bare = [&](int off, int cnt) {
+      return cnt == 1 && j.rec[off].g < 0 && j.rec[off].coef == 1.0f ? j.rec[off].comp : -1;
+    };
+    T.xdir = bare(T.xoff, T.xcnt);
+    T.ydir = bare(T.yoff, T.ycnt);
+    T.xslot = T.xdir >= 0 ? -1 : j.nslot++;
+    T.yslot = T.ydir >= 0 ? -1 : j.nslot++;
+    int o = 0;
+    while (o + 1 <= j.nout && j.out_term_off[o + 1] <= t) ++o;
+    j.term_out[t] = o;
+  }
+  // factor every built side by component: H rows shared between sides when identical
+  std::vector<std::vector<std::pair<int, float>>> rows;
+  j.nh = 0;
+  int ns = 0, nse = 0;
+  for (int t = 0; t < j.nterm; ++t)
+    for (int side = 0; side < 2; ++side) {
+      const PairTermDesc& T = j.term[t];
+      const int slot = side ? T.yslot : T.xslot;
+      if (slot < 0) continue;
+      if (slot != ns) throw Error{6, "pair reduction: slot order"};
+      j.s_off[ns] = nse;
+      const int off = side ? T.yoff : T.xoff, cnt = side ? T.ycnt : T.xcnt;
+      std::vector<int> comps;
+      for (int e = 0; e < cnt; ++e)
+        if (std::find(comps.begin(), comps.end(), j.rec[off + e].comp) == comps.end()) comps.push_back(j.rec[off + e].comp);
+      for (int c : comps) {
+        std::vector<std::pair<int, float>> row;
+        for (int e = 0; e < cnt; ++e)
+          if (j.rec[off + e].comp == c) row.push_back({j.rec[off + e].g, j.rec[off + e].coef});
+        int h = -1;
+        for (size_t r = 0; r < rows.size(); ++r)
+          if (rows[r] == row) h = (int)r;
+        if (h < 0) {
+          h = (int)rows.size();
+          rows.push_back(row);
+        }
+        if (nse >= 512) throw Error{6, "pair reduction: too many side entries"};
+        j.s_ent[nse][0] = c;
+        j.s_ent[nse][1] = h;
+        ++nse;
+      }
+      ++ns;
+    }
+  j.s_off[ns] = nse;
+  if (rows.size() > 128) throw Error{6, "pair reduction: too many H rows"};
+  int ne = 0;
+  for (size_t r = 0; r < rows.size(); ++r) {
+    j.h_off[r] = ne;
+    for (auto& e : rows[r]) {
+      if (ne >= 512) throw Error{6, "pair reduction: too many H entries"};
+      j.h_ent[ne++] = {0, e.first, e.second};
+    }
+  }
+  j.nh = (int)rows.size();
+  j.h_off[j.nh] = ne;
+  return j;
 }
 
-__global__ void __launch_bounds__(PR_THREADS) k_pair(int nbp, int ntile, int ksplit, int items, double* partials) {
+size_t pair_scratch_bytes(const PairJob& job) {
+  const PairLaunch c = pair_launch_cfg(classify(job));
+  return (size_t)c.nblk * c.warps * 32 * c.TM * c.TN * sizeof(double);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int NW>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW)); }
+
+// copy one chunk of every component row [b][comp] and G row into shared memory
+__device__ __forceinline__ void pair_stage(float* raw, int64_t x0, int nbp) {
   const PairJob& J = c_pj;
-  extern __shared__ float sh[];
-  float* Xs = sh;                                  // [nterm][nbp][PR_LD]
-  float* Ys = sh + (size_t)J.nterm * nbp * PR_LD;  // [nterm][nbp][PR_LD]
-  float* raw = Ys + (size_t)J.nterm * nbp * PR_LD; // [nb*ncomp + ng][PR_CH]
+  constexpr int Q = PR_CH / 4;
   const int nraw = J.nb * J.ncomp;
-  const int64_t nchunk = J.Ng / PR_CH;
-  // zero padded rows once
-  for (int i = threadIdx.x; i < 2 * J.nterm * nbp * PR_LD; i += blockDim.x) sh[i] = 0.f;
-  __syncthreads();
-  // work items of this thread
-  int it_o[PR_IPT], it_b1[PR_IPT], it_b2[PR_IPT], it_x0[PR_IPT];
-  bool it_ok[PR_IPT];
-  const int slice = PR_CH / ksplit;
-#pragma unroll
-  for (int k = 0; k < PR_IPT; ++k) {
-    const int w = threadIdx.x + k * PR_THREADS;
-    it_ok[k] = w < items;
-    const int u = w / ksplit, ks = w % ksplit;
-    const int o = u / (ntile * ntile), r = u % (ntile * ntile);
-    it_o[k] = it_ok[k] ? o : 0;
-    it_b1[k] = 4 * (r / ntile);
-    it_b2[k] = 4 * (r % ntile);
-    it_x0[k] = ks * slice;
+  const int n = (nraw + J.ng) * Q;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int f = i / Q, q = i % Q;
+    const float* src;
+    int row;
+    if (f < nraw) {
+      src = J.fields + (size_t)f * J.Ng + x0 + 4 * q;
+      row = f;
+    } else {
+      src = J.gfields + (size_t)(f - nraw) * J.Ng + x0 + 4 * q;
+      row = nbp * J.ncomp + (f - nraw);
+    }
+    cp_async16(raw + (size_t)row * PR_LD + 4 * q, src);
   }
-  float acc[PR_IPT][16];
-  double acc64[PR_IPT][16];
+}
+
+template <int TM, int TN, int NTHR>
+__global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int rows, int ksplit, double* partials) {
+  const PairJob& J = c_pj;
+  extern __shared__ __align__(16) float sh[];
+  float* mat = sh + (size_t)PR_NSTAGE * rows * PR_LD;  // [nslot][nbp][PR_LD]
+  const int grow0 = nbp * J.ncomp;
+  const int64_t nchunk = J.Ng / PR_CH;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int t = warp / ksplit, ks = warp % ksplit;
+  const int slice = PR_CH / ksplit;
+  const int b1 = (lane >> 3) * TM, b2 = (lane & 7) * TN;
+  const PairTermDesc T = J.term[t];
+  double* slot = partials + (((size_t)blockIdx.x * nwarp + warp) * 32 + lane) * (TM * TN);
 #pragma unroll
-  for (int k = 0; k < PR_IPT; ++k)
+  for (int q = 0; q < TM * TN; ++q) slot[q] = 0.0;
+  float acc[TM][TN];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[k][q] = 0.f, acc64[k][q] = 0.0;
-  int since_flush = 0;
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  // prologue: the first PR_NSTAGE - 1 chunks
+  int64_t chs[PR_NSTAGE];
+#pragma unroll
+  for (int s = 0; s < PR_NSTAGE - 1; ++s) {
+    chs[s] = blockIdx.x + (int64_t)s * gridDim.x;
+    if (chs[s] < nchunk) pair_stage(sh + (size_t)s * rows * PR_LD, chs[s] * PR_CH, nbp);
+    cp_async_commit();
+  }
+  int since_flush = 0, stage = 0;
   for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-    const int64_t x0 = ch * PR_CH;
-    __syncthreads();
-    // stage the chunk of every field component and G field (one coalesced read each)
-    for (int i = threadIdx.x; i < (nraw + J.ng) * PR_CH; i += blockDim.x) {
-      const int f = i / PR_CH, x = i % PR_CH;
-      raw[i] = f < nraw ? __ldg(J.fields + (size_t)f * J.Ng + x0 + x)
-                        : __ldg(J.gfields + (size_t)(f - nraw) * J.Ng + x0 + x);
+    cp_async_wait<PR_NSTAGE - 2>();
+    __syncthreads();  // chunk ch has landed; every warp is done with the previous chunk
+    {
+      const int64_t nx = ch + (int64_t)(PR_NSTAGE - 1) * gridDim.x;
+      const int ns = (stage + PR_NSTAGE - 1) % PR_NSTAGE;
+      if (nx < nchunk) pair_stage(sh + (size_t)ns * rows * PR_LD, nx * PR_CH, nbp);
+      cp_async_commit();
     }
-    __syncthreads();
-    // build the two sides of every term for this chunk
-    const int per_side = J.nb * PR_CH;
-    for (int i = threadIdx.x; i < 2 * J.nterm * per_side; i += blockDim.x) {
-      const int x = i % PR_CH;
-      const int b = (i / PR_CH) % J.nb;
-      const int ts = i / per_side;  // term * 2 + side
-      const int t = ts >> 1, side = ts & 1;
-      const PairTermDesc& T = J.term[t];
-      const int off = side ? T.yoff : T.xoff, cnt = side ? T.ycnt : T.xcnt;
-      float v = 0.f;
-      for (int e = 0; e < cnt; ++e) {
-        const PairRecipe R = J.rec[off + e];
-        float f = raw[(b * J.ncomp + R.comp) * PR_CH + x];
-        if (R.g >= 0) f *= raw[(nraw + R.g) * PR_CH + x];
-        v = fmaf(R.coef, f, v);
-      }
-      (side ? Ys : Xs)[((size_t)t * nbp + b) * PR_LD + x] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < PR_IPT; ++k) {
-      if (!it_ok[k]) continue;
-      const int o = it_o[k];
-      for (int t = J.out_term_off[o]; t < J.out_term_off[o + 1]; ++t) {
-        const float* xr = Xs + ((size_t)t * nbp + it_b1[k]) * PR_LD + it_x0[k];
-        const float* yr = Ys + ((size_t)t * nbp + it_b2[k]) * PR_LD + it_x0[k];
-        for (int x = 0; x < slice; x += 4) {
-          float4 a[4], c[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            a[i] = *reinterpret_cast<const float4*>(xr + i * PR_LD + x);
-            c[i] = *reinterpret_cast<const float4*>(yr + i * PR_LD + x);
+    const float* raw = sh + (size_t)stage * rows * PR_LD;
+    // built sides: H_h(x) = sum coef G_g(x) (shared by all bins), then
+    // mat[slot][b][x] = sum_(c,h) P_c(b, x) H_h(x); four cells per thread
+    if (J.nslot) {
+      float* Hs = mat + (size_t)J.nslot * nbp * PR_LD;  // [nh][PR_CH]
+      constexpr int Q = PR_CH / 4;
+      for (int i = threadIdx.x; i < J.nh * Q; i += blockDim.x) {
+        const int h = i / Q, q = i % Q;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = J.h_off[h]; e < J.h_off[h + 1]; ++e) {
+          const PairRecipe R = J.h_ent[e];
+          if (R.g >= 0) {
+            const float4 gv = *reinterpret_cast<const float4*>(raw + (size_t)(grow0 + R.g) * PR_LD + 4 * q);
+            v.x = fmaf(R.coef, gv.x, v.x);
+            v.y = fmaf(R.coef, gv.y, v.y);
+            v.z = fmaf(R.coef, gv.z, v.z);
+            v.w = fmaf(R.coef, gv.w, v.w);
+          } else {
+            v.x += R.coef;
+            v.y += R.coef;
+            v.z += R.coef;
+            v.w += R.coef;
           }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              float s = acc[k][i * 4 + j];
-              s = fmaf(a[i].x, c[j].x, s);
-              s = fmaf(a[i].y, c[j].y, s);
-              s = fmaf(a[i].z, c[j].z, s);
-              s = fmaf(a[i].w, c[j].w, s);
-              acc[k][i * 4 + j] = s;
-            }
+        }
+        *reinterpret_cast<float4*>(Hs + (size_t)h * PR_CH + 4 * q) = v;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < J.nb * Q; i += blockDim.x) {
+        const int b = i / Q, q = i % Q;
+        const float* rb = raw + (size_t)b * J.ncomp * PR_LD + 4 * q;
+        for (int sl = 0; sl < J.nslot; ++sl) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int e = J.s_off[sl]; e < J.s_off[sl + 1]; ++e) {
+            const int c = J.s_ent[e][0], h = J.s_ent[e][1];
+            const float4 pv = *reinterpret_cast<const float4*>(rb + (size_t)c * PR_LD);
+            const float4 hv = *reinterpret_cast<const float4*>(Hs + (size_t)h * PR_CH + 4 * q);
+            v.x = fmaf(pv.x, hv.x, v.x);
+            v.y = fmaf(pv.y, hv.y, v.y);
+            v.z = fmaf(pv.z, hv.z, v.z);
+            v.w = fmaf(pv.w, hv.w, v.w);
+          }
+          *reinterpret_cast<float4*>(mat + ((size_t)sl * nbp + b) * PR_LD + 4 * q) = v;
         }
       }
+      __syncthreads();
     }
-    if (++since_flush == PR_FLUSH) {
+    const float* xr;
+    const float* yr;
+    int sx, sy;
+    if (T.xdir >= 0) {
+      xr = raw + (size_t)(b1 * J.ncomp + T.xdir) * PR_LD;
+      sx = J.ncomp * PR_LD;
+    } else {
+      xr = mat + ((size_t)T.xslot * nbp + b1) * PR_LD;
+      sx = PR_LD;
+    }
+    if (T.ydir >= 0) {
+      yr = raw + (size_t)(b2 * J.ncomp + T.ydir) * PR_LD;
+      sy = J.ncomp * PR_LD;
+    } else {
+      yr = mat + ((size_t)T.yslot * nbp + b2) * PR_LD;
+      sy = PR_LD;
+    }
+    xr += ks * slice;
+    yr += ks * slice;
+    for (int x = 0; x < slice; x += 4) {
+      float4 a[TM], c[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = *reinterpret_cast<const float4*>(xr + i * sx + x);
+#pragma unroll
+      for (int j = 0; j < TN; ++j) c[j] = *reinterpret_cast<const float4*>(yr + j * sy + x);
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          float s = acc[i][j];
+          s = fmaf(a[i].x, c[j].x, s);
+          s = fmaf(a[i].y, c[j].y, s);
+          s = fmaf(a[i].z, c[j].z, s);
+          s = fmaf(a[i].w, c[j].w, s);
+          acc[i][j] = s;
+        }
+    }
+    if (++since_flush == PR_FLUSH || ch + gridDim.x >= nchunk) {
       since_flush = 0;
 #pragma unroll
-      for (int k = 0; k < PR_IPT; ++k)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int q = 0; q < 16; ++q) acc64[k][q] += (double)acc[k][q], acc[k][q] = 0.f;
+        for (int j = 0; j < TN; ++j) {
+          slot[i * TN + j] += (double)acc[i][j];
+          acc[i][j] = 0.f;
+        }
     }
+    stage = (stage + 1) % PR_NSTAGE;
   }
-#pragma unroll
-  for (int k = 0; k < PR_IPT; ++k) {
-    const int w = threadIdx.x + k * PR_THREADS;
-    if (w >= items) continue;
-#pragma unroll
-    for (int q = 0; q < 16; ++q)
-      partials[((size_t)blockIdx.x * items + w) * 16 + q] = acc64[k][q] + (double)acc[k][q];
-  }
+  cp_async_wait<0>();
 }
 
-// out[o][b1][b2] = sum over CTAs (in order) and k slices (in order)
-__global__ void k_pair_final(const double* partials, int nblk, int items, int ksplit, int ntile, int nb, int nout,
-                             double* out) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nout * nb * nb) return;
-  const int o = idx / (nb * nb), b1 = (idx / nb) % nb, b2 = idx % nb;
-  const int u = (o * ntile + b1 / 4) * ntile + b2 / 4;
-  const int q = (b1 % 4) * 4 + (b2 % 4);
+// out[o][b1][b2] = sum over terms of o, then CTAs and x slices in a fixed order; one warp
+// per output value, lanes stride over CTAs, fixed shuffle tree.
+__global__ void k_pair_final(const double* partials, int nblk, int warps, int ksplit, int TM, int TN, int nb,
+                             int nout, double* out) {
+  const PairJob& J = c_pj;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= nout * nb * nb) return;
+  const int o = gw / (nb * nb), b1 = (gw / nb) % nb, b2 = gw % nb;
+  const int ln = (b1 / TM) * 8 + b2 / TN, q = (b1 % TM) * TN + (b2 % TN);
   double s = 0.0;
-  for (int c = 0; c < nblk; ++c)
-    for (int ks = 0; ks < ksplit; ++ks) s += partials[((size_t)c * items + u * ksplit + ks) * 16 + q];
-  out[idx] = s;
+  for (int t = J.out_term_off[o]; t < J.out_term_off[o + 1]; ++t)
+    for (int ks = 0; ks < ksplit; ++ks) {
+      const int w = t * ksplit + ks;
+      for (int c = lane; c < nblk; c += 32) s += partials[(((size_t)c * warps + w) * 32 + ln) * (TM * TN) + q];
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) out[gw] = s;
 }
 
 void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scratch_bytes, cudaStream_t s,
                  int* launches) {
-  const PairLaunch c = pair_launch_cfg(job);
-  if (scratch_bytes < pair_scratch_bytes(job)) throw Error{2, "pair reduction scratch too small"};
-  if (job.Ng % PR_CH) throw Error{6, "mesh size not a multiple of the chunk"};
-  BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &job, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
-  if (c.smem > 48 * 1024)
-    BISP_CUDA(cudaFuncSetAttribute(k_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+  const PairJob j = classify(job);
+  const PairLaunch c = pair_launch_cfg(j);
+  if (scratch_bytes < pair_scratch_bytes(j)) throw Error{2, "pair reduction scratch too small"};
+  if (j.Ng % PR_CH) throw Error{6, "mesh size not a multiple of the chunk"};
+  if (c.smem > 227 * 1024) throw Error{6, "pair reduction: shared memory budget exceeded"};
+  BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &j, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
   double* partials = reinterpret_cast<double*>(scratch);
-  k_pair<<<c.nblk, PR_THREADS, c.smem, s>>>(c.nbp, c.ntile, c.ksplit, c.items, partials);
+#define BISP_PAIR3(A, B, NT)                                                                              \
+  if (c.TM == A && c.TN == B && c.warps * 32 <= NT) {                                                   \
+    BISP_CUDA(cudaFuncSetAttribute(k_pair<A, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem)); \
+    k_pair<A, B, NT><<<c.nblk, c.warps * 32, c.smem, s>>>(c.nbp, c.rows, c.ksplit, partials);           \
+    launched = true;                                                                                     \
+  }
+#define BISP_PAIR(A, B) \
+  if (!launched) BISP_PAIR3(A, B, 512) if (!launched) BISP_PAIR3(A, B, 1024)
+#define BISP_PAIR_S(A, B) \
+  if (!launched) BISP_PAIR3(A, B, 512)
+  bool launched = false;
+  BISP_PAIR(1, 1) BISP_PAIR(2, 1) BISP_PAIR(3, 2) BISP_PAIR(4, 2) BISP_PAIR(5, 3) BISP_PAIR(6, 3)
+  BISP_PAIR_S(7, 4) BISP_PAIR_S(8, 4) BISP_PAIR_S(10, 5)
+#undef BISP_PAIR
+#undef BISP_PAIR_S
+#undef BISP_PAIR3
+  if (!launched) throw Error{6, "pair reduction: no kernel for this shape"};
   BISP_CHECK_LAUNCH();
-  const int nout = job.nout * job.nb * job.nb;
-  k_pair_final<<<(nout + 255) / 256, 256, 0, s>>>(partials, c.nblk, c.items, c.ksplit, c.ntile, job.nb, job.nout,
-                                                  out_dev);
+  const int nout = j.nout * j.nb * j.nb;
+  k_pair_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(partials, c.nblk, c.warps, c.ksplit, c.TM, c.TN, j.nb,
+                                                       j.nout, out_dev);
   BISP_CHECK_LAUNCH();
   if (launches) *launches += 2;
 }
