@@ -32,6 +32,10 @@ WORKLOADS = {
     "survey512": dict(kind="survey", N=512, L=3000.0, n_gen=256, observer=(1500.0, 1500.0, -300.0),
                       n_gal=1_000_000, n_ran=50_000_000, edges=list(np.round(np.linspace(0.01, 0.26, 26), 6)),
                       ells=[(0, 0, 0), (2, 0, 2), (1, 1, 2)], mas="TSC", interlace=True, P0=1e4, window=True),
+    "survey128": dict(kind="survey", N=128, L=3000.0, n_gen=128, observer=(1500.0, 1500.0, -300.0),
+                      n_gal=1_000_000 // 64, n_ran=50_000_000 // 64,
+                      edges=list(np.round(np.linspace(0.005, 0.13, 26), 6)),
+                      ells=[(0, 0, 0), (2, 0, 2), (1, 1, 2)], mas="TSC", interlace=True, P0=1e4, window=True),
     "box256": dict(kind="box", N=256, L=1000.0, n_gen=256, n_p=4_000_000,
                    edges=list(np.round(np.linspace(0.01, 0.21, 21), 6)),
                    ells=[(0, 0, 0), (1, 1, 0), (2, 2, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2)], mas="TSC",

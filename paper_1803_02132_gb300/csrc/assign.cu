@@ -358,47 +358,57 @@ __device__ __forceinline__ float wker(float t) {
   return 0.f;
 }
 
-constexpr int DEP_CG = 4;  // channels per deposit pass
-
-// One thread per mesh node c.  It visits the home nodes h = c + o, o in [OLO, OHI]^3 (z
-// innermost), and every particle of each home node in sorted order, so the sum order is
-// fixed.  Node positions: mesh 0 at c H, mesh 1 (interlaced) at (c + 1/2) H.
-template <int P, int ILV>
+// One thread per mesh node c (z fastest).  It visits the home nodes h = c + o,
+// o in [OLO, OHI]^3, as contiguous z runs of the sorted particle array (the run of keys
+// (hx, hy, cz+OLO) .. (hx, hy, cz+OHI)), in a fixed order, so the sums are bit-reproducible.
+// Node positions: mesh 0 at c H, mesh 1 (interlaced) at (c + 1/2) H.  All channels are
+// accumulated in one pass (NC >= nchan registers per mesh).
+template <int P, int ILV, int NC>
 __global__ void __launch_bounds__(256) k_deposit(const uint32_t* __restrict__ cell_start,
+                                                 const uint32_t* __restrict__ keys,
                                                  const float4* __restrict__ frac, const float* __restrict__ vals,
                                                  int64_t n, int N, int nchan, float* mesh0, float* mesh1) {
-  // home-node offsets o = h - c that can reach node c
-  constexpr int OLO = (P == 2) ? -1 : (P == 1 ? 0 : -1);
-  constexpr int OHI = ILV ? (P == 2 ? 1 : (P == 1 ? 1 : 2)) : (P == 2 ? 0 : (P == 1 ? 0 : 1));
+  constexpr int OLO = (P == 1) ? 0 : -1;
+  constexpr int OHI = ILV ? (P == 3 ? 2 : 1) : (P == 3 ? 1 : 0);
   const int64_t Ng = (int64_t)N * N * N;
   const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= Ng) return;
-  const int c0 = blockIdx.y * DEP_CG;
-  const int nc = min(DEP_CG, nchan - c0);
   const int cz = (int)(cell % N), cy = (int)((cell / N) % N), cx = (int)(cell / ((int64_t)N * N));
-  float a0[DEP_CG], a1[DEP_CG];
+  float a0[NC], a1[NC];
 #pragma unroll
-  for (int k = 0; k < DEP_CG; ++k) a0[k] = a1[k] = 0.f;
+  for (int k = 0; k < NC; ++k) a0[k] = a1[k] = 0.f;
+  const bool wrap = cz + OLO < 0 || cz + OHI > N - 1;
   for (int ox = OLO; ox <= OHI; ++ox) {
     const int hx = (cx + ox) & (N - 1);
     for (int oy = OLO; oy <= OHI; ++oy) {
       const int hy = (cy + oy) & (N - 1);
       const uint32_t rowkey = ((uint32_t)hx * N + (uint32_t)hy) * (uint32_t)N;
-      for (int oz = OLO; oz <= OHI; ++oz) {
-        const int hz = (cz + oz) & (N - 1);
-        const uint32_t key = rowkey + (uint32_t)hz;
-        const uint32_t p0 = cell_start[key], p1 = cell_start[key + 1];
+      // one run without wrap, else one run per home node
+      const int nrun = wrap ? (OHI - OLO + 1) : 1;
+      for (int rr = 0; rr < nrun; ++rr) {
+        uint32_t k0, k1;
+        if (wrap) {
+          k0 = rowkey + (uint32_t)((cz + OLO + rr) & (N - 1));
+          k1 = k0;
+        } else {
+          k0 = rowkey + (uint32_t)(cz + OLO);
+          k1 = rowkey + (uint32_t)(cz + OHI);
+        }
+        const uint32_t p0 = cell_start[k0], p1 = cell_start[k1 + 1];
         for (uint32_t p = p0; p < p1; ++p) {
           const float4 d = frac[p];
+          int oz = (int)(keys[p] & (uint32_t)(N - 1)) - cz;
+          if (oz > OHI) oz -= N;
+          if (oz < OLO) oz += N;
           // distance particle - node along each axis: (h - c) + d
           const float tx = (float)ox + d.x, ty = (float)oy + d.y, tz = (float)oz + d.z;
           const float w0 = wker<P>(tx) * wker<P>(ty) * wker<P>(tz);
           float w1 = 0.f;
           if (ILV) w1 = wker<P>(tx - 0.5f) * wker<P>(ty - 0.5f) * wker<P>(tz - 0.5f);
 #pragma unroll
-          for (int k = 0; k < DEP_CG; ++k) {
-            if (k < nc) {
-              const float v = vals[(size_t)(c0 + k) * n + p];
+          for (int k = 0; k < NC; ++k) {
+            if (k < nchan) {
+              const float v = vals[(size_t)k * n + p];
               a0[k] = fmaf(w0, v, a0[k]);
               if (ILV) a1[k] = fmaf(w1, v, a1[k]);
             }
@@ -408,29 +418,39 @@ __global__ void __launch_bounds__(256) k_deposit(const uint32_t* __restrict__ ce
     }
   }
 #pragma unroll
-  for (int k = 0; k < DEP_CG; ++k) {
-    if (k < nc) {
-      mesh0[(size_t)(c0 + k) * Ng + cell] = a0[k];
-      if (ILV) mesh1[(size_t)(c0 + k) * Ng + cell] = a1[k];
+  for (int k = 0; k < NC; ++k) {
+    if (k < nchan) {
+      mesh0[(size_t)k * Ng + cell] = a0[k];
+      if (ILV) mesh1[(size_t)k * Ng + cell] = a1[k];
     }
   }
 }
 
-void launch_deposit(const DepositArgs& a, cudaStream_t s, int* launches) {
+template <int P, int ILV>
+static void deposit_p(const DepositArgs& a, cudaStream_t s) {
   const int64_t Ng = (int64_t)a.N * a.N * a.N;
-  dim3 grid((unsigned)((Ng + 255) / 256), (unsigned)((a.nchan + DEP_CG - 1) / DEP_CG));
-#define BISP_DEP(P_, I_) \
-  k_deposit<P_, I_><<<grid, 256, 0, s>>>(a.cell_start, a.frac, a.vals, a.n, a.N, a.nchan, a.mesh0, a.mesh1)
-  if (a.interlace) {
-    if (a.mas == 1) BISP_DEP(1, 1);
-    else if (a.mas == 2) BISP_DEP(2, 1);
-    else BISP_DEP(3, 1);
-  } else {
-    if (a.mas == 1) BISP_DEP(1, 0);
-    else if (a.mas == 2) BISP_DEP(2, 0);
-    else BISP_DEP(3, 0);
-  }
+  const unsigned grid = (unsigned)((Ng + 255) / 256);
+#define BISP_DEP(NC_) \
+  k_deposit<P, ILV, NC_><<<grid, 256, 0, s>>>(a.cell_start, a.keys, a.frac, a.vals, a.n, a.N, a.nchan, a.mesh0, a.mesh1)
+  if (a.nchan <= 1) BISP_DEP(1);
+  else if (a.nchan <= 2) BISP_DEP(2);
+  else if (a.nchan <= 6) BISP_DEP(6);
+  else if (a.nchan <= 12) BISP_DEP(12);
+  else if (a.nchan <= 16) BISP_DEP(16);
+  else throw Error{6, "deposit: more than 16 channels"};
 #undef BISP_DEP
+}
+
+void launch_deposit(const DepositArgs& a, cudaStream_t s, int* launches) {
+  if (a.interlace) {
+    if (a.mas == 1) deposit_p<1, 1>(a, s);
+    else if (a.mas == 2) deposit_p<2, 1>(a, s);
+    else deposit_p<3, 1>(a, s);
+  } else {
+    if (a.mas == 1) deposit_p<1, 0>(a, s);
+    else if (a.mas == 2) deposit_p<2, 0>(a, s);
+    else deposit_p<3, 0>(a, s);
+  }
   BISP_CHECK_LAUNCH();
   if (launches) ++*launches;
 }

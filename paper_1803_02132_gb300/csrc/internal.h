@@ -69,6 +69,7 @@ void launch_gather_particles(const uint32_t* perm, int64_t n, const float4* frac
                              int nchan, float4* frac_out, float* vals_out, cudaStream_t s);
 struct DepositArgs {
   const uint32_t* cell_start;  // N^3 + 1
+  const uint32_t* keys;        // sorted home-node keys
   const float4* frac;          // sorted
   const float* vals;           // sorted [nchan][n]
   int64_t n;
@@ -126,8 +127,8 @@ struct ZsumArgs {
   double sbar_re, sbar_im;
   int N, P;
   int nbins;
-  const long long* qlo;   // [nbins]
-  const long long* qhi;
+  const uint32_t* modes;  // half-spectrum shell modes, (sx+512) | (sy+512) << 10 | nz << 20
+  const int64_t* mode_off;  // modes of bin b: [mode_off[b], mode_off[b+1])
   const float* cw2_1d;
   int interlace;
   int nlm;                // number of (l, m) pairs, m >= 0

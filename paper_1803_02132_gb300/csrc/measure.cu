@@ -51,21 +51,14 @@ __device__ __forceinline__ float2 ystar(int l, int m, float x, float y, float z,
 __global__ void __launch_bounds__(ZS_THREADS) k_zsum() {
   const ZsumArgs& A = c_zs;
   const int b = blockIdx.y;
-  const long long qlo = A.qlo[b], qhi = A.qhi[b];
-  int P = (int)floor(sqrt((double)(qhi - 1)));
-  if (P > A.N / 2 - 1) P = A.N / 2 - 1;
   const int N = A.N, NH = N / 2;
-  const int ny_ = 2 * P + 1;
-  const long long nmode = (long long)ny_ * ny_ * (P + 1);
+  const int64_t m0 = A.mode_off[b], m1 = A.mode_off[b + 1];
   double acc[ZS_MAXLM][2];
 #pragma unroll
   for (int q = 0; q < ZS_MAXLM; ++q) acc[q][0] = acc[q][1] = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nmode; i += (long long)gridDim.x * blockDim.x) {
-    const int nz = (int)(i % (P + 1));
-    const int sy = (int)((i / (P + 1)) % ny_) - P;
-    const int sx = (int)(i / ((long long)(P + 1) * ny_)) - P;
-    const long long q = (long long)sx * sx + (long long)sy * sy + (long long)nz * nz;
-    if (q < qlo || q >= qhi) continue;
+  for (int64_t i = m0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m1; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t code = A.modes[i];
+    const int sx = (int)(code & 1023u) - 512, sy = (int)((code >> 10) & 1023u) - 512, nz = (int)(code >> 20);
     const int jx = sx & (N - 1), jy = sy & (N - 1);
     const size_t gi = ((size_t)jx * N + jy) * NH + nz;
     const float2 d = A.D00[gi];
@@ -177,7 +170,7 @@ constexpr int PR_NSTAGE = 3;       // chunks staged ahead
 constexpr int PR_MAXWARP = 16;
 
 struct PairLaunch {
-  int TM, TN, nbp, ksplit, warps, nblk, rows;
+  int TM, TN, nbp, bs, ksplit, warps, nblk, rows;
   size_t smem;
 };
 
@@ -201,7 +194,8 @@ static PairLaunch pair_launch_cfg(const PairJob& j) {
   c.ksplit = 1;
   while (c.ksplit < 8 && j.nterm * c.ksplit * 2 <= PR_MAXWARP) c.ksplit *= 2;
   c.warps = j.nterm * c.ksplit;
-  c.rows = c.nbp * j.ncomp + j.ng;
+  c.bs = j.ncomp | 1;  // odd rows per bin: consecutive bins fall on different banks
+  c.rows = c.nbp * c.bs + j.ng;
   c.smem = ((size_t)PR_NSTAGE * c.rows * PR_LD + (size_t)j.nslot * c.nbp * PR_LD + (size_t)j.nh * PR_CH) *
            sizeof(float);
   int dev = 0, nsm = 148;
@@ -290,7 +284,7 @@ template <int NW>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW)); }
 
 // copy one chunk of every component row [b][comp] and G row into shared memory
-__device__ __forceinline__ void pair_stage(float* raw, int64_t x0, int nbp) {
+__device__ __forceinline__ void pair_stage(float* raw, int64_t x0, int nbp, int bs) {
   const PairJob& J = c_pj;
   constexpr int Q = PR_CH / 4;
   const int nraw = J.nb * J.ncomp;
@@ -301,26 +295,27 @@ __device__ __forceinline__ void pair_stage(float* raw, int64_t x0, int nbp) {
     int row;
     if (f < nraw) {
       src = J.fields + (size_t)f * J.Ng + x0 + 4 * q;
-      row = f;
+      const int b = f / J.ncomp;
+      row = b * bs + (f - b * J.ncomp);
     } else {
       src = J.gfields + (size_t)(f - nraw) * J.Ng + x0 + 4 * q;
-      row = nbp * J.ncomp + (f - nraw);
+      row = nbp * bs + (f - nraw);
     }
     cp_async16(raw + (size_t)row * PR_LD + 4 * q, src);
   }
 }
 
 template <int TM, int TN, int NTHR>
-__global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int rows, int ksplit, double* partials) {
+__global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int ksplit, double* partials) {
   const PairJob& J = c_pj;
   extern __shared__ __align__(16) float sh[];
   float* mat = sh + (size_t)PR_NSTAGE * rows * PR_LD;  // [nslot][nbp][PR_LD]
-  const int grow0 = nbp * J.ncomp;
+  const int grow0 = nbp * bs;
   const int64_t nchunk = J.Ng / PR_CH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int t = warp / ksplit, ks = warp % ksplit;
   const int slice = PR_CH / ksplit;
-  const int b1 = (lane >> 3) * TM, b2 = (lane & 7) * TN;
+  const int b1 = lane >> 3, b2 = lane & 7;  // rows b1 + 4 i and b2 + 8 j
   const PairTermDesc T = J.term[t];
   double* slot = partials + (((size_t)blockIdx.x * nwarp + warp) * 32 + lane) * (TM * TN);
 #pragma unroll
@@ -335,7 +330,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int rows, int ksplit,
 #pragma unroll
   for (int s = 0; s < PR_NSTAGE - 1; ++s) {
     chs[s] = blockIdx.x + (int64_t)s * gridDim.x;
-    if (chs[s] < nchunk) pair_stage(sh + (size_t)s * rows * PR_LD, chs[s] * PR_CH, nbp);
+    if (chs[s] < nchunk) pair_stage(sh + (size_t)s * rows * PR_LD, chs[s] * PR_CH, nbp, bs);
     cp_async_commit();
   }
   int since_flush = 0, stage = 0;
@@ -345,7 +340,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int rows, int ksplit,
     {
       const int64_t nx = ch + (int64_t)(PR_NSTAGE - 1) * gridDim.x;
       const int ns = (stage + PR_NSTAGE - 1) % PR_NSTAGE;
-      if (nx < nchunk) pair_stage(sh + (size_t)ns * rows * PR_LD, nx * PR_CH, nbp);
+      if (nx < nchunk) pair_stage(sh + (size_t)ns * rows * PR_LD, nx * PR_CH, nbp, bs);
       cp_async_commit();
     }
     const float* raw = sh + (size_t)stage * rows * PR_LD;
@@ -375,22 +370,22 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int rows, int ksplit,
         *reinterpret_cast<float4*>(Hs + (size_t)h * PR_CH + 4 * q) = v;
       }
       __syncthreads();
-      for (int i = threadIdx.x; i < J.nb * Q; i += blockDim.x) {
-        const int b = i / Q, q = i % Q;
-        const float* rb = raw + (size_t)b * J.ncomp * PR_LD + 4 * q;
-        for (int sl = 0; sl < J.nslot; ++sl) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          for (int e = J.s_off[sl]; e < J.s_off[sl + 1]; ++e) {
-            const int c = J.s_ent[e][0], h = J.s_ent[e][1];
-            const float4 pv = *reinterpret_cast<const float4*>(rb + (size_t)c * PR_LD);
-            const float4 hv = *reinterpret_cast<const float4*>(Hs + (size_t)h * PR_CH + 4 * q);
-            v.x = fmaf(pv.x, hv.x, v.x);
-            v.y = fmaf(pv.y, hv.y, v.y);
-            v.z = fmaf(pv.z, hv.z, v.z);
-            v.w = fmaf(pv.w, hv.w, v.w);
-          }
-          *reinterpret_cast<float4*>(mat + ((size_t)sl * nbp + b) * PR_LD + 4 * q) = v;
+      const int per_slot = J.nb * Q;
+      for (int i = threadIdx.x; i < J.nslot * per_slot; i += blockDim.x) {
+        const int sl = i / per_slot, r = i - sl * per_slot;
+        const int b = r / Q, q = r % Q;
+        const float* rb = raw + (size_t)b * bs * PR_LD + 4 * q;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = J.s_off[sl]; e < J.s_off[sl + 1]; ++e) {
+          const int c = J.s_ent[e][0], h = J.s_ent[e][1];
+          const float4 pv = *reinterpret_cast<const float4*>(rb + (size_t)c * PR_LD);
+          const float4 hv = *reinterpret_cast<const float4*>(Hs + (size_t)h * PR_CH + 4 * q);
+          v.x = fmaf(pv.x, hv.x, v.x);
+          v.y = fmaf(pv.y, hv.y, v.y);
+          v.z = fmaf(pv.z, hv.z, v.z);
+          v.w = fmaf(pv.w, hv.w, v.w);
         }
+        *reinterpret_cast<float4*>(mat + ((size_t)sl * nbp + b) * PR_LD + 4 * q) = v;
       }
       __syncthreads();
     }
@@ -398,18 +393,18 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int rows, int ksplit,
     const float* yr;
     int sx, sy;
     if (T.xdir >= 0) {
-      xr = raw + (size_t)(b1 * J.ncomp + T.xdir) * PR_LD;
-      sx = J.ncomp * PR_LD;
+      xr = raw + (size_t)(b1 * bs + T.xdir) * PR_LD;
+      sx = 4 * bs * PR_LD;
     } else {
       xr = mat + ((size_t)T.xslot * nbp + b1) * PR_LD;
-      sx = PR_LD;
+      sx = 4 * PR_LD;
     }
     if (T.ydir >= 0) {
-      yr = raw + (size_t)(b2 * J.ncomp + T.ydir) * PR_LD;
-      sy = J.ncomp * PR_LD;
+      yr = raw + (size_t)(b2 * bs + T.ydir) * PR_LD;
+      sy = 8 * bs * PR_LD;
     } else {
       yr = mat + ((size_t)T.yslot * nbp + b2) * PR_LD;
-      sy = PR_LD;
+      sy = 8 * PR_LD;
     }
     xr += ks * slice;
     yr += ks * slice;
@@ -454,7 +449,7 @@ __global__ void k_pair_final(const double* partials, int nblk, int warps, int ks
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= nout * nb * nb) return;
   const int o = gw / (nb * nb), b1 = (gw / nb) % nb, b2 = gw % nb;
-  const int ln = (b1 / TM) * 8 + b2 / TN, q = (b1 % TM) * TN + (b2 % TN);
+  const int ln = (b1 % 4) * 8 + b2 % 8, q = (b1 / 4) * TN + b2 / 8;
   double s = 0.0;
   for (int t = J.out_term_off[o]; t < J.out_term_off[o + 1]; ++t)
     for (int ks = 0; ks < ksplit; ++ks) {
@@ -478,7 +473,7 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
 #define BISP_PAIR3(A, B, NT)                                                                              \
   if (c.TM == A && c.TN == B && c.warps * 32 <= NT) {                                                   \
     BISP_CUDA(cudaFuncSetAttribute(k_pair<A, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem)); \
-    k_pair<A, B, NT><<<c.nblk, c.warps * 32, c.smem, s>>>(c.nbp, c.rows, c.ksplit, partials);           \
+    k_pair<A, B, NT><<<c.nblk, c.warps * 32, c.smem, s>>>(c.nbp, c.bs, c.rows, c.ksplit, partials);           \
     launched = true;                                                                                     \
   }
 #define BISP_PAIR(A, B) \

@@ -191,6 +191,8 @@ struct bisp_plan {
   std::vector<long long> qlo, qhi;
   std::vector<int> Pb;
   std::vector<double> nmodes;
+  std::vector<uint32_t> zlist;
+  std::vector<int64_t> zoff;
   std::vector<Comp> comps;
   std::map<std::tuple<int, int, int>, int> comp_index;  // (l, m, part) -> index
   std::vector<std::vector<cplx>> Y;                     // [b][lm index (l, m signed)]
@@ -200,7 +202,7 @@ struct bisp_plan {
   };
   std::vector<std::vector<Term>> terms;
   // device constants
-  DBuf tw, winv, ynorm, cw2, qlo_d, qhi_d;
+  DBuf tw, winv, ynorm, cw2, qlo_d, qhi_d, zmodes, zmode_off;
   Catalog cat[2];
   // measurement buffers
   DBuf pass_spec[2], gf[2], qf, pool, invscr, pairscr, pairout, zpart;
@@ -352,6 +354,26 @@ void build_shells(bisp_plan* P) {
           }
       }
   P->nmodes = cnt;
+  // half-spectrum shell mode lists (nz >= 0; for nz = 0 both k and -k are listed)
+  {
+    std::vector<std::vector<uint32_t>> lists(nb);
+    for (int x = -Pm; x <= Pm; ++x)
+      for (int y = -Pm; y <= Pm; ++y)
+        for (int z = 0; z <= Pm; ++z) {
+          const long long q = (long long)x * x + (long long)y * y + (long long)z * z;
+          if (q == 0 || q > qmax) continue;
+          const int b = binq[q];
+          if (b < 0 || std::abs(x) > P->Pb[b] || std::abs(y) > P->Pb[b] || z > P->Pb[b]) continue;
+          lists[b].push_back((uint32_t)(x + 512) | ((uint32_t)(y + 512) << 10) | ((uint32_t)z << 20));
+        }
+    P->zlist.clear();
+    P->zoff.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+      P->zoff[b] = (int64_t)P->zlist.size();
+      P->zlist.insert(P->zlist.end(), lists[b].begin(), lists[b].end());
+    }
+    P->zoff[nb] = (int64_t)P->zlist.size();
+  }
   P->Y.assign(nb, std::vector<cplx>(nlm));
   for (int b = 0; b < nb; ++b)
     for (int i = 0; i < nlm; ++i)
@@ -467,6 +489,11 @@ void upload_tables(bisp_plan* P) {
   P->winv.ensure(winv.size() * sizeof(float), &P->bytes);
   P->cw2.ensure(cw2.size() * sizeof(float), &P->bytes);
   P->ynorm.ensure(yn.size() * sizeof(float), &P->bytes);
+  P->zmodes.ensure(std::max<size_t>(P->zlist.size(), 1) * 4, &P->bytes);
+  P->zmode_off.ensure(P->zoff.size() * 8, &P->bytes);
+  if (!P->zlist.empty())
+    BISP_CUDA(cudaMemcpy(P->zmodes.p, P->zlist.data(), P->zlist.size() * 4, cudaMemcpyHostToDevice));
+  BISP_CUDA(cudaMemcpy(P->zmode_off.p, P->zoff.data(), P->zoff.size() * 8, cudaMemcpyHostToDevice));
   P->qlo_d.ensure(P->nb * sizeof(long long), &P->bytes);
   P->qhi_d.ensure(P->nb * sizeof(long long), &P->bytes);
   BISP_CUDA(cudaMemcpy(P->tw.p, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
@@ -628,6 +655,7 @@ void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const 
   if (ilv) mesh1.ensure((size_t)nchan * Ng * 4, &tb);
   DepositArgs da{};
   da.cell_start = cstart;
+  da.keys = skeys.as<uint32_t>();
   da.frac = sfrac.as<float4>();
   da.vals = svals.as<float>();
   da.n = n;
@@ -935,8 +963,8 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
             z.sbar_im = sbv.i;
             z.N = P->N;
             z.nbins = nb;
-            z.qlo = P->qlo_d.as<long long>();
-            z.qhi = P->qhi_d.as<long long>();
+            z.modes = P->zmodes.as<uint32_t>();
+            z.mode_off = P->zmode_off.as<int64_t>();
             z.cw2_1d = P->cw2.as<float>();
             z.interlace = P->interlace;
             z.nlm = cnt;
@@ -1047,7 +1075,7 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
 void destroy(bisp_plan* P) {
   if (!P) return;
   size_t* t = &P->bytes;
-  for (auto* d : {&P->tw, &P->winv, &P->ynorm, &P->cw2, &P->qlo_d, &P->qhi_d, &P->pool, &P->invscr, &P->pairscr,
+  for (auto* d : {&P->tw, &P->winv, &P->ynorm, &P->cw2, &P->qlo_d, &P->qhi_d, &P->zmodes, &P->zmode_off, &P->pool, &P->invscr, &P->pairscr,
                   &P->pairout, &P->zpart})
     d->release(t);
   for (int k = 0; k < 2; ++k) {
