@@ -154,8 +154,13 @@ struct PairJob {
   int out_term_off[33];   // terms of output o: [off[o], off[o+1])
   int nterm;
   int nslot;              // sides built per chunk
-  int term_out[64];       // output of each term
+  int term_out[64];       // output of each term (before merging)
   PairTermDesc term[64];
+  // after merging terms that differ only by a scalar: output o = sum over its entries
+  // (term u, FP64 multiplier) of the sum over cells of term u
+  int out_ent_off[33];
+  int out_ent_term[128];
+  double out_ent_mult[128];
   // built sides: side s = sum over its entries (c, h) of P_c(b, x) H_h(x), where
   // H_h(x) = sum over its entries (g, coef) of coef G_g(x) (g < 0: the constant coef)
   int nh;

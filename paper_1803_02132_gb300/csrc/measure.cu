@@ -9,6 +9,8 @@
 //    memory.  FP32 products in 4x4 register tiles, FP32 partials over at most 1024
 //    cells, FP64 above that; per-CTA partials are reduced in a fixed order.
 #include <algorithm>
+#include <tuple>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -192,7 +194,7 @@ static PairLaunch pair_launch_cfg(const PairJob& j) {
   if (j.nterm > 2 * PR_MAXWARP || (j.nterm > PR_MAXWARP && c.TM * c.TN > 18))
     throw Error{6, "pair reduction: too many terms for one CTA"};
   c.ksplit = 1;
-  while (c.ksplit < 8 && j.nterm * c.ksplit * 2 <= PR_MAXWARP) c.ksplit *= 2;
+  while (c.ksplit < 2 && j.nterm * c.ksplit * 2 <= PR_MAXWARP) c.ksplit *= 2;  // slices of >= 16 cells
   c.warps = j.nterm * c.ksplit;
   c.bs = j.ncomp | 1;  // odd rows per bin: consecutive bins fall on different banks
   c.rows = c.nbp * c.bs + j.ng;
@@ -205,9 +207,68 @@ static PairLaunch pair_launch_cfg(const PairJob& j) {
   return c;
 }
 
-// classify the sides of every term: bare component field (read in place) or built
+// merge terms equal up to a scalar, then classify the sides of every term: bare component
+// field (read in place) or built
 static PairJob classify(const PairJob& job) {
   PairJob j = job;
+  {
+    // normalised term: a single-entry X side (c, g, coef) with a bare Y side is coef times
+    // the unit term (c, g, 1 | Y); other terms are kept as they are (multiplier 1)
+    struct Key {
+      std::vector<std::tuple<int, int, float>> x, y;
+      bool operator==(const Key& o) const { return x == o.x && y == o.y; }
+    };
+    std::vector<Key> keys;
+    std::vector<PairTermDesc> nterm;
+    std::vector<PairRecipe> nrec;
+    int ne = 0;
+    for (int o = 0; o < j.nout; ++o) {
+      j.out_ent_off[o] = ne;
+      for (int t = job.out_term_off[o]; t < job.out_term_off[o + 1]; ++t) {
+        const PairTermDesc& T = job.term[t];
+        Key k;
+        double mult = 1.0;
+        for (int e = 0; e < T.xcnt; ++e) {
+          const PairRecipe& R = job.rec[T.xoff + e];
+          k.x.push_back({R.comp, R.g, R.coef});
+        }
+        for (int e = 0; e < T.ycnt; ++e) {
+          const PairRecipe& R = job.rec[T.yoff + e];
+          k.y.push_back({R.comp, R.g, R.coef});
+        }
+        auto bare_y = [&]() { return k.y.size() == 1 && std::get<1>(k.y[0]) < 0 && std::get<2>(k.y[0]) == 1.0f; };
+        if (k.x.size() == 1 && bare_y()) {
+          mult = std::get<2>(k.x[0]);
+          std::get<2>(k.x[0]) = 1.0f;
+        }
+        int u = -1;
+        for (size_t i = 0; i < keys.size(); ++i)
+          if (keys[i] == k) u = (int)i;
+        if (u < 0) {
+          u = (int)keys.size();
+          keys.push_back(k);
+          PairTermDesc d{};
+          d.xoff = (int)nrec.size();
+          d.xcnt = (int)k.x.size();
+          for (auto& r : k.x) nrec.push_back({std::get<0>(r), std::get<1>(r), std::get<2>(r)});
+          d.yoff = (int)nrec.size();
+          d.ycnt = (int)k.y.size();
+          for (auto& r : k.y) nrec.push_back({std::get<0>(r), std::get<1>(r), std::get<2>(r)});
+          nterm.push_back(d);
+        }
+        if (ne >= 128) throw Error{6, "pair reduction: too many output entries"};
+        j.out_ent_term[ne] = u;
+        j.out_ent_mult[ne] = mult;
+        ++ne;
+      }
+    }
+    j.out_ent_off[j.nout] = ne;
+    if (nterm.size() > 64 || nrec.size() > 512) throw Error{6, "pair reduction: recipe tables overflow"};
+    j.nterm = (int)nterm.size();
+    for (int t = 0; t < j.nterm; ++t) j.term[t] = nterm[t];
+    j.nrec = (int)nrec.size();
+    for (int r = 0; r < j.nrec; ++r) j.rec[r] = nrec[r];
+  }
   j.nslot = 0;
   for (int t = 0; t < j.nterm; ++t) {
     PairTermDesc& T = j.term[t];
@@ -218,9 +279,6 @@ static PairJob classify(const PairJob& job) {
     T.ydir = bare(T.yoff, T.ycnt);
     T.xslot = T.xdir >= 0 ? -1 : j.nslot++;
     T.yslot = T.ydir >= 0 ? -1 : j.nslot++;
-    int o = 0;
-    while (o + 1 <= j.nout && j.out_term_off[o + 1] <= t) ++o;
-    j.term_out[t] = o;
   }
   // factor every built side by component: H rows shared between sides when identical
   std::vector<std::vector<std::pair<int, float>>> rows;
@@ -256,6 +314,10 @@ static PairJob classify(const PairJob& job) {
       ++ns;
     }
   j.s_off[ns] = nse;
+  for (int q = 0; q < ns; ++q)
+    if (j.s_off[q + 1] - j.s_off[q] > 8) throw Error{6, "pair reduction: more than 8 components in a side"};
+  for (int t = 0; t < j.nterm; ++t)
+    if (j.term[t].xslot >= 0 && j.term[t].yslot >= 0) throw Error{6, "pair reduction: both sides built"};
   if (rows.size() > 128) throw Error{6, "pair reduction: too many H rows"};
   int ne = 0;
   for (size_t r = 0; r < rows.size(); ++r) {
@@ -309,7 +371,7 @@ template <int TM, int TN, int NTHR>
 __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int ksplit, double* partials) {
   const PairJob& J = c_pj;
   extern __shared__ __align__(16) float sh[];
-  float* mat = sh + (size_t)PR_NSTAGE * rows * PR_LD;  // [nslot][nbp][PR_LD]
+  float* mat = sh + (size_t)PR_NSTAGE * rows * PR_LD;  // [nslot][nbp][PR_LD], then H rows
   const int grow0 = nbp * bs;
   const int64_t nchunk = J.Ng / PR_CH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -408,23 +470,26 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int
     }
     xr += ks * slice;
     yr += ks * slice;
-    for (int x = 0; x < slice; x += 4) {
-      float4 a[TM], c[TN];
+    for (int xb = 0; xb < slice; xb += 16) {
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = *reinterpret_cast<const float4*>(xr + i * sx + x);
+      for (int x = xb; x < xb + 16; x += 4) {
+        float4 a[TM], c[TN];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) c[j] = *reinterpret_cast<const float4*>(yr + j * sy + x);
+        for (int i = 0; i < TM; ++i) a[i] = *reinterpret_cast<const float4*>(xr + i * sx + x);
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+        for (int j = 0; j < TN; ++j) c[j] = *reinterpret_cast<const float4*>(yr + j * sy + x);
 #pragma unroll
-        for (int j = 0; j < TN; ++j) {
-          float s = acc[i][j];
-          s = fmaf(a[i].x, c[j].x, s);
-          s = fmaf(a[i].y, c[j].y, s);
-          s = fmaf(a[i].z, c[j].z, s);
-          s = fmaf(a[i].w, c[j].w, s);
-          acc[i][j] = s;
-        }
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            float s = acc[i][j];
+            s = fmaf(a[i].x, c[j].x, s);
+            s = fmaf(a[i].y, c[j].y, s);
+            s = fmaf(a[i].z, c[j].z, s);
+            s = fmaf(a[i].w, c[j].w, s);
+            acc[i][j] = s;
+          }
+      }
     }
     if (++since_flush == PR_FLUSH || ch + gridDim.x >= nchunk) {
       since_flush = 0;
@@ -450,15 +515,19 @@ __global__ void k_pair_final(const double* partials, int nblk, int warps, int ks
   if (gw >= nout * nb * nb) return;
   const int o = gw / (nb * nb), b1 = (gw / nb) % nb, b2 = gw % nb;
   const int ln = (b1 % 4) * 8 + b2 % 8, q = (b1 / 4) * TN + b2 / 8;
-  double s = 0.0;
-  for (int t = J.out_term_off[o]; t < J.out_term_off[o + 1]; ++t)
+  double tot = 0.0;
+  for (int e = J.out_ent_off[o]; e < J.out_ent_off[o + 1]; ++e) {
+    const int t = J.out_ent_term[e];
+    double s = 0.0;
     for (int ks = 0; ks < ksplit; ++ks) {
       const int w = t * ksplit + ks;
       for (int c = lane; c < nblk; c += 32) s += partials[(((size_t)c * warps + w) * 32 + ln) * (TM * TN) + q];
     }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-  if (lane == 0) out[gw] = s;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    tot += J.out_ent_mult[e] * s;
+  }
+  if (lane == 0) out[gw] = tot;
 }
 
 void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scratch_bytes, cudaStream_t s,

@@ -118,7 +118,6 @@ struct cplx {
   double r = 0, i = 0;
 };
 cplx cm(cplx a, cplx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
-cplx cc(cplx a) { return {a.r, -a.i}; }
 
 // ---------------------------------------------------------------------------------
 // device buffer cache
