@@ -140,6 +140,26 @@ bisp_status bisp_plan_query(const bisp_plan* plan, bisp_plan_info* info);
 bisp_status bisp_cell_order(int nmesh, double box_len, int mas, const float* xyz, int64_t n,
                             uint32_t* keys_out, uint32_t* order_out, void* stream);
 
+/* Largest catalogue accepted by bisp_cell_order_noalloc. */
+#define BISP_NOALLOC_MAX_PARTICLES (1 << 20)
+
+/* bisp_cell_order without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory during the call -
+ * code running under a framework that forbids cudaMalloc/cudaFree inside a step or while a
+ * CUDA graph is being recorded, allocators that must not be re-entered, or processes
+ * without spare device memory.  Same arguments, outputs and errors as bisp_cell_order.
+ *   - Scratch lives in one statically sized device array in the library (about
+ *     32 bytes per particle of BISP_NOALLOC_MAX_PARTICLES plus 4 MiB, i.e. 36 MiB); every
+ *     GPU that loads the library holds it until the process exits.
+ *   - n > BISP_NOALLOC_MAX_PARTICLES returns BISP_EINVAL and names the limit.
+ *   - The first call on a device resolves the array's device address with that device
+ *     current; make that first call before any stream capture.
+ *   - All calls share the one array: calls whose GPU work overlaps (on different streams or
+ *     host threads) race and corrupt each other's results.  Serialise them.
+ *   - The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine). */
+bisp_status bisp_cell_order_noalloc(int nmesh, double box_len, int mas, const float* xyz, int64_t n,
+                                    uint32_t* keys_out, uint32_t* order_out, void* stream);
+
 /* Copy an internal array of the plan to host memory (tests):
  *   what = BISP_DBG_SPECTRUM: the deconvolved half spectrum of channel `index` of
  *          catalogue `which`, complex64 [N][N][N/2] (nz < N/2), 8*N*N*N/2 bytes;

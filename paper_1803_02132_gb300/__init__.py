@@ -61,8 +61,9 @@ def _load():
     lib.bisp_plan_query.argtypes = [vp, C.POINTER(_Info)]
     lib.bisp_cell_order.argtypes = [C.c_int, C.c_double, C.c_int, vp, C.c_int64, vp, vp, vp]
     lib.bisp_debug_fetch.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, C.c_size_t]
+    lib.bisp_cell_order_noalloc.argtypes = [C.c_int, C.c_double, C.c_int, vp, C.c_int64, vp, vp, vp]
     for f in ("bisp_plan_create", "bisp_assign", "bisp_measure", "bisp_plan_destroy", "bisp_plan_query",
-              "bisp_cell_order", "bisp_debug_fetch"):
+              "bisp_cell_order", "bisp_debug_fetch", "bisp_cell_order_noalloc"):
         getattr(lib, f).restype = C.c_int
     return lib
 

@@ -20,6 +20,8 @@ struct Error {
       throw ::bisp::Error{3, std::string(#call) + ": " + cudaGetErrorString(e_)};         \
   } while (0)
 #define BISP_CHECK_LAUNCH() BISP_CUDA(cudaGetLastError())
+// message returned by bisp_last_error() on the calling thread
+void set_last_error(const std::string& m);
 
 // ---- channel descriptors --------------------------------------------------------
 // A channel is one real mesh: weight^power * (Re or Im)(y_L^M(x_hat) or its conjugate).

@@ -171,6 +171,8 @@ struct Catalog {
 
 }  // namespace
 
+void bisp::set_last_error(const std::string& m) { g_err = m; }
+
 struct bisp_plan {
   // parameters
   int N = 0, NH = 0, nb = 0, nmult = 0, los = 0, mas = 2, interlace = 0, want_window = 0;
