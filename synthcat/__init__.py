@@ -66,7 +66,7 @@ def clustered_field(n, box, seed, kaiser=0.7, quadratic=True):
     amp = np.sqrt(power_law_pk(kk) * n ** 3 / vol).astype(np.float32)
     dk = wk * amp
     del wk, amp
-    dg = np.fft.irfftn(dk, s=(n, n, n)).astype(np.float32)
+    dg = np.fft.irfftn(dk, s=(n, n, n), axes=(0, 1, 2)).astype(np.float32)
     del dk
     if quadratic:
         dg = dg + 0.5 * (dg * dg - np.mean(dg.astype(np.float64) ** 2)).astype(np.float32)
@@ -75,7 +75,7 @@ def clustered_field(n, box, seed, kaiser=0.7, quadratic=True):
         with np.errstate(invalid="ignore", divide="ignore"):
             mu2 = np.where(kk > 0, (kz[None, None, :] / np.where(kk > 0, kk, 1.0)) ** 2, 0.0)
         dk *= (1.0 + kaiser * mu2).astype(np.float32)
-        dg = np.fft.irfftn(dk, s=(n, n, n)).astype(np.float32)
+        dg = np.fft.irfftn(dk, s=(n, n, n), axes=(0, 1, 2)).astype(np.float32)
         del dk
     return dg
 
