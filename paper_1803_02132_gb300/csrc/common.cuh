@@ -150,4 +150,40 @@ __device__ __forceinline__ void fft_smem(float2* s, const float2* __restrict__ t
   FftStage<NF, LB, SIGN, 1, NF>::run(s, tw, ldl, threadIdx.x % LB, threadIdx.x / LB);
 }
 
+// ---------------------------------------------------------------------------------
+// In-register DFT of R = 2..32 points (R a power of two), radix-2 decimation in time,
+// unnormalised, sign SIGN: X[k] = sum_n v[n] e^{SIGN 2 pi i n k / R}; tw is the twiddle
+// table e^{-2 pi i j / BISP_TWN}.
+// ---------------------------------------------------------------------------------
+// 32nd roots of unity e^{-2 pi i j / 32} for the in-register DFTs (indices are compile-time
+// constants there, so the values are read as constant-bank operands).  Each translation
+// unit has its own copy; the one that uses DftReg uploads it (upload_root32 in fft.cu).
+static __constant__ float2 c_root32[32];
+
+template <int R, int SIGN>
+struct DftReg {
+  static __device__ __forceinline__ void run(float2* v, const float2* __restrict__ tw) {
+    float2 e[R / 2], o[R / 2];
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      e[k] = v[2 * k];
+      o[k] = v[2 * k + 1];
+    }
+    DftReg<R / 2, SIGN>::run(e, tw);
+    DftReg<R / 2, SIGN>::run(o, tw);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      float2 w = c_root32[k * (32 / R)];
+      if (SIGN > 0) w.y = -w.y;
+      const float2 t = cmul(w, o[k]);
+      v[k] = cadd(e[k], t);
+      v[k + R / 2] = csub(e[k], t);
+    }
+  }
+};
+template <int SIGN>
+struct DftReg<1, SIGN> {
+  static __device__ __forceinline__ void run(float2*, const float2* __restrict__) {}
+};
+
 }  // namespace bisp

@@ -13,6 +13,10 @@
 
 namespace bisp {
 
+void upload_root32(const float2* host32) {
+  BISP_CUDA(cudaMemcpyToSymbol(c_root32, host32, 32 * sizeof(float2)));
+}
+
 template <int N>
 struct Geo {
   static constexpr int NH = N / 2;
@@ -371,6 +375,83 @@ __global__ void __launch_bounds__(Geo<N>::TZ) k_inv_z(const float2* t2all, const
   }
 }
 
+// c2r along z with the FFT held in registers: NH = A x B, A threads per row, each holding
+// B values.  Step 1: Z[n] for n = a + A b (c2r pre-processing from the T2 row, read from
+// global memory); step 2: B-point DFTs over b; step 3: twiddle e^{2 pi i a kb / NH};
+// step 4: transpose through shared memory; step 5: A-point DFTs over a; outputs
+// z[kb + B ka] -> cells 2m, 2m+1 with m = kb + B ka.
+__host__ __device__ constexpr int regz_a(int nh) {
+  return nh >= 256 ? 16 : (nh >= 64 ? 8 : (nh >= 32 ? 4 : 2));
+}
+template <int N>
+struct RegZ {
+  static constexpr int NH = N / 2;
+  static constexpr int A = regz_a(NH);  // threads per row
+  static constexpr int B = NH / A;      // values per thread (a multiple of A)
+  static constexpr int ROWS = 256 / A;  // rows per CTA (256 threads)
+  // transpose buffer, then e^{2 pi i j / NH} (NH entries) and e^{2 pi i j / N} (NH entries)
+  static constexpr size_t SMEM = ((size_t)ROWS * B * (A + 1) + 2 * NH) * sizeof(float2);
+};
+
+template <int N>
+__global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const float2* __restrict__ tw) {
+  constexpr int NH = N / 2, A = RegZ<N>::A, B = RegZ<N>::B, ROWS = RegZ<N>::ROWS;
+  constexpr int LDT = A + 1;  // padded transpose row
+  static_assert(B % A == 0, "B must be a multiple of A");
+  extern __shared__ float2 sbuf[];
+  float2* wNH = sbuf + ROWS * B * LDT;  // e^{+2 pi i j / NH}
+  float2* wN = wNH + NH;                // e^{+2 pi i j / N}, j < NH
+  for (int j = threadIdx.x; j < NH; j += blockDim.x) {
+    wNH[j] = cconj(tw[(j * (BISP_TWN / NH)) & (BISP_TWN - 1)]);
+    wN[j] = cconj(tw[(j * (BISP_TWN / N)) & (BISP_TWN - 1)]);
+  }
+  __syncthreads();
+  const InvBatch& Bt = c_inv;
+  const InvGeo g = inv_geo(N, Bt.P, Geo<N>::LB);
+  const int f = blockIdx.y;
+  const int l = threadIdx.x / A, a = threadIdx.x % A;
+  const size_t row = (size_t)blockIdx.x * ROWS + l;
+  const float2* x = t2all + (size_t)f * g.t2 + row * g.Pz;
+  const int P = Bt.P;
+  float2 v[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int n = a + A * b;
+    // X[k], k <= P (and X[0] real); X[NH] = 0 (Nyquist dropped)
+    float2 xa = n <= P ? x[n] : make_float2(0.f, 0.f);
+    const int nm = NH - n;
+    float2 xb = (n > 0 && nm <= P) ? x[nm] : make_float2(0.f, 0.f);
+    if (n == 0) xa.y = 0.f;
+    // Z[n] = (X[n] + X*[NH-n]) + i (X[n] - X*[NH-n]) e^{2 pi i n / N}
+    const float2 sp = make_float2(xa.x + xb.x, xa.y - xb.y);
+    const float2 dm = make_float2(xa.x - xb.x, xa.y + xb.y);
+    const float2 t = cmul(dm, wN[n]);
+    v[b] = make_float2(sp.x - t.y, sp.y + t.x);
+  }
+  DftReg<B, +1>::run(v, tw);
+  // twiddle e^{+2 pi i a kb / NH} and transpose: element (a, kb) -> sbuf[l][kb][a]
+#pragma unroll
+  for (int kb = 0; kb < B; ++kb) {
+    sbuf[(l * B + kb) * LDT + a] = cmul(v[kb], wNH[(a * kb) & (NH - 1)]);
+  }
+  __syncthreads();
+  // stage 2: thread a handles kb = a + A r, r < B / A, an A-point DFT over a' each
+  float* out = Bt.f[f].out + row * N;
+#pragma unroll
+  for (int r = 0; r < B / A; ++r) {
+    const int kb = a + A * r;
+    float2 u[A];
+#pragma unroll
+    for (int aa = 0; aa < A; ++aa) u[aa] = sbuf[(l * B + kb) * LDT + aa];
+    DftReg<A, +1>::run(u, tw);
+#pragma unroll
+    for (int ka = 0; ka < A; ++ka) {
+      const int m = kb + B * ka;
+      reinterpret_cast<float2*>(out)[m] = u[ka];
+    }
+  }
+}
+
 template <int N>
 static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStream_t s, int* launches) {
   using G = Geo<N>;
@@ -385,7 +466,9 @@ static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStr
   BISP_CHECK_LAUNCH();
   k_inv_y<N><<<dim3(g.Pz / G::LB, N, b.nf), G::TS, s1, s>>>(t1, t2, tw);
   BISP_CHECK_LAUNCH();
-  k_inv_z<N><<<dim3(N * N / G::LBZ, b.nf), G::TZ, 0, s>>>(t2, tw);
+  using RZ = RegZ<N>;
+  smem_attr(k_inv_z_reg<N>, RZ::SMEM);
+  k_inv_z_reg<N><<<dim3(N * N / RZ::ROWS, b.nf), 256, RZ::SMEM, s>>>(t2, tw);
   BISP_CHECK_LAUNCH();
   if (launches) *launches += 3;
 }

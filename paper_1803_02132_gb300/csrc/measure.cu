@@ -9,6 +9,7 @@
 //    memory.  FP32 products in 4x4 register tiles, FP32 partials over at most 1024
 //    cells, FP64 above that; per-CTA partials are reduced in a fixed order.
 #include <algorithm>
+#include <cstdlib>
 #include <tuple>
 #include <vector>
 
@@ -165,10 +166,10 @@ void launch_zsum(const ZsumArgs& a, cudaStream_t s) {
 // memory; a second kernel reduces the slots in a fixed order.
 // ------------------------------------------------------------------------------------
 __constant__ PairJob c_pj;
-constexpr int PR_CH = 32;          // cells per chunk
+constexpr int PR_CH = 64;          // cells per chunk
 constexpr int PR_LD = PR_CH + 4;   // padded row (bank spread for 16-byte loads)
-constexpr int PR_FLUSH = 32;       // chunks per FP32 partial (<= 1024 cells)
-constexpr int PR_NSTAGE = 3;       // chunks staged ahead
+constexpr int PR_FLUSH = 16;       // chunks per FP32 partial (<= 1024 cells)
+constexpr int PR_NSTAGE = 2;       // chunks staged ahead
 constexpr int PR_MAXWARP = 16;
 
 struct PairLaunch {
@@ -194,11 +195,12 @@ static PairLaunch pair_launch_cfg(const PairJob& j) {
   if (j.nterm > 2 * PR_MAXWARP || (j.nterm > PR_MAXWARP && c.TM * c.TN > 18))
     throw Error{6, "pair reduction: too many terms for one CTA"};
   c.ksplit = 1;
-  while (c.ksplit < 2 && j.nterm * c.ksplit * 2 <= PR_MAXWARP) c.ksplit *= 2;  // slices of >= 16 cells
+  while (c.ksplit < 4 && j.nterm * c.ksplit * 2 <= PR_MAXWARP) c.ksplit *= 2;  // slices of >= 16 cells
   c.warps = j.nterm * c.ksplit;
   c.bs = j.ncomp | 1;  // odd rows per bin: consecutive bins fall on different banks
-  c.rows = c.nbp * c.bs + j.ng;
-  c.smem = ((size_t)PR_NSTAGE * c.rows * PR_LD + (size_t)j.nslot * c.nbp * PR_LD + (size_t)j.nh * PR_CH) *
+  c.rows = j.nb * c.bs + j.ng;  // padded bins (b >= nb) read a valid row; their outputs are dropped
+  c.smem = ((size_t)PR_NSTAGE * c.rows * PR_LD + (size_t)j.nslot * j.nb * PR_LD + (size_t)j.nh * PR_CH +
+            (size_t)(j.nb * j.ncomp + j.ng)) *
            sizeof(float);
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
@@ -332,9 +334,17 @@ static PairJob classify(const PairJob& job) {
   return j;
 }
 
+// the tensor-core contraction covers up to 32 bins; BISP_PAIR_FP32=1 forces the FP32 FMA kernel
+static bool pair_use_tc(const PairJob& j) {
+  const char* e = getenv("BISP_PAIR_FP32");
+  return j.nb <= 32 && !(e && e[0] == '1');
+}
+
 size_t pair_scratch_bytes(const PairJob& job) {
-  const PairLaunch c = pair_launch_cfg(classify(job));
-  return (size_t)c.nblk * c.warps * 32 * c.TM * c.TN * sizeof(double);
+  const PairJob j = classify(job);
+  const PairLaunch c = pair_launch_cfg(j);
+  const size_t per = pair_use_tc(j) ? 32 : (size_t)c.TM * c.TN;
+  return (size_t)c.nblk * c.warps * 32 * per * sizeof(double);
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -345,25 +355,69 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int NW>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW)); }
 
-// copy one chunk of every component row [b][comp] and G row into shared memory
-__device__ __forceinline__ void pair_stage(float* raw, int64_t x0, int nbp, int bs) {
+// copy one chunk of every component row [b][comp] and G row into shared memory;
+// rowmap[f] = destination row of source row f (f < nb*ncomp: field (b, comp); then G rows)
+__device__ __forceinline__ void pair_stage(float* raw, int64_t x0, const int* rowmap) {
+  const PairJob& J = c_pj;
+  constexpr int Q = PR_CH / 4;  // 16-byte pieces per row (a power of two)
+  constexpr int QS = Q == 16 ? 4 : (Q == 8 ? 3 : 2);
+  const int nraw = J.nb * J.ncomp;
+  const int n = (nraw + J.ng) << QS;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int f = i >> QS, q = i & (Q - 1);
+    const float* src = (f < nraw ? J.fields + (size_t)f * J.Ng : J.gfields + (size_t)(f - nraw) * J.Ng) + x0 + 4 * q;
+    cp_async16(raw + (size_t)rowmap[f] * PR_LD + 4 * q, src);
+  }
+}
+
+// built sides, block-wide: first the H rows of the chunk, H_h(x) = sum coef G_g(x) (shared by
+// all bins), then one thread per (side, bin, 4-cell quad): X(b, x) = sum_(c,h) P_c(b, x) H_h(x).
+// mnb = ceil(2^32 / nb): j / nb = umulhi(j, mnb) for the small j used here.
+__device__ __forceinline__ void pair_build_sides(const float* raw, float* mat, float* Hs, int bs, unsigned mnb) {
   const PairJob& J = c_pj;
   constexpr int Q = PR_CH / 4;
-  const int nraw = J.nb * J.ncomp;
-  const int n = (nraw + J.ng) * Q;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int f = i / Q, q = i % Q;
-    const float* src;
-    int row;
-    if (f < nraw) {
-      src = J.fields + (size_t)f * J.Ng + x0 + 4 * q;
-      const int b = f / J.ncomp;
-      row = b * bs + (f - b * J.ncomp);
-    } else {
-      src = J.gfields + (size_t)(f - nraw) * J.Ng + x0 + 4 * q;
-      row = nbp * bs + (f - nraw);
+  constexpr int QS = Q == 16 ? 4 : (Q == 8 ? 3 : 2);
+  const int grow0 = J.nb * bs;
+  for (int i = threadIdx.x; i < (J.nh << QS); i += blockDim.x) {
+    const int h = i >> QS, q = i & (Q - 1);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = J.h_off[h]; e < J.h_off[h + 1]; ++e) {
+      const PairRecipe R = J.h_ent[e];
+      if (R.g >= 0) {
+        const float4 gv = *reinterpret_cast<const float4*>(raw + (size_t)(grow0 + R.g) * PR_LD + 4 * q);
+        v.x = fmaf(R.coef, gv.x, v.x);
+        v.y = fmaf(R.coef, gv.y, v.y);
+        v.z = fmaf(R.coef, gv.z, v.z);
+        v.w = fmaf(R.coef, gv.w, v.w);
+      } else {
+        v.x += R.coef;
+        v.y += R.coef;
+        v.z += R.coef;
+        v.w += R.coef;
+      }
     }
-    cp_async16(raw + (size_t)row * PR_LD + 4 * q, src);
+    *reinterpret_cast<float4*>(Hs + (size_t)h * PR_CH + 4 * q) = v;
+  }
+  __syncthreads();
+  const int n = (J.nslot * J.nb) << QS;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned j = (unsigned)i >> QS;
+    const int q = i & (Q - 1);
+    const int sl = (int)__umulhi(j, mnb);
+    const int b = (int)j - sl * J.nb;
+    const float* rb = raw + (size_t)b * bs * PR_LD + 4 * q;
+    const float* hq = Hs + 4 * q;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e1 = J.s_off[sl + 1];
+    for (int e = J.s_off[sl]; e < e1; ++e) {
+      const float4 pv = *reinterpret_cast<const float4*>(rb + J.s_ent[e][0] * PR_LD);
+      const float4 hv = *reinterpret_cast<const float4*>(hq + J.s_ent[e][1] * PR_CH);
+      v.x = fmaf(pv.x, hv.x, v.x);
+      v.y = fmaf(pv.y, hv.y, v.y);
+      v.z = fmaf(pv.z, hv.z, v.z);
+      v.w = fmaf(pv.w, hv.w, v.w);
+    }
+    *reinterpret_cast<float4*>(mat + ((size_t)sl * J.nb + b) * PR_LD + 4 * q) = v;
   }
 }
 
@@ -371,14 +425,21 @@ template <int TM, int TN, int NTHR>
 __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int ksplit, double* partials) {
   const PairJob& J = c_pj;
   extern __shared__ __align__(16) float sh[];
-  float* mat = sh + (size_t)PR_NSTAGE * rows * PR_LD;  // [nslot][nbp][PR_LD], then H rows
-  const int grow0 = nbp * bs;
+  float* mat = sh + (size_t)PR_NSTAGE * rows * PR_LD;  // [nslot][nb][PR_LD]
+  float* Hs = mat + (size_t)J.nslot * J.nb * PR_LD;  // [nh][PR_CH]
+  int* rowmap = reinterpret_cast<int*>(Hs + (size_t)J.nh * PR_CH);
+  const unsigned mnb = (unsigned)((0x100000000ull + J.nb - 1) / J.nb);
   const int64_t nchunk = J.Ng / PR_CH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int t = warp / ksplit, ks = warp % ksplit;
   const int slice = PR_CH / ksplit;
   const int b1 = lane >> 3, b2 = lane & 7;  // rows b1 + 4 i and b2 + 8 j
   const PairTermDesc T = J.term[t];
+  for (int f = threadIdx.x; f < J.nb * J.ncomp + J.ng; f += blockDim.x) {
+    const int nraw = J.nb * J.ncomp;
+    rowmap[f] = f < nraw ? (f / J.ncomp) * bs + f % J.ncomp : J.nb * bs + (f - nraw);
+  }
+  __syncthreads();
   double* slot = partials + (((size_t)blockIdx.x * nwarp + warp) * 32 + lane) * (TM * TN);
 #pragma unroll
   for (int q = 0; q < TM * TN; ++q) slot[q] = 0.0;
@@ -387,108 +448,62 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
-  // prologue: the first PR_NSTAGE - 1 chunks
-  int64_t chs[PR_NSTAGE];
-#pragma unroll
-  for (int s = 0; s < PR_NSTAGE - 1; ++s) {
-    chs[s] = blockIdx.x + (int64_t)s * gridDim.x;
-    if (chs[s] < nchunk) pair_stage(sh + (size_t)s * rows * PR_LD, chs[s] * PR_CH, nbp, bs);
-    cp_async_commit();
-  }
+  if (blockIdx.x < nchunk) pair_stage(sh, (int64_t)blockIdx.x * PR_CH, rowmap);
+  cp_async_commit();
   int since_flush = 0, stage = 0;
   for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
-    cp_async_wait<PR_NSTAGE - 2>();
-    __syncthreads();  // chunk ch has landed; every warp is done with the previous chunk
+    cp_async_wait<0>();
+    __syncthreads();
     {
-      const int64_t nx = ch + (int64_t)(PR_NSTAGE - 1) * gridDim.x;
-      const int ns = (stage + PR_NSTAGE - 1) % PR_NSTAGE;
-      if (nx < nchunk) pair_stage(sh + (size_t)ns * rows * PR_LD, nx * PR_CH, nbp, bs);
+      const int64_t nx = ch + gridDim.x;
+      if (nx < nchunk) pair_stage(sh + (size_t)(stage ^ 1) * rows * PR_LD, nx * PR_CH, rowmap);
       cp_async_commit();
     }
     const float* raw = sh + (size_t)stage * rows * PR_LD;
-    // built sides: H_h(x) = sum coef G_g(x) (shared by all bins), then
-    // mat[slot][b][x] = sum_(c,h) P_c(b, x) H_h(x); four cells per thread
     if (J.nslot) {
-      float* Hs = mat + (size_t)J.nslot * nbp * PR_LD;  // [nh][PR_CH]
-      constexpr int Q = PR_CH / 4;
-      for (int i = threadIdx.x; i < J.nh * Q; i += blockDim.x) {
-        const int h = i / Q, q = i % Q;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int e = J.h_off[h]; e < J.h_off[h + 1]; ++e) {
-          const PairRecipe R = J.h_ent[e];
-          if (R.g >= 0) {
-            const float4 gv = *reinterpret_cast<const float4*>(raw + (size_t)(grow0 + R.g) * PR_LD + 4 * q);
-            v.x = fmaf(R.coef, gv.x, v.x);
-            v.y = fmaf(R.coef, gv.y, v.y);
-            v.z = fmaf(R.coef, gv.z, v.z);
-            v.w = fmaf(R.coef, gv.w, v.w);
-          } else {
-            v.x += R.coef;
-            v.y += R.coef;
-            v.z += R.coef;
-            v.w += R.coef;
-          }
-        }
-        *reinterpret_cast<float4*>(Hs + (size_t)h * PR_CH + 4 * q) = v;
-      }
-      __syncthreads();
-      const int per_slot = J.nb * Q;
-      for (int i = threadIdx.x; i < J.nslot * per_slot; i += blockDim.x) {
-        const int sl = i / per_slot, r = i - sl * per_slot;
-        const int b = r / Q, q = r % Q;
-        const float* rb = raw + (size_t)b * bs * PR_LD + 4 * q;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int e = J.s_off[sl]; e < J.s_off[sl + 1]; ++e) {
-          const int c = J.s_ent[e][0], h = J.s_ent[e][1];
-          const float4 pv = *reinterpret_cast<const float4*>(rb + (size_t)c * PR_LD);
-          const float4 hv = *reinterpret_cast<const float4*>(Hs + (size_t)h * PR_CH + 4 * q);
-          v.x = fmaf(pv.x, hv.x, v.x);
-          v.y = fmaf(pv.y, hv.y, v.y);
-          v.z = fmaf(pv.z, hv.z, v.z);
-          v.w = fmaf(pv.w, hv.w, v.w);
-        }
-        *reinterpret_cast<float4*>(mat + ((size_t)sl * nbp + b) * PR_LD + 4 * q) = v;
-      }
+      pair_build_sides(raw, mat, Hs, bs, mnb);
       __syncthreads();
     }
-    const float* xr;
-    const float* yr;
-    int sx, sy;
-    if (T.xdir >= 0) {
-      xr = raw + (size_t)(b1 * bs + T.xdir) * PR_LD;
-      sx = 4 * bs * PR_LD;
-    } else {
-      xr = mat + ((size_t)T.xslot * nbp + b1) * PR_LD;
-      sx = 4 * PR_LD;
+    // row pointers of this lane's bins b1 + 4 i and b2 + 8 j (clamped to a valid row)
+    const float* xrow[TM];
+    const float* yrow[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int b = min(b1 + 4 * i, J.nb - 1);
+      xrow[i] = (T.xdir >= 0 ? raw + (size_t)(b * bs + T.xdir) * PR_LD : mat + ((size_t)T.xslot * J.nb + b) * PR_LD) +
+                ks * slice;
     }
-    if (T.ydir >= 0) {
-      yr = raw + (size_t)(b2 * bs + T.ydir) * PR_LD;
-      sy = 8 * bs * PR_LD;
-    } else {
-      yr = mat + ((size_t)T.yslot * nbp + b2) * PR_LD;
-      sy = 8 * PR_LD;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int b = min(b2 + 8 * j, J.nb - 1);
+      yrow[j] = (T.ydir >= 0 ? raw + (size_t)(b * bs + T.ydir) * PR_LD : mat + ((size_t)T.yslot * J.nb + b) * PR_LD) +
+                ks * slice;
     }
-    xr += ks * slice;
-    yr += ks * slice;
     for (int xb = 0; xb < slice; xb += 16) {
 #pragma unroll
       for (int x = xb; x < xb + 16; x += 4) {
         float4 a[TM], c[TN];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = *reinterpret_cast<const float4*>(xr + i * sx + x);
+        for (int i = 0; i < TM; ++i) a[i] = *reinterpret_cast<const float4*>(xrow[i] + x);
 #pragma unroll
-        for (int j = 0; j < TN; ++j) c[j] = *reinterpret_cast<const float4*>(yr + j * sy + x);
+        for (int j = 0; j < TN; ++j) c[j] = *reinterpret_cast<const float4*>(yrow[j] + x);
+        // component-outer order: consecutive FMAs update different accumulators
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < TN; ++j) {
-            float s = acc[i][j];
-            s = fmaf(a[i].x, c[j].x, s);
-            s = fmaf(a[i].y, c[j].y, s);
-            s = fmaf(a[i].z, c[j].z, s);
-            s = fmaf(a[i].w, c[j].w, s);
-            acc[i][j] = s;
-          }
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i].x, c[j].x, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i].y, c[j].y, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i].z, c[j].z, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i].w, c[j].w, acc[i][j]);
       }
     }
     if (++since_flush == PR_FLUSH || ch + gridDim.x >= nchunk) {
@@ -501,9 +516,152 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int
           acc[i][j] = 0.f;
         }
     }
-    stage = (stage + 1) % PR_NSTAGE;
+    stage ^= 1;
   }
   cp_async_wait<0>();
+}
+
+// ------------------------------------------------------------------------------------
+// Tensor-core variant of the contraction (nb <= 32): per warp and term, C (32 x 32 bins)
+// += X (32 bins x cells) Y^T with mma.sync m16n8k8 TF32 in three passes (split FP32 values
+// v = hi + lo, hi and lo TF32: X_hi Y_hi + X_hi Y_lo + X_lo Y_hi), which keeps FP32-level
+// accuracy.  The MMA accumulators restart from zero every chunk; chunk results are added
+// with FP32 round-to-nearest adds and flushed to FP64 as in k_pair.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_hi(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float v, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_hi(v);
+  lo = tf32_hi(v - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int NTHR>
+__global__ void __launch_bounds__(NTHR, 1) k_pair_tc(int nbp, int bs, int rows, int ksplit, double* partials) {
+  const PairJob& J = c_pj;
+  extern __shared__ __align__(16) float sh[];
+  float* mat = sh + (size_t)PR_NSTAGE * rows * PR_LD;  // [nslot][nb][PR_LD]
+  float* Hs = mat + (size_t)J.nslot * J.nb * PR_LD;  // [nh][PR_CH]
+  int* rowmap = reinterpret_cast<int*>(Hs + (size_t)J.nh * PR_CH);
+  const unsigned mnb = (unsigned)((0x100000000ull + J.nb - 1) / J.nb);
+  const int64_t nchunk = J.Ng / PR_CH;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = warp / ksplit, ks = warp % ksplit;
+  const int slice = PR_CH / ksplit;
+  const int g = lane >> 2, tq = lane & 3;
+  const PairTermDesc T = J.term[t];
+  for (int f = threadIdx.x; f < J.nb * J.ncomp + J.ng; f += blockDim.x) {
+    const int nraw = J.nb * J.ncomp;
+    rowmap[f] = f < nraw ? (f / J.ncomp) * bs + f % J.ncomp : J.nb * bs + (f - nraw);
+  }
+  __syncthreads();
+  double* slot = partials + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * 32;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) slot[q] = 0.0;
+  float run[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) run[q] = 0.f;
+  if (blockIdx.x < nchunk) pair_stage(sh, (int64_t)blockIdx.x * PR_CH, rowmap);
+  cp_async_commit();
+  int since_flush = 0, stage = 0;
+  for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    cp_async_wait<0>();
+    __syncthreads();
+    {
+      const int64_t nx = ch + gridDim.x;
+      if (nx < nchunk) pair_stage(sh + (size_t)(stage ^ 1) * rows * PR_LD, nx * PR_CH, rowmap);
+      cp_async_commit();
+    }
+    const float* raw = sh + (size_t)stage * rows * PR_LD;
+    if (J.nslot) {
+      pair_build_sides(raw, mat, Hs, bs, mnb);
+      __syncthreads();
+    }
+    // rows of the fragments: A rows b1 = 16 mi + g (+8), B rows b2 = 8 ni + g (clamped)
+    const float* ar[4];
+    const float* br[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int b = min(8 * r + g, J.nb - 1);
+      ar[r] = (T.xdir >= 0 ? raw + (size_t)(b * bs + T.xdir) * PR_LD : mat + ((size_t)T.xslot * J.nb + b) * PR_LD) +
+              ks * slice + tq;
+      br[r] = (T.ydir >= 0 ? raw + (size_t)(b * bs + T.ydir) * PR_LD : mat + ((size_t)T.yslot * J.nb + b) * PR_LD) +
+              ks * slice + tq;
+    }
+    float c[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) c[q] = 0.f;
+    for (int k0 = 0; k0 < slice; k0 += 8) {
+      uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        split_tf32(ar[2 * mi][k0], ah[mi][0], al[mi][0]);
+        split_tf32(ar[2 * mi + 1][k0], ah[mi][1], al[mi][1]);
+        split_tf32(ar[2 * mi][k0 + 4], ah[mi][2], al[mi][2]);
+        split_tf32(ar[2 * mi + 1][k0 + 4], ah[mi][3], al[mi][3]);
+      }
+#pragma unroll
+      for (int ni = 0; ni < 4; ++ni) {
+        split_tf32(br[ni][k0], bh[ni][0], bl[ni][0]);
+        split_tf32(br[ni][k0 + 4], bh[ni][1], bl[ni][1]);
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni) {
+          float* cc = c + (mi * 4 + ni) * 4;
+          mma_tf32(cc, al[mi], bh[ni]);
+          mma_tf32(cc, ah[mi], bl[ni]);
+          mma_tf32(cc, ah[mi], bh[ni]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) run[q] += c[q];
+    if (++since_flush == PR_FLUSH || ch + gridDim.x >= nchunk) {
+      since_flush = 0;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        slot[q] += (double)run[q];
+        run[q] = 0.f;
+      }
+    }
+    stage ^= 1;
+  }
+  cp_async_wait<0>();
+}
+
+// final reduction for k_pair_tc: bin (b1, b2) of term t sits in warp t*ksplit+ks, lane
+// (b1%8)*4 + (b2%8)/2, register ((b1/16)*4 + b2/8)*4 + ((b1/8)%2)*2 + b2%2
+__global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int ksplit, int nb, int nout,
+                                double* out) {
+  const PairJob& J = c_pj;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= nout * nb * nb) return;
+  const int o = gw / (nb * nb), b1 = (gw / nb) % nb, b2 = gw % nb;
+  const int ln = (b1 % 8) * 4 + (b2 % 8) / 2;
+  const int q = ((b1 / 16) * 4 + b2 / 8) * 4 + ((b1 / 8) % 2) * 2 + (b2 % 2);
+  double tot = 0.0;
+  for (int e = J.out_ent_off[o]; e < J.out_ent_off[o + 1]; ++e) {
+    const int t = J.out_ent_term[e];
+    double s = 0.0;
+    for (int ks = 0; ks < ksplit; ++ks) {
+      const int w = t * ksplit + ks;
+      for (int c = lane; c < nblk; c += 32) s += partials[(((size_t)c * warps + w) * 32 + ln) * 32 + q];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    tot += J.out_ent_mult[e] * s;
+  }
+  if (lane == 0) out[gw] = tot;
 }
 
 // out[o][b1][b2] = sum over terms of o, then CTAs and x slices in a fixed order; one warp
@@ -539,6 +697,23 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
   if (c.smem > 227 * 1024) throw Error{6, "pair reduction: shared memory budget exceeded"};
   BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &j, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
   double* partials = reinterpret_cast<double*>(scratch);
+  if (pair_use_tc(j)) {
+    const int nthr = c.warps * 32;
+    if (nthr <= 512) {
+      BISP_CUDA(cudaFuncSetAttribute(k_pair_tc<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+      k_pair_tc<512><<<c.nblk, nthr, c.smem, s>>>(c.nbp, c.bs, c.rows, c.ksplit, partials);
+    } else {
+      BISP_CUDA(cudaFuncSetAttribute(k_pair_tc<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem));
+      k_pair_tc<1024><<<c.nblk, nthr, c.smem, s>>>(c.nbp, c.bs, c.rows, c.ksplit, partials);
+    }
+    BISP_CHECK_LAUNCH();
+    const int nout = j.nout * j.nb * j.nb;
+    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(partials, c.nblk, c.warps, c.ksplit, j.nb, j.nout,
+                                                            out_dev);
+    BISP_CHECK_LAUNCH();
+    if (launches) *launches += 2;
+    return;
+  }
 #define BISP_PAIR3(A, B, NT)                                                                              \
   if (c.TM == A && c.TN == B && c.warps * 32 <= NT) {                                                   \
     BISP_CUDA(cudaFuncSetAttribute(k_pair<A, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem)); \
