@@ -452,6 +452,85 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
   }
 }
 
+// ------------------------------------------------------------------------------------
+// Register four-step FFT of LB interleaved complex lines of NF points (strided passes):
+// thread (line l = tid % LB, a = tid / LB) holds x[a + A b], b < B; B-point DFTs in
+// registers, twiddle e^{SIGN 2 pi i a kb / NF}, transpose through shared memory laid out
+// [kb][a][l], A-point DFTs; output m = kb + B ka.
+// ------------------------------------------------------------------------------------
+__host__ __device__ constexpr int regl_a(int nf) {
+  return nf >= 1024 ? 32 : (nf >= 256 ? 16 : (nf >= 64 ? 8 : (nf >= 32 ? 4 : 2)));
+}
+template <int N>
+struct RegL {
+  static constexpr int LB = Geo<N>::LB;
+  static constexpr int A = regl_a(N);
+  static constexpr int B = N / A;
+  static constexpr int THREADS = LB * A;
+  static constexpr size_t SMEM = ((size_t)B * A * LB + N) * sizeof(float2);
+};
+
+// stage 2 + output: the caller has written v (after stage 1 and the twiddle) into s
+template <int N, int SIGN, class Store>
+__device__ __forceinline__ void regl_finish(const float2* s, int l, int a, const Store& store) {
+  constexpr int A = RegL<N>::A, B = RegL<N>::B, LB = RegL<N>::LB;
+#pragma unroll
+  for (int r = 0; r < B / A; ++r) {
+    const int kb = a + A * r;
+    float2 u[A];
+#pragma unroll
+    for (int aa = 0; aa < A; ++aa) u[aa] = s[(kb * A + aa) * LB + l];
+    DftReg<A, SIGN>::run(u, nullptr);
+#pragma unroll
+    for (int ka = 0; ka < A; ++ka) store(kb + B * ka, u[ka]);
+  }
+}
+
+template <int N, int SIGN>
+__device__ __forceinline__ void regl_stage1(float2* v, float2* s, const float2* wtab, int l, int a) {
+  constexpr int A = RegL<N>::A, B = RegL<N>::B, LB = RegL<N>::LB;
+  DftReg<B, SIGN>::run(v, nullptr);
+#pragma unroll
+  for (int kb = 0; kb < B; ++kb) s[(kb * A + a) * LB + l] = cmul(v[kb], wtab[(a * kb) & (N - 1)]);
+}
+
+// twiddle table e^{SIGN 2 pi i j / N} in shared memory
+template <int N, int SIGN>
+__device__ __forceinline__ void regl_twiddles(float2* wtab, const float2* __restrict__ tw) {
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float2 w = tw[(j * (BISP_TWN / N)) & (BISP_TWN - 1)];
+    if (SIGN > 0) w.y = -w.y;
+    wtab[j] = w;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(RegL<N>::THREADS) k_inv_y_reg(const float2* t1all, float2* t2all,
+                                                                  const float2* __restrict__ tw) {
+  constexpr int A = RegL<N>::A, B = RegL<N>::B, LB = RegL<N>::LB;
+  extern __shared__ float2 sm[];
+  float2* s = sm;
+  float2* wtab = sm + (size_t)B * A * LB;
+  regl_twiddles<N, +1>(wtab, tw);
+  const InvBatch& Bt = c_inv;
+  const InvGeo g = inv_geo(N, Bt.P, LB);
+  const int nz0 = blockIdx.x * LB, x = blockIdx.y, f = blockIdx.z;
+  const int l = threadIdx.x % LB, a = threadIdx.x / LB;
+  const float2* t1 = t1all + (size_t)f * g.t1 + (size_t)x * g.ny * g.Pz + nz0 + l;
+  float2 v[B];
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int n = a + A * b;
+    const int sy = sgn_idx(n, N);
+    v[b] = (sy >= -g.P && sy <= g.P) ? t1[(size_t)(sy + g.P) * g.Pz] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();  // twiddle table ready
+  regl_stage1<N, +1>(v, s, wtab, l, a);
+  __syncthreads();
+  float2* t2 = t2all + (size_t)f * g.t2 + (size_t)x * N * g.Pz + nz0 + l;
+  regl_finish<N, +1>(s, l, a, [&](int m, float2 u) { t2[(size_t)m * g.Pz] = u; });
+}
+
 template <int N>
 static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStream_t s, int* launches) {
   using G = Geo<N>;
@@ -459,12 +538,13 @@ static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStr
   float2* t1 = reinterpret_cast<float2*>(scratch);
   float2* t2 = t1 + (size_t)b.nf * g.t1;
   BISP_CUDA(cudaMemcpyToSymbolAsync(c_inv, &b, sizeof(InvBatch), 0, cudaMemcpyHostToDevice, s));
+  using RL = RegL<N>;
   const size_t s1 = (size_t)N * G::LB * sizeof(float2);
   smem_attr(k_inv_x<N>, s1);
-  smem_attr(k_inv_y<N>, s1);
+  smem_attr(k_inv_y_reg<N>, RL::SMEM);
   k_inv_x<N><<<dim3(g.Pz / G::LB, g.ny), G::TS, s1, s>>>(t1, tw);
   BISP_CHECK_LAUNCH();
-  k_inv_y<N><<<dim3(g.Pz / G::LB, N, b.nf), G::TS, s1, s>>>(t1, t2, tw);
+  k_inv_y_reg<N><<<dim3(g.Pz / G::LB, N, b.nf), RL::THREADS, RL::SMEM, s>>>(t1, t2, tw);
   BISP_CHECK_LAUNCH();
   using RZ = RegZ<N>;
   smem_attr(k_inv_z_reg<N>, RZ::SMEM);
