@@ -16,6 +16,7 @@ independent realisation (replicas; no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -198,29 +199,56 @@ def run_gpu(args, w, rank, world):
     pair_ms_avg = sum(ms_pair) / max(pair_launches, 1)
     pair_gbs = (pair_bytes / max(pair_launches, 1)) / (pair_ms_avg / 1e3) / 1e9 if pair_ms_avg > 0 else None
     out = {
-        "metric": "B_l1l2L(k1,k2) bins/s at 512^3 (local LOS, B000+B202+B112 + window)"
-        if w["N"] == 512 else f"B_l1l2L(k1,k2) bins/s at {w['N']}^3",
+        "metric": metric_name(w),
         "value": value, "unit": "bins/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (FP64 accumulation)", "data": "synthetic",
-        "config": {"workload": args.workload, "nmesh": w["N"], "box_len": w["L"], "nbins": len(w["edges"]) - 1,
-                   "ells": w["ells"], "n_gal": w.get("n_gal", w.get("n_p")), "n_ran": w.get("n_ran", 0),
-                   "bins_per_step": nbins, "los": "local" if w["kind"] == "survey" else "global",
-                   "mas": w["mas"], "interlace": w["interlace"], "window": w["window"],
-                   "l2": "inputs larger than L2 (meshes and fields of 0.5 GB each)",
-                   "parallelism": f"replicas x{world}"},
+        "config": config_of(args.workload, w, world),
         "e2e": {"value": world * nbins / (ms_e2e / args.steps / 1e3), "unit": "bins/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": "k_pair (mesh sum of F F G)", "achieved": pair_gbs,
-                     "peak": hbm, "unit": "GB/s", "frac": (pair_gbs / hbm) if pair_gbs else None,
-                     "traffic": None, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
-                     else "fallback 6800 GB/s"},
+        "roofline": {"bound": "hbm", "kernel": "k_pair_tc (mesh sum of F F G, Eq. bi_estimator_FFTs)",
+                     "achieved": pair_gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": (pair_gbs / hbm) if pair_gbs else None,
+                     "traffic": pair_traffic(pair_bytes / max(pair_launches, 1)),
+                     "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
+                     else "of fallback 6800 GB/s"},
         "stages_ms": {"assign_data": info["ms_assign_data"], "assign_randoms": info["ms_assign_randoms"],
                       "measure": info["ms_measure"], "pair": info["ms_pair"]},
         "clocks": clk,
     }
     return out
+
+
+def metric_name(w):
+    los = "local LOS" if w["kind"] == "survey" else "global LOS"
+    mult = "+".join("B%d%d%d" % tuple(e) for e in w["ells"]) + (" + window" if w["window"] else "")
+    return f"B_l1l2L(k1,k2) bins/s at {w['N']}^3 ({los}, {mult})"
+
+
+def config_of(name, w, world):
+    nb = len(w["edges"]) - 1
+    return {"workload": name, "nmesh": w["N"], "box_len": w["L"], "nbins": nb,
+            "ells": w["ells"], "n_gal": w.get("n_gal", w.get("n_p")), "n_ran": w.get("n_ran", 0),
+            "bins_per_step": n_bins_output(w), "los": "local" if w["kind"] == "survey" else "global",
+            "mas": w["mas"], "interlace": w["interlace"], "window": w["window"],
+            "l2": "inputs larger than L2 (meshes and fields of 0.5 GB each)" if w["N"] >= 256
+            else "working set of a few hundred MB (no flush)",
+            "parallelism": f"replicas x{world}"}
+
+
+def pair_traffic(alg_bytes_per_launch):
+    """DRAM bytes per k_pair_tc launch: the measured DRAM/algorithmic ratio of a small-case
+    ncu capture of the same kernel, times this launch's algorithmic bytes (traffic grows with
+    the number of mesh cells).  None when the kernel source changed since the capture."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_pair_tc_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_1803_02132_gb300", "csrc", "measure.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["dram_bytes_per_algorithmic_byte"] * alg_bytes_per_launch
+    except Exception:
+        return None
 
 
 def cpu_baseline(args, w):
@@ -248,20 +276,22 @@ def cpu_baseline(args, w):
         p = E.Params(N=N, L=L, edges=edges, ells=w["ells"], los="global",
                      mas={"NGP": 1, "CIC": 2, "TSC": 3}[w["mas"]], interlace=w["interlace"])
     t0 = time.perf_counter()
+    c0 = time.process_time()
     E.measure(p, gal, ran)
     dt = time.perf_counter() - t0
+    cpu = time.process_time() - c0
     nb = len(edges) - 1
     nbins = sum(nb * (nb + 1) // 2 if l1 == l2 else nb * nb for (l1, l2, _) in w["ells"]) * (2 if w["window"] else 1)
-    cores = 1
-    try:
-        import threadpoolctl
-        cores = max(1, max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1)
-    except Exception:
-        pass
-    return {"value": nbins / dt, "unit": "bins/s", "cores": cores, "kind": "oracle",
+    # threads actually used: process CPU time over wall time (numpy's FFT and bincount run on
+    # one thread; BLAS calls may use more)
+    cores = max(1, int(round(cpu / dt)))
+    # in the metric's unit: the oracle's cost per output bin grows with the number of mesh
+    # cells, so the sample's rate is scaled by the cell ratio to the workload's mesh
+    return {"value": nbins / dt * frac, "unit": "bins/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle on the same recipe at {N}^3 (1/{int(round(1 / frac))} of the cells and particles), "
-                      f"{nb} bins below that mesh's Nyquist, {nbins} bins in {dt:.1f} s",
-            "seconds": dt}
+                      f"{nb} bins below that mesh's Nyquist, {nbins} bins in {dt:.1f} s "
+                      f"({nbins / dt:.3g} bins/s at {N}^3); value = that rate x {N}^3/{w['N']}^3",
+            "sample_bins_per_s": nbins / dt, "seconds": dt, "cpu_seconds": cpu}
 
 
 def main():
@@ -288,9 +318,10 @@ def main():
         v = float(np.mean([c["value"] for c in vals]))
         cb = dict(vals[-1])
         cb["value"] = v
-        print(json.dumps({"impl": "reference", "metric": "B_l1l2L(k1,k2) bins/s (FP64 CPU oracle, bounded sample)",
-                          "value": v, "unit": "bins/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-                          "higher_is_better": True, "config": {"workload": args.workload}, "cpu_baseline": cb,
+        print(json.dumps({"impl": "reference", "metric": metric_name(w),
+                          "value": v, "unit": "bins/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": config_of(args.workload, w, world), "cpu_baseline": cb,
                           "e2e": {"value": v, "unit": "bins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                           "seconds": time.perf_counter() - t0}))
         return

@@ -21,7 +21,7 @@ only library primitive used as a step):
 It also evaluates the same estimator as the mode sum over triangles (Eq. bi_estimator,
 "direct mode") and, for a handful of particles, with exact DFTs ("particle-exact mode").
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled (the CUDA path takes the same ones):
 * bins are [e_b, e_{b+1}) in k = kF sqrt(|n|^2), decided in FP64; modes on a Nyquist
   plane (any |n_i| = N/2) and k = 0 are in no bin; N_mode counts the full cube;
 * every spectrum is zero on the Nyquist planes (the interlaced combination is not

@@ -14,7 +14,7 @@ import paper_1803_02132_gb300 as bisp  # noqa: E402
 import synthcat  # noqa: E402
 from oracle import estimator as E  # noqa: E402
 
-# the benchmark spec tolerance: per multipole, max relative error <= 1e-4 over bins with
+# tolerance: per multipole, max relative error <= 1e-4 over bins with
 # |B| > 1% of the multipole's maximum |B|
 TOL = 1e-4
 
