@@ -1,0 +1,909 @@
+// The mesh sum of Eq. bi_estimator_FFTs (Sec. 4.2), contracted over the (m1, m2, M) terms
+// of the real expansion:  out[o][b1][b2] = sum_x sum_{t in o} X_t(x; b1) Y_t(x; b2), where
+// each side is either one filtered component field F_c(x; b) ("bare") or a small
+// combination sum_(c,h) F_c(x; b) H_h(x) with H_h = sum_g coef G_g ("built").
+//  * k_pair_tma: bins <= 32.  TMA tensor-map loads (128-byte swizzle, mbarrier completion)
+//    stage 64-cell chunks of every field in shared memory; built sides are formed there;
+//    each warp multiplies its term's X and Y tiles with mma.sync m16n8k8 TF32 in three
+//    passes (v = hi + lo split, X_hi Y_hi + X_hi Y_lo + X_lo Y_hi: FP32-class products).
+//  * k_pair: any bin count up to 40, FP32 FMA register tiles (fallback).
+// Both keep FP32 partial sums over at most 1024 cells and FP64 above that; per-CTA partials
+// are reduced in a fixed order, so results are bit-reproducible.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace bisp {
+
+// ------------------------------------------------------------------------------------
+// pair reduction
+//   out[o][b1][b2] = sum_x sum_{t in o} X_t(x; b1) Y_t(x; b2)
+// Each CTA streams chunks of PR_CH cells.  All component fields and G fields of a chunk
+// are copied to shared memory with 16-byte cp.async, PR_NSTAGE chunks in flight.  Sides
+// that are combinations of fields are built in shared memory; bare component sides are
+// read in place.  One warp owns one (term, x slice): its 32 lanes form a 4 x 8 grid and
+// each lane holds a TM x TN register tile of (b1, b2), so the warp covers 4TM x 8TN bins.
+// FP32 partials over at most PR_FLUSH chunks are added to lane-owned FP64 slots in global
+// memory; a second kernel reduces the slots in a fixed order.
+// ------------------------------------------------------------------------------------
+__constant__ PairJob c_pj;
+constexpr int PR_CH = 64;          // cells per chunk
+constexpr int PR_LD = PR_CH + 4;   // padded row (bank spread for 16-byte loads)
+constexpr int PR_FLUSH = 16;       // chunks per FP32 partial (<= 1024 cells)
+constexpr int PR_NSTAGE = 2;       // chunks staged ahead
+constexpr int PR_MAXWARP = 16;
+
+struct PairLaunch {
+  int TM, TN, nbp, bs, ksplit, warps, nblk, rows;
+  size_t smem;
+};
+
+static void pick_tile(int nb, int* TM, int* TN) {
+  static const int tab[][2] = {{1, 1}, {2, 1}, {3, 2}, {4, 2}, {5, 3}, {6, 3}, {7, 4}, {8, 4}, {10, 5}};
+  for (auto& t : tab)
+    if (4 * t[0] >= nb && 8 * t[1] >= nb) {
+      *TM = t[0];
+      *TN = t[1];
+      return;
+    }
+  throw Error{6, "pair reduction: more than 40 bins"};
+}
+
+static PairLaunch pair_launch_cfg(const PairJob& j) {
+  PairLaunch c;
+  pick_tile(j.nb, &c.TM, &c.TN);
+  c.nbp = std::max(4 * c.TM, 8 * c.TN);
+  if (j.nterm > 2 * PR_MAXWARP || (j.nterm > PR_MAXWARP && c.TM * c.TN > 18))
+    throw Error{6, "pair reduction: too many terms for one CTA"};
+  c.ksplit = 1;
+  while (c.ksplit < 4 && j.nterm * c.ksplit * 2 <= PR_MAXWARP) c.ksplit *= 2;  // slices of >= 16 cells
+  c.warps = j.nterm * c.ksplit;
+  c.bs = j.ncomp | 1;  // odd rows per bin: consecutive bins fall on different banks
+  c.rows = j.nb * c.bs + j.ng;  // padded bins (b >= nb) read a valid row; their outputs are dropped
+  c.smem = ((size_t)PR_NSTAGE * c.rows * PR_LD + (size_t)j.nslot * j.nb * PR_LD + (size_t)j.nh * PR_CH +
+            (size_t)(j.nb * j.ncomp + j.ng)) *
+           sizeof(float);
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  c.nblk = nsm;
+  return c;
+}
+
+// merge terms equal up to a scalar, then classify the sides of every term: bare component
+// field (read in place) or built
+static PairJob classify(const PairJob& job) {
+  PairJob j = job;
+  {
+    // normalised term: a single-entry X side (c, g, coef) with a bare Y side is coef times
+    // the unit term (c, g, 1 | Y); other terms are kept as they are (multiplier 1)
+    struct Key {
+      std::vector<std::tuple<int, int, float>> x, y;
+      bool operator==(const Key& o) const { return x == o.x && y == o.y; }
+    };
+    std::vector<Key> keys;
+    std::vector<PairTermDesc> nterm;
+    std::vector<PairRecipe> nrec;
+    int ne = 0;
+    for (int o = 0; o < j.nout; ++o) {
+      j.out_ent_off[o] = ne;
+      for (int t = job.out_term_off[o]; t < job.out_term_off[o + 1]; ++t) {
+        const PairTermDesc& T = job.term[t];
+        Key k;
+        double mult = 1.0;
+        for (int e = 0; e < T.xcnt; ++e) {
+          const PairRecipe& R = job.rec[T.xoff + e];
+          k.x.push_back({R.comp, R.g, R.coef});
+        }
+        for (int e = 0; e < T.ycnt; ++e) {
+          const PairRecipe& R = job.rec[T.yoff + e];
+          k.y.push_back({R.comp, R.g, R.coef});
+        }
+        auto bare_y = [&]() { return k.y.size() == 1 && std::get<1>(k.y[0]) < 0 && std::get<2>(k.y[0]) == 1.0f; };
+        if (k.x.size() == 1 && bare_y()) {
+          mult = std::get<2>(k.x[0]);
+          std::get<2>(k.x[0]) = 1.0f;
+        }
+        int u = -1;
+        for (size_t i = 0; i < keys.size(); ++i)
+          if (keys[i] == k) u = (int)i;
+        if (u < 0) {
+          u = (int)keys.size();
+          keys.push_back(k);
+          PairTermDesc d{};
+          d.xoff = (int)nrec.size();
+          d.xcnt = (int)k.x.size();
+          for (auto& r : k.x) nrec.push_back({std::get<0>(r), std::get<1>(r), std::get<2>(r)});
+          d.yoff = (int)nrec.size();
+          d.ycnt = (int)k.y.size();
+          for (auto& r : k.y) nrec.push_back({std::get<0>(r), std::get<1>(r), std::get<2>(r)});
+          nterm.push_back(d);
+        }
+        if (ne >= 128) throw Error{6, "pair reduction: too many output entries"};
+        j.out_ent_term[ne] = u;
+        j.out_ent_mult[ne] = mult;
+        ++ne;
+      }
+    }
+    j.out_ent_off[j.nout] = ne;
+    if (nterm.size() > 64 || nrec.size() > 512) throw Error{6, "pair reduction: recipe tables overflow"};
+    j.nterm = (int)nterm.size();
+    for (int t = 0; t < j.nterm; ++t) j.term[t] = nterm[t];
+    j.nrec = (int)nrec.size();
+    for (int r = 0; r < j.nrec; ++r) j.rec[r] = nrec[r];
+  }
+  j.nslot = 0;
+  for (int t = 0; t < j.nterm; ++t) {
+    PairTermDesc& T = j.term[t];
+    auto bare = [&](int off, int cnt) {
+      return cnt == 1 && j.rec[off].g < 0 && j.rec[off].coef == 1.0f ? j.rec[off].comp : -1;
+    };
+    T.xdir = bare(T.xoff, T.xcnt);
+    T.ydir = bare(T.yoff, T.ycnt);
+    T.xslot = T.xdir >= 0 ? -1 : j.nslot++;
+    T.yslot = T.ydir >= 0 ? -1 : j.nslot++;
+  }
+  // factor every built side by component: H rows shared between sides when identical
+  std::vector<std::vector<std::pair<int, float>>> rows;
+  j.nh = 0;
+  int ns = 0, nse = 0;
+  for (int t = 0; t < j.nterm; ++t)
+    for (int side = 0; side < 2; ++side) {
+      const PairTermDesc& T = j.term[t];
+      const int slot = side ? T.yslot : T.xslot;
+      if (slot < 0) continue;
+      if (slot != ns) throw Error{6, "pair reduction: slot order"};
+      j.s_off[ns] = nse;
+      const int off = side ? T.yoff : T.xoff, cnt = side ? T.ycnt : T.xcnt;
+      std::vector<int> comps;
+      for (int e = 0; e < cnt; ++e)
+        if (std::find(comps.begin(), comps.end(), j.rec[off + e].comp) == comps.end()) comps.push_back(j.rec[off + e].comp);
+      for (int c : comps) {
+        std::vector<std::pair<int, float>> row;
+        for (int e = 0; e < cnt; ++e)
+          if (j.rec[off + e].comp == c) row.push_back({j.rec[off + e].g, j.rec[off + e].coef});
+        int h = -1;
+        for (size_t r = 0; r < rows.size(); ++r)
+          if (rows[r] == row) h = (int)r;
+        if (h < 0) {
+          h = (int)rows.size();
+          rows.push_back(row);
+        }
+        if (nse >= 512) throw Error{6, "pair reduction: too many side entries"};
+        j.s_ent[nse][0] = c;
+        j.s_ent[nse][1] = h;
+        ++nse;
+      }
+      ++ns;
+    }
+  j.s_off[ns] = nse;
+  for (int q = 0; q < ns; ++q)
+    if (j.s_off[q + 1] - j.s_off[q] > 8) throw Error{6, "pair reduction: more than 8 components in a side"};
+  for (int t = 0; t < j.nterm; ++t)
+    if (j.term[t].xslot >= 0 && j.term[t].yslot >= 0) throw Error{6, "pair reduction: both sides built"};
+  if (rows.size() > 128) throw Error{6, "pair reduction: too many H rows"};
+  int ne = 0;
+  for (size_t r = 0; r < rows.size(); ++r) {
+    j.h_off[r] = ne;
+    for (auto& e : rows[r]) {
+      if (ne >= 512) throw Error{6, "pair reduction: too many H entries"};
+      j.h_ent[ne++] = {0, e.first, e.second};
+    }
+  }
+  j.nh = (int)rows.size();
+  j.h_off[j.nh] = ne;
+  return j;
+}
+
+// the tensor-core contraction covers up to 32 bins; BISP_PAIR_FP32=1 forces the FP32 FMA kernel
+static bool pair_use_tc(const PairJob& j) {
+  const char* e = getenv("BISP_PAIR_FP32");
+  return j.nb <= 32 && !(e && e[0] == '1');
+}
+
+struct TmaLayout;
+static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps);
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int NW>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW)); }
+
+// copy one chunk of every component row [b][comp] and G row into shared memory;
+// rowmap[f] = destination row of source row f (f < nb*ncomp: field (b, comp); then G rows)
+__device__ __forceinline__ void pair_stage(float* raw, int64_t x0, const int* rowmap) {
+  const PairJob& J = c_pj;
+  constexpr int Q = PR_CH / 4;  // 16-byte pieces per row (a power of two)
+  constexpr int QS = Q == 16 ? 4 : (Q == 8 ? 3 : 2);
+  const int nraw = J.nb * J.ncomp;
+  const int n = (nraw + J.ng) << QS;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int f = i >> QS, q = i & (Q - 1);
+    const float* src = (f < nraw ? J.fields + (size_t)f * J.Ng : J.gfields + (size_t)(f - nraw) * J.Ng) + x0 + 4 * q;
+    cp_async16(raw + (size_t)rowmap[f] * PR_LD + 4 * q, src);
+  }
+}
+
+// built sides, block-wide: first the H rows of the chunk, H_h(x) = sum coef G_g(x) (shared by
+// all bins), then one thread per (side, bin, 4-cell quad): X(b, x) = sum_(c,h) P_c(b, x) H_h(x).
+// mnb = ceil(2^32 / nb): j / nb = umulhi(j, mnb) for the small j used here.
+__device__ __forceinline__ void pair_build_sides(const float* raw, float* mat, float* Hs, int bs, unsigned mnb) {
+  const PairJob& J = c_pj;
+  constexpr int Q = PR_CH / 4;
+  constexpr int QS = Q == 16 ? 4 : (Q == 8 ? 3 : 2);
+  const int grow0 = J.nb * bs;
+  for (int i = threadIdx.x; i < (J.nh << QS); i += blockDim.x) {
+    const int h = i >> QS, q = i & (Q - 1);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = J.h_off[h]; e < J.h_off[h + 1]; ++e) {
+      const PairRecipe R = J.h_ent[e];
+      if (R.g >= 0) {
+        const float4 gv = *reinterpret_cast<const float4*>(raw + (size_t)(grow0 + R.g) * PR_LD + 4 * q);
+        v.x = fmaf(R.coef, gv.x, v.x);
+        v.y = fmaf(R.coef, gv.y, v.y);
+        v.z = fmaf(R.coef, gv.z, v.z);
+        v.w = fmaf(R.coef, gv.w, v.w);
+      } else {
+        v.x += R.coef;
+        v.y += R.coef;
+        v.z += R.coef;
+        v.w += R.coef;
+      }
+    }
+    *reinterpret_cast<float4*>(Hs + (size_t)h * PR_CH + 4 * q) = v;
+  }
+  __syncthreads();
+  const int n = (J.nslot * J.nb) << QS;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned j = (unsigned)i >> QS;
+    const int q = i & (Q - 1);
+    const int sl = (int)__umulhi(j, mnb);
+    const int b = (int)j - sl * J.nb;
+    const float* rb = raw + (size_t)b * bs * PR_LD + 4 * q;
+    const float* hq = Hs + 4 * q;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e1 = J.s_off[sl + 1];
+    for (int e = J.s_off[sl]; e < e1; ++e) {
+      const float4 pv = *reinterpret_cast<const float4*>(rb + J.s_ent[e][0] * PR_LD);
+      const float4 hv = *reinterpret_cast<const float4*>(hq + J.s_ent[e][1] * PR_CH);
+      v.x = fmaf(pv.x, hv.x, v.x);
+      v.y = fmaf(pv.y, hv.y, v.y);
+      v.z = fmaf(pv.z, hv.z, v.z);
+      v.w = fmaf(pv.w, hv.w, v.w);
+    }
+    *reinterpret_cast<float4*>(mat + ((size_t)sl * J.nb + b) * PR_LD + 4 * q) = v;
+  }
+}
+
+template <int TM, int TN, int NTHR>
+__global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int ksplit, double* partials) {
+  const PairJob& J = c_pj;
+  extern __shared__ __align__(16) float sh[];
+  float* mat = sh + (size_t)PR_NSTAGE * rows * PR_LD;  // [nslot][nb][PR_LD]
+  float* Hs = mat + (size_t)J.nslot * J.nb * PR_LD;  // [nh][PR_CH]
+  int* rowmap = reinterpret_cast<int*>(Hs + (size_t)J.nh * PR_CH);
+  const unsigned mnb = (unsigned)((0x100000000ull + J.nb - 1) / J.nb);
+  const int64_t nchunk = J.Ng / PR_CH;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int t = warp / ksplit, ks = warp % ksplit;
+  const int slice = PR_CH / ksplit;
+  const int b1 = lane >> 3, b2 = lane & 7;  // rows b1 + 4 i and b2 + 8 j
+  const PairTermDesc T = J.term[t];
+  for (int f = threadIdx.x; f < J.nb * J.ncomp + J.ng; f += blockDim.x) {
+    const int nraw = J.nb * J.ncomp;
+    rowmap[f] = f < nraw ? (f / J.ncomp) * bs + f % J.ncomp : J.nb * bs + (f - nraw);
+  }
+  __syncthreads();
+  double* slot = partials + (((size_t)blockIdx.x * nwarp + warp) * 32 + lane) * (TM * TN);
+#pragma unroll
+  for (int q = 0; q < TM * TN; ++q) slot[q] = 0.0;
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  if (blockIdx.x < nchunk) pair_stage(sh, (int64_t)blockIdx.x * PR_CH, rowmap);
+  cp_async_commit();
+  int since_flush = 0, stage = 0;
+  for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    cp_async_wait<0>();
+    __syncthreads();
+    {
+      const int64_t nx = ch + gridDim.x;
+      if (nx < nchunk) pair_stage(sh + (size_t)(stage ^ 1) * rows * PR_LD, nx * PR_CH, rowmap);
+      cp_async_commit();
+    }
+    const float* raw = sh + (size_t)stage * rows * PR_LD;
+    if (J.nslot) {
+      pair_build_sides(raw, mat, Hs, bs, mnb);
+      __syncthreads();
+    }
+    // row pointers of this lane's bins b1 + 4 i and b2 + 8 j (clamped to a valid row)
+    const float* xrow[TM];
+    const float* yrow[TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int b = min(b1 + 4 * i, J.nb - 1);
+      xrow[i] = (T.xdir >= 0 ? raw + (size_t)(b * bs + T.xdir) * PR_LD : mat + ((size_t)T.xslot * J.nb + b) * PR_LD) +
+                ks * slice;
+    }
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int b = min(b2 + 8 * j, J.nb - 1);
+      yrow[j] = (T.ydir >= 0 ? raw + (size_t)(b * bs + T.ydir) * PR_LD : mat + ((size_t)T.yslot * J.nb + b) * PR_LD) +
+                ks * slice;
+    }
+    for (int xb = 0; xb < slice; xb += 16) {
+#pragma unroll
+      for (int x = xb; x < xb + 16; x += 4) {
+        float4 a[TM], c[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = *reinterpret_cast<const float4*>(xrow[i] + x);
+#pragma unroll
+        for (int j = 0; j < TN; ++j) c[j] = *reinterpret_cast<const float4*>(yrow[j] + x);
+        // component-outer order: consecutive FMAs update different accumulators
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i].x, c[j].x, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i].y, c[j].y, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i].z, c[j].z, acc[i][j]);
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i].w, c[j].w, acc[i][j]);
+      }
+    }
+    if (++since_flush == PR_FLUSH || ch + gridDim.x >= nchunk) {
+      since_flush = 0;
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          slot[i * TN + j] += (double)acc[i][j];
+          acc[i][j] = 0.f;
+        }
+    }
+    stage ^= 1;
+  }
+  cp_async_wait<0>();
+}
+
+// ------------------------------------------------------------------------------------
+// Tensor-core variant (nb <= 32).  Per chunk of 64 cells, for every term t:
+//   C_t (32 x 32 bins) += X_t (32 bins x 64 cells) Y_t^T
+// with mma.sync m16n8k8 TF32 in three passes over a split v = hi + lo of each FP32 value
+// (hi, lo both TF32: X_hi Y_hi + X_hi Y_lo + X_lo Y_hi), i.e. FP32-class products.
+//
+// Staging: a 3D TMA tensor map views the component fields as [nb][ncomp][Ng] and loads, per
+// 32-cell half and component c, the box of all bins as a [32 bins][32 cells] block (bins
+// >= nb read as zeros); a 2D map loads the G fields as [ng][32 cells].  Blocks use the
+// 128-byte swizzle (16-byte piece p of row r stored at piece p ^ (r & 7)), so the 8-row
+// ldmatrix reads below hit 8 different bank groups.  Two stages: the TMA of chunk i+1 runs
+// while chunk i is used; an mbarrier per stage carries the transaction bytes.  Every wait
+// is bounded in time and reports a timeout through err instead of hanging.
+//
+// Per chunk: (1) H rows H_h(x) = sum coef G_g(x) (shared by all bins), stored in the order
+// the MMA fragments read them; (2) one warp per (term, cell half): a built side
+// X(b, x) = sum_(c,h) F_c(b, x) H_h(x) is accumulated directly in fragment registers from
+// ldmatrix loads of the F_c blocks, a bare side is loaded as it is; then the three MMA passes.
+// The MMA accumulators restart every chunk; chunk results go to FP32 running sums that are
+// added to lane-owned FP64 slots every PR_FLUSH chunks (<= 1024 cells per FP32 partial).
+// ------------------------------------------------------------------------------------
+struct TmaLayout {
+  unsigned fsz, gsz;  // bytes of the F blocks (ncomp x 4096) and of the G block of one half
+  unsigned half;      // fsz + gsz
+  unsigned stage;     // 2 * half
+  unsigned hs;        // offset of the H rows [nh][64 floats], fragment order
+  unsigned bar;       // offset of the two mbarriers
+  unsigned bytes;     // dynamic shared memory to request (includes 1024 B alignment slack)
+  unsigned tx;        // transaction bytes per stage
+  int ncomp, gbox;    // F blocks per half, G rows
+};
+
+constexpr int TMA_MAXWARP = 10;
+constexpr unsigned long long TMA_WAIT_NS = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// wait for the phase with the given parity; false after TMA_WAIT_NS without completion
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > TMA_WAIT_NS) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar,
+                                            unsigned long long policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, uint32_t* r) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(uint32_t bits, uint32_t& hi, uint32_t& lo) {
+  const float v = __uint_as_float(bits);
+  hi = tf32_rna(v);
+  lo = tf32_rna(v - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// byte offset of 16-byte piece p of row r in a 128-byte-swizzled [rows][32 floats] block
+__device__ __forceinline__ unsigned swz(int r, int p) { return (unsigned)r * 128u + ((unsigned)(p ^ (r & 7)) << 4); }
+
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar,
+                                            unsigned long long policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar), "l"(policy)
+      : "memory");
+}
+
+// Accumulate a built side sum_(c,h) F_c(b, x) H_h(x) of one 32-cell half into fragment
+// registers f[kk][i][.] (kk: 8-cell k step, i: ldmatrix group).  ROLE 0: A operand, whose
+// registers hold cells (tq, tq, tq+4, tq+4); ROLE 1: B operand, cells (tq, tq+4, tq, tq+4).
+// hr points at this half of H row 0 in fragment order (pair (tq, tq+4) of step kk at 8kk+2tq).
+template <int ROLE>
+__device__ __forceinline__ void build_side(float (&f)[4][2][4], unsigned fhalf, const float* hr, int e0, int e1,
+                                           const unsigned (&loff)[2], const unsigned (&poff)[4], int tq) {
+  const PairJob& J = c_pj;
+  for (int e = e0; e < e1; ++e) {
+    const unsigned fb = fhalf + (unsigned)J.s_ent[e][0] * 4096u;
+    const float* h = hr + J.s_ent[e][1] * PR_CH + 2 * tq;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const float2 hv = *reinterpret_cast<const float2*>(h + 8 * kk);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        uint32_t v[4];
+        ldsm_x4(fb + loff[i] + poff[kk], v);
+        const float h1 = ROLE == 0 ? hv.x : hv.y, h2 = ROLE == 0 ? hv.y : hv.x;
+        f[kk][i][0] = fmaf(__uint_as_float(v[0]), hv.x, f[kk][i][0]);
+        f[kk][i][1] = fmaf(__uint_as_float(v[1]), h1, f[kk][i][1]);
+        f[kk][i][2] = fmaf(__uint_as_float(v[2]), h2, f[kk][i][2]);
+        f[kk][i][3] = fmaf(__uint_as_float(v[3]), hv.y, f[kk][i][3]);
+      }
+    }
+  }
+}
+
+template <int NTHR>
+__global__ void __launch_bounds__(NTHR, 1)
+    k_pair_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const TmaLayout L,
+               int ksplit, double* partials, int* err) {
+  const PairJob& J = c_pj;
+  extern __shared__ unsigned char dsm[];
+  __shared__ int s_abort;
+  const unsigned raw0 = smem_u32(dsm);
+  const unsigned base = (raw0 + 1023u) & ~1023u;
+  unsigned char* const gb = dsm + (base - raw0);  // generic pointer to the aligned base
+  float* const Hs = reinterpret_cast<float*>(gb + L.hs);
+  const unsigned bar0 = base + L.bar;
+  const int64_t nchunk = J.Ng / PR_CH;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t = warp / ksplit, ks = warp % ksplit;
+  const PairTermDesc T = J.term[t];
+  unsigned long long pol = 0;
+  if (tid == 0) {
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    mbar_init(bar0, 1);
+    mbar_init(bar0 + 8, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncthreads();
+  auto issue = [&](int64_t ch, int st) {  // thread 0 only
+    const unsigned bar = bar0 + 8u * st;
+    mbar_expect_tx(bar, L.tx);
+    for (int h = 0; h < 2; ++h) {
+      const unsigned hb = base + st * L.stage + h * L.half;
+      const int x = (int)(ch * PR_CH + 32 * h);
+      for (int c = 0; c < L.ncomp; ++c) tma_load_3d(hb + (unsigned)c * 4096u, &tmF, x, c, 0, bar, pol);
+      tma_load_2d(hb + L.fsz, &tmG, x, 0, bar, pol);
+    }
+  };
+
+  double* slot = partials + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * 32;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) slot[q] = 0.0;
+  float run[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) run[q] = 0.f;
+
+  // ldmatrix rows of this lane: matrix j = lane/8, row r = lane%8 of that matrix; every
+  // fragment row is congruent to r mod 8, so its swizzled piece is (piece ^ r).
+  // A: matrices (rows 0-7 | 8-15) x (k 0-3 | 4-7): row 16 i + 8 (j&1) + r, piece 2 kk + (j>>1)
+  // B: matrices (ni k 0-3, ni k 4-7, ni+1 k 0-3, ni+1 k 4-7), ni = 2 i: row 8 (2i + (j>>1)) + r,
+  //    piece 2 kk + (j&1)
+  const int jm = lane >> 3, r = lane & 7, tq = lane & 3;
+  unsigned loffA[2], loffB[2], poffA[4], poffB[4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    loffA[i] = (unsigned)(16 * i + 8 * (jm & 1) + r) * 128u;
+    loffB[i] = (unsigned)(8 * (2 * i + (jm >> 1)) + r) * 128u;
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    poffA[kk] = (unsigned)((2 * kk + (jm >> 1)) ^ r) << 4;
+    poffB[kk] = (unsigned)((2 * kk + (jm & 1)) ^ r) << 4;
+  }
+  const bool xb = T.xslot >= 0, yb = T.yslot >= 0;  // built sides (at most one)
+  const int bslot = xb ? T.xslot : (yb ? T.yslot : 0);
+  const int e0 = (xb || yb) ? J.s_off[bslot] : 0, e1 = (xb || yb) ? J.s_off[bslot + 1] : 0;
+  const unsigned xoff = xb ? 0u : (unsigned)T.xdir * 4096u, yoff = yb ? 0u : (unsigned)T.ydir * 4096u;
+  const int hfirst = ksplit == 2 ? ks : 0, hlast = ksplit == 2 ? ks + 1 : 2;
+
+  if (tid == 0 && blockIdx.x < nchunk) issue(blockIdx.x, 0);
+  int since_flush = 0, it = 0;
+  for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x, ++it) {
+    const int st = it & 1;
+    if (tid == 0 && ch + gridDim.x < nchunk) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(ch + gridDim.x, st ^ 1);
+    }
+    if (!mbar_wait_bounded(bar0 + 8u * st, (unsigned)(it >> 1) & 1u)) {
+      s_abort = 1;
+      atomicExch(err, 1);
+    }
+    const unsigned sbo = st * L.stage;  // offset of this stage
+    // (1) H rows, stored per half as [kk][tq][cell tq | cell tq+4]
+    for (int i = tid; i < (J.nh << 4); i += blockDim.x) {
+      const int h = i >> 4, q = i & 15, hh = q >> 3, p = q & 7;
+      const unsigned char* g0 = gb + sbo + hh * L.half + L.fsz;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int e = J.h_off[h]; e < J.h_off[h + 1]; ++e) {
+        const PairRecipe R = J.h_ent[e];
+        if (R.g >= 0) {
+          const float4 gv = *reinterpret_cast<const float4*>(g0 + swz(R.g, p));
+          v.x = fmaf(R.coef, gv.x, v.x);
+          v.y = fmaf(R.coef, gv.y, v.y);
+          v.z = fmaf(R.coef, gv.z, v.z);
+          v.w = fmaf(R.coef, gv.w, v.w);
+        } else {
+          v.x += R.coef;
+          v.y += R.coef;
+          v.z += R.coef;
+          v.w += R.coef;
+        }
+      }
+      // cells 4p..4p+3 of half hh: step kk = p/2, slot s = p%2 of the pairs of lanes tq = 0..3
+      float* d = Hs + h * PR_CH + hh * 32 + (p >> 1) * 8 + (p & 1);
+      d[0] = v.x;
+      d[2] = v.y;
+      d[4] = v.z;
+      d[6] = v.w;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    // (2) this warp's term over its cell half (or both halves)
+    float c[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) c[q] = 0.f;
+    for (int hh = hfirst; hh < hlast; ++hh) {
+      const unsigned fh = base + sbo + hh * L.half;
+      float sd[4][2][4];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) sd[kk][i][e] = 0.f;
+      if (xb)
+        build_side<0>(sd, fh, Hs + hh * 32, e0, e1, loffA, poffA, tq);
+      else if (yb)
+        build_side<1>(sd, fh, Hs + hh * 32, e0, e1, loffB, poffB, tq);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        uint32_t av[2][4], bv[2][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          if (xb) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) av[i][e] = __float_as_uint(sd[kk][i][e]);
+          } else {
+            ldsm_x4(fh + xoff + loffA[i] + poffA[kk], av[i]);
+          }
+          if (yb) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) bv[i][e] = __float_as_uint(sd[kk][i][e]);
+          } else {
+            ldsm_x4(fh + yoff + loffB[i] + poffB[kk], bv[i]);
+          }
+        }
+        uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            split_tf32(av[i][e], ah[i][e], al[i][e]);
+            split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
+          }
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+          for (int ni = 0; ni < 4; ++ni) {
+            float* cc = c + (mi * 4 + ni) * 4;
+            mma_tf32(cc, al[mi], bh[ni]);
+            mma_tf32(cc, ah[mi], bl[ni]);
+            mma_tf32(cc, ah[mi], bh[ni]);
+          }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) run[q] += c[q];
+    if (++since_flush == PR_FLUSH || ch + gridDim.x >= nchunk) {
+      since_flush = 0;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        slot[q] += (double)run[q];
+        run[q] = 0.f;
+      }
+    }
+    __syncthreads();
+  }
+  // after an abort the prefetched stage may still be in flight: wait for it (bounded)
+  if (tid == 0 && s_abort) mbar_wait_bounded(bar0 + 8u * ((it + 1) & 1), (unsigned)((it + 1) >> 1) & 1u);
+}
+
+static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) {
+  if (j.nb > 32 || j.nterm > TMA_MAXWARP || j.ng < 1 || j.ng > 256 || j.ncomp < 1) return false;
+  auto r1024 = [](size_t b) { return (b + 1023) / 1024 * 1024; };
+  const size_t fsz = (size_t)j.ncomp * 4096, gsz = r1024((size_t)j.ng * 128);
+  const size_t half = fsz + gsz, stage = 2 * half, hs = 2 * stage;
+  const size_t bar = (hs + (size_t)j.nh * PR_CH * 4 + 15) / 16 * 16;
+  const size_t bytes = bar + 16 + 1024;
+  if (bytes > 227 * 1024 - 256) return false;
+  L->fsz = (unsigned)fsz;
+  L->gsz = (unsigned)gsz;
+  L->half = (unsigned)half;
+  L->stage = (unsigned)stage;
+  L->hs = (unsigned)hs;
+  L->bar = (unsigned)bar;
+  L->bytes = (unsigned)bytes;
+  L->ncomp = j.ncomp;
+  L->gbox = j.ng;
+  L->tx = (unsigned)(2 * (fsz + (size_t)j.ng * 128));
+  *ksplit = 2 * j.nterm <= TMA_MAXWARP ? 2 : 1;
+  *warps = j.nterm * *ksplit;
+  return true;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  if (!fn) throw Error{3, "cuTensorMapEncodeTiled is not available from the driver"};
+  return fn;
+}
+
+// G fields: rows x Ng FP32 (row stride Ng), boxes of 32 cells x rows, 128-byte swizzle
+static CUtensorMap g_map(const float* base, int64_t Ng, int rows) {
+  CUtensorMap m;
+  const cuuint64_t dim[2] = {(cuuint64_t)Ng, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)Ng * sizeof(float)};
+  const cuuint32_t box[2] = {32, (cuuint32_t)rows};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dim, stride, box,
+                                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error{3, "cuTensorMapEncodeTiled (G fields) failed (" + std::to_string((int)r) + ")"};
+  return m;
+}
+
+// component fields [nb][ncomp][Ng]: boxes of 32 cells x 1 component x 32 bins (bins >= nb
+// are filled with zeros), 128-byte swizzle
+static CUtensorMap f_map(const float* base, int64_t Ng, int ncomp, int nb) {
+  CUtensorMap m;
+  const cuuint64_t dim[3] = {(cuuint64_t)Ng, (cuuint64_t)ncomp, (cuuint64_t)nb};
+  const cuuint64_t stride[2] = {(cuuint64_t)Ng * sizeof(float), (cuuint64_t)Ng * ncomp * sizeof(float)};
+  const cuuint32_t box[3] = {32, 1, 32};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dim, stride, box,
+                                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error{3, "cuTensorMapEncodeTiled (component fields) failed (" + std::to_string((int)r) + ")"};
+  return m;
+}
+
+static int pair_blocks() {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm;
+}
+
+size_t pair_scratch_bytes(const PairJob& job) {
+  const PairJob j = classify(job);
+  TmaLayout L;
+  int ksplit = 1, warps = 1;
+  if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps))
+    return (size_t)pair_blocks() * warps * 32 * 32 * sizeof(double) + 256;
+  const PairLaunch c = pair_launch_cfg(j);
+  return (size_t)c.nblk * c.warps * 32 * c.TM * c.TN * sizeof(double);
+}
+
+
+// final reduction for k_pair_tc: bin (b1, b2) of term t sits in warp t*ksplit+ks, lane
+// (b1%8)*4 + (b2%8)/2, register ((b1/16)*4 + b2/8)*4 + ((b1/8)%2)*2 + b2%2
+__global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int ksplit, int nb, int nout,
+                                double* out) {
+  const PairJob& J = c_pj;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= nout * nb * nb) return;
+  const int o = gw / (nb * nb), b1 = (gw / nb) % nb, b2 = gw % nb;
+  const int ln = (b1 % 8) * 4 + (b2 % 8) / 2;
+  const int q = ((b1 / 16) * 4 + b2 / 8) * 4 + ((b1 / 8) % 2) * 2 + (b2 % 2);
+  double tot = 0.0;
+  for (int e = J.out_ent_off[o]; e < J.out_ent_off[o + 1]; ++e) {
+    const int t = J.out_ent_term[e];
+    double s = 0.0;
+    for (int ks = 0; ks < ksplit; ++ks) {
+      const int w = t * ksplit + ks;
+      for (int c = lane; c < nblk; c += 32) s += partials[(((size_t)c * warps + w) * 32 + ln) * 32 + q];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    tot += J.out_ent_mult[e] * s;
+  }
+  if (lane == 0) out[gw] = tot;
+}
+
+// out[o][b1][b2] = sum over terms of o, then CTAs and x slices in a fixed order; one warp
+// per output value, lanes stride over CTAs, fixed shuffle tree.
+__global__ void k_pair_final(const double* partials, int nblk, int warps, int ksplit, int TM, int TN, int nb,
+                             int nout, double* out) {
+  const PairJob& J = c_pj;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= nout * nb * nb) return;
+  const int o = gw / (nb * nb), b1 = (gw / nb) % nb, b2 = gw % nb;
+  const int ln = (b1 % 4) * 8 + b2 % 8, q = (b1 / 4) * TN + b2 / 8;
+  double tot = 0.0;
+  for (int e = J.out_ent_off[o]; e < J.out_ent_off[o + 1]; ++e) {
+    const int t = J.out_ent_term[e];
+    double s = 0.0;
+    for (int ks = 0; ks < ksplit; ++ks) {
+      const int w = t * ksplit + ks;
+      for (int c = lane; c < nblk; c += 32) s += partials[(((size_t)c * warps + w) * 32 + ln) * (TM * TN) + q];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    tot += J.out_ent_mult[e] * s;
+  }
+  if (lane == 0) out[gw] = tot;
+}
+
+void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scratch_bytes, cudaStream_t s,
+                 int* launches) {
+  const PairJob j = classify(job);
+  if (scratch_bytes < pair_scratch_bytes(job)) throw Error{2, "pair reduction scratch too small"};
+  if (j.Ng % PR_CH) throw Error{6, "mesh size not a multiple of the chunk"};
+  BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &j, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
+  double* partials = reinterpret_cast<double*>(scratch);
+  TmaLayout L;
+  int ksplit = 1, warps = 1;
+  if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) {
+    const int nblk = pair_blocks();
+    const size_t need = (size_t)nblk * warps * 32 * 32 * sizeof(double);
+    int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + need);
+    BISP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb);
+    const CUtensorMap mg = g_map(j.gfields, j.Ng, j.ng);
+    BISP_CUDA(cudaFuncSetAttribute(k_pair_tma<32 * TMA_MAXWARP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)L.bytes));
+    k_pair_tma<32 * TMA_MAXWARP><<<nblk, warps * 32, L.bytes, s>>>(mf, mg, L, ksplit, partials, err);
+    BISP_CHECK_LAUNCH();
+    const int nout = j.nout * j.nb * j.nb;
+    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(partials, nblk, warps, ksplit, j.nb, j.nout, out_dev);
+    BISP_CHECK_LAUNCH();
+    int herr = 0;
+    BISP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BISP_CUDA(cudaStreamSynchronize(s));
+    if (herr) throw Error{5, "pair reduction: a TMA stage did not arrive within 2 s"};
+    if (launches) *launches += 2;
+    return;
+  }
+  const PairLaunch c = pair_launch_cfg(j);
+  if (c.smem > 227 * 1024) throw Error{6, "pair reduction: shared memory budget exceeded"};
+#define BISP_PAIR3(A, B, NT)                                                                              \
+  if (c.TM == A && c.TN == B && c.warps * 32 <= NT) {                                                   \
+    BISP_CUDA(cudaFuncSetAttribute(k_pair<A, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem)); \
+    k_pair<A, B, NT><<<c.nblk, c.warps * 32, c.smem, s>>>(c.nbp, c.bs, c.rows, c.ksplit, partials);           \
+    launched = true;                                                                                     \
+  }
+#define BISP_PAIR(A, B) \
+  if (!launched) BISP_PAIR3(A, B, 512) if (!launched) BISP_PAIR3(A, B, 1024)
+#define BISP_PAIR_S(A, B) \
+  if (!launched) BISP_PAIR3(A, B, 512)
+  bool launched = false;
+  BISP_PAIR(1, 1) BISP_PAIR(2, 1) BISP_PAIR(3, 2) BISP_PAIR(4, 2) BISP_PAIR(5, 3) BISP_PAIR(6, 3)
+  BISP_PAIR_S(7, 4) BISP_PAIR_S(8, 4) BISP_PAIR_S(10, 5)
+#undef BISP_PAIR
+#undef BISP_PAIR_S
+#undef BISP_PAIR3
+  if (!launched) throw Error{6, "pair reduction: no kernel for this shape"};
+  BISP_CHECK_LAUNCH();
+  const int nout = j.nout * j.nb * j.nb;
+  k_pair_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(partials, c.nblk, c.warps, c.ksplit, c.TM, c.TN, j.nb,
+                                                       j.nout, out_dev);
+  BISP_CHECK_LAUNCH();
+  if (launches) *launches += 2;
+}
+
+}  // namespace bisp
+
