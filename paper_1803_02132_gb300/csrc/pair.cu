@@ -475,18 +475,17 @@ __device__ __forceinline__ void ldsm_x4(unsigned addr, uint32_t* r) {
                : "r"(addr));
 }
 
-__device__ __forceinline__ uint32_t tf32_rna(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return r;
-}
+// v = hi + lo: hi keeps the sign, exponent and top 10 mantissa bits of v (a valid TF32
+// value), lo = v - hi is exact in FP32 and the tensor core reads its top 19 bits.  The three
+// passes then miss below 3 * 2^-20 of each product, always toward zero by a fraction that does
+// not depend on the product's sign or size: a sum is scaled by about 1 - 1.5e-6 plus noise of
+// order 1e-6 of its root-sum-square.
 __device__ __forceinline__ void split_tf32(uint32_t bits, uint32_t& hi, uint32_t& lo) {
-  const float v = __uint_as_float(bits);
-  hi = tf32_rna(v);
-  lo = tf32_rna(v - __uint_as_float(hi));
+  hi = bits & 0xffffe000u;
+  lo = __float_as_uint(__uint_as_float(bits) - __uint_as_float(hi));
 }
 __device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
@@ -569,9 +568,9 @@ __global__ void __launch_bounds__(NTHR, 1)
     }
   };
 
-  double* slot = partials + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * 32;
+  float2* slot = reinterpret_cast<float2*>(partials) + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * 32;
 #pragma unroll
-  for (int q = 0; q < 32; ++q) slot[q] = 0.0;
+  for (int q = 0; q < 32; ++q) slot[q] = make_float2(0.f, 0.f);
   float run[32];
 #pragma unroll
   for (int q = 0; q < 32; ++q) run[q] = 0.f;
@@ -684,24 +683,34 @@ __global__ void __launch_bounds__(NTHR, 1)
             split_tf32(av[i][e], ah[i][e], al[i][e]);
             split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
           }
+        // small products first, pass-major so that consecutive MMAs are independent
 #pragma unroll
         for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-          for (int ni = 0; ni < 4; ++ni) {
-            float* cc = c + (mi * 4 + ni) * 4;
-            mma_tf32(cc, al[mi], bh[ni]);
-            mma_tf32(cc, ah[mi], bl[ni]);
-            mma_tf32(cc, ah[mi], bh[ni]);
-          }
+          for (int ni = 0; ni < 4; ++ni) mma_tf32(c + (mi * 4 + ni) * 4, al[mi], bh[ni]);
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+          for (int ni = 0; ni < 4; ++ni) mma_tf32(c + (mi * 4 + ni) * 4, ah[mi], bl[ni]);
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+          for (int ni = 0; ni < 4; ++ni) mma_tf32(c + (mi * 4 + ni) * 4, ah[mi], bh[ni]);
       }
     }
 #pragma unroll
     for (int q = 0; q < 32; ++q) run[q] += c[q];
     if (++since_flush == PR_FLUSH || ch + gridDim.x >= nchunk) {
       since_flush = 0;
+      // compensated (Kahan) FP32 sum per slot: (s, e) with the true sum s - e
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        slot[q] += (double)run[q];
+        float2 v = slot[q];
+        const float y = run[q] - v.y;
+        const float tt = v.x + y;
+        v.y = (tt - v.x) - y;
+        v.x = tt;
+        slot[q] = v;
         run[q] = 0.f;
       }
     }
@@ -799,7 +808,7 @@ size_t pair_scratch_bytes(const PairJob& job) {
 }
 
 
-// final reduction for k_pair_tc: bin (b1, b2) of term t sits in warp t*ksplit+ks, lane
+// final reduction for k_pair_tma (slots are compensated FP32 pairs): bin (b1, b2) of term t sits in warp t*ksplit+ks, lane
 // (b1%8)*4 + (b2%8)/2, register ((b1/16)*4 + b2/8)*4 + ((b1/8)%2)*2 + b2%2
 __global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int ksplit, int nb, int nout,
                                 double* out) {
@@ -815,7 +824,10 @@ __global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int
     double s = 0.0;
     for (int ks = 0; ks < ksplit; ++ks) {
       const int w = t * ksplit + ks;
-      for (int c = lane; c < nblk; c += 32) s += partials[(((size_t)c * warps + w) * 32 + ln) * 32 + q];
+      for (int c = lane; c < nblk; c += 32) {
+        const float2 v = reinterpret_cast<const float2*>(partials)[(((size_t)c * warps + w) * 32 + ln) * 32 + q];
+        s += (double)v.x - (double)v.y;
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
