@@ -149,6 +149,7 @@ struct PairTermDesc {
   int xoff, xcnt, yoff, ycnt;  // recipe entries of the two sides
   int xdir, ydir;              // side is a bare component field (index), or -1
   int xslot, yslot;            // shared-memory slot of a side built per chunk, or -1
+  int tr;                      // 1: computed as Y X^T (tensor-core kernel), read back transposed
 };
 struct PairJob {
   const float* fields;    // component field (b, c) at fields + (b*ncomp + c) * Ng

@@ -401,11 +401,15 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int
 // is bounded in time and reports a timeout through err instead of hanging.
 //
 // Per chunk: (1) H rows H_h(x) = sum coef G_g(x) (shared by all bins), stored in the order
-// the MMA fragments read them; (2) one warp per (term, cell half): a built side
-// X(b, x) = sum_(c,h) F_c(b, x) H_h(x) is accumulated directly in fragment registers from
-// ldmatrix loads of the F_c blocks, a bare side is loaded as it is; then the three MMA passes.
-// The MMA accumulators restart every chunk; chunk results go to FP32 running sums that are
-// added to lane-owned FP64 slots every PR_FLUSH chunks (<= 1024 cells per FP32 partial).
+// the MMA fragments read them; (2) two warps per (term, cell half), one per 16-row half of
+// the 32 x 32 tile: a built side X(b, x) = sum_(c,h) F_c(b, x) H_h(x) is accumulated directly
+// in fragment registers from ldmatrix loads of the F_c blocks, a bare side is loaded as it
+// is; then the three MMA passes.  Terms are normalised so that only X is ever built (a term
+// with a built Y is computed as Y X^T and read back transposed).
+// The MMA accumulators restart every chunk; chunk results go to FP32 running sums, and every
+// chunk one of the 16 (round robin, so each covers at most 1024 cells) is added with Kahan
+// compensation to a lane-owned FP32 (sum, compensation) slot in global memory, whose load is
+// issued at the start of the chunk.
 // ------------------------------------------------------------------------------------
 struct TmaLayout {
   unsigned fsz, gsz;  // bytes of the F blocks (ncomp x 4096) and of the G block of one half
@@ -418,7 +422,7 @@ struct TmaLayout {
   int ncomp, gbox;    // F blocks per half, G rows
 };
 
-constexpr int TMA_MAXWARP = 10;
+constexpr int TMA_MAXWARP = 20;  // two warps (row halves) per term and cell half
 constexpr unsigned long long TMA_WAIT_NS = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -504,34 +508,13 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map
       : "memory");
 }
 
-// Accumulate a built side sum_(c,h) F_c(b, x) H_h(x) of one 32-cell half into fragment
-// registers f[kk][i][.] (kk: 8-cell k step, i: ldmatrix group).  ROLE 0: A operand, whose
-// registers hold cells (tq, tq, tq+4, tq+4); ROLE 1: B operand, cells (tq, tq+4, tq, tq+4).
-// hr points at this half of H row 0 in fragment order (pair (tq, tq+4) of step kk at 8kk+2tq).
-template <int ROLE>
-__device__ __forceinline__ void build_side(float (&f)[4][2][4], unsigned fhalf, const float* hr, int e0, int e1,
-                                           const unsigned (&loff)[2], const unsigned (&poff)[4], int tq) {
-  const PairJob& J = c_pj;
-  for (int e = e0; e < e1; ++e) {
-    const unsigned fb = fhalf + (unsigned)J.s_ent[e][0] * 4096u;
-    const float* h = hr + J.s_ent[e][1] * PR_CH + 2 * tq;
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const float2 hv = *reinterpret_cast<const float2*>(h + 8 * kk);
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        uint32_t v[4];
-        ldsm_x4(fb + loff[i] + poff[kk], v);
-        const float h1 = ROLE == 0 ? hv.x : hv.y, h2 = ROLE == 0 ? hv.y : hv.x;
-        f[kk][i][0] = fmaf(__uint_as_float(v[0]), hv.x, f[kk][i][0]);
-        f[kk][i][1] = fmaf(__uint_as_float(v[1]), h1, f[kk][i][1]);
-        f[kk][i][2] = fmaf(__uint_as_float(v[2]), h2, f[kk][i][2]);
-        f[kk][i][3] = fmaf(__uint_as_float(v[3]), hv.y, f[kk][i][3]);
-      }
-    }
-  }
+// compensated (Kahan) FP32 accumulation into a slot (s, e) whose true sum is s - e
+__device__ __forceinline__ void kahan_add(float2& v, float x) {
+  const float y = x - v.y;
+  const float t = v.x + y;
+  v.y = (t - v.x) - y;
+  v.x = t;
 }
-
 template <int NTHR>
 __global__ void __launch_bounds__(NTHR, 1)
     k_pair_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const TmaLayout L,
@@ -546,7 +529,9 @@ __global__ void __launch_bounds__(NTHR, 1)
   const unsigned bar0 = base + L.bar;
   const int64_t nchunk = J.Ng / PR_CH;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int t = warp / ksplit, ks = warp % ksplit;
+  // warp = ((term * ksplit) + cell half) * 2 + row half: rows 16 mi .. 16 mi + 15 of the term tile
+  const int mi = warp & 1, grp = warp >> 1;
+  const int t = grp / ksplit, ks = grp % ksplit;
   const PairTermDesc T = J.term[t];
   unsigned long long pol = 0;
   if (tid == 0) {
@@ -568,44 +553,47 @@ __global__ void __launch_bounds__(NTHR, 1)
     }
   };
 
-  float2* slot = reinterpret_cast<float2*>(partials) + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * 32;
+  float2* slot = reinterpret_cast<float2*>(partials) + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * 16;
 #pragma unroll
-  for (int q = 0; q < 32; ++q) slot[q] = make_float2(0.f, 0.f);
-  float run[32];
+  for (int q = 0; q < 16; ++q) slot[q] = make_float2(0.f, 0.f);
+  float run[16];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) run[q] = 0.f;
+  for (int q = 0; q < 16; ++q) run[q] = 0.f;
 
   // ldmatrix rows of this lane: matrix j = lane/8, row r = lane%8 of that matrix; every
   // fragment row is congruent to r mod 8, so its swizzled piece is (piece ^ r).
-  // A: matrices (rows 0-7 | 8-15) x (k 0-3 | 4-7): row 16 i + 8 (j&1) + r, piece 2 kk + (j>>1)
+  // A: matrices (rows 0-7 | 8-15) x (k 0-3 | 4-7) of row block mi: row 16 mi + 8 (j&1) + r,
+  //    piece 2 kk + (j>>1); registers hold cells (tq, tq, tq+4, tq+4)
   // B: matrices (ni k 0-3, ni k 4-7, ni+1 k 0-3, ni+1 k 4-7), ni = 2 i: row 8 (2i + (j>>1)) + r,
   //    piece 2 kk + (j&1)
   const int jm = lane >> 3, r = lane & 7, tq = lane & 3;
-  unsigned loffA[2], loffB[2], poffA[4], poffB[4];
+  const unsigned loffA = (unsigned)(16 * mi + 8 * (jm & 1) + r) * 128u;
+  unsigned loffB[2], poffA[4], poffB[4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    loffA[i] = (unsigned)(16 * i + 8 * (jm & 1) + r) * 128u;
-    loffB[i] = (unsigned)(8 * (2 * i + (jm >> 1)) + r) * 128u;
-  }
+  for (int i = 0; i < 2; ++i) loffB[i] = (unsigned)(8 * (2 * i + (jm >> 1)) + r) * 128u;
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
     poffA[kk] = (unsigned)((2 * kk + (jm >> 1)) ^ r) << 4;
     poffB[kk] = (unsigned)((2 * kk + (jm & 1)) ^ r) << 4;
   }
-  const bool xb = T.xslot >= 0, yb = T.yslot >= 0;  // built sides (at most one)
-  const int bslot = xb ? T.xslot : (yb ? T.yslot : 0);
-  const int e0 = (xb || yb) ? J.s_off[bslot] : 0, e1 = (xb || yb) ? J.s_off[bslot + 1] : 0;
-  const unsigned xoff = xb ? 0u : (unsigned)T.xdir * 4096u, yoff = yb ? 0u : (unsigned)T.ydir * 4096u;
+  // terms are normalised so that only the X (A operand) side can be built
+  const bool xb = T.xslot >= 0;
+  const int e0 = xb ? J.s_off[T.xslot] : 0, e1 = xb ? J.s_off[T.xslot + 1] : 0;
+  const unsigned xoff = xb ? 0u : (unsigned)T.xdir * 4096u, yoff = (unsigned)T.ydir * 4096u;
   const int hfirst = ksplit == 2 ? ks : 0, hlast = ksplit == 2 ? ks + 1 : 2;
 
   if (tid == 0 && blockIdx.x < nchunk) issue(blockIdx.x, 0);
-  int since_flush = 0, it = 0;
+  int it = 0;
   for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x, ++it) {
     const int st = it & 1;
     if (tid == 0 && ch + gridDim.x < nchunk) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(ch + gridDim.x, st ^ 1);
     }
+    // slot it % 16 is flushed at the end of this chunk; load it now so that the L2 round
+    // trip overlaps the chunk's work
+    const int fg = it & 15;
+    float2 pre = slot[fg];
     if (!mbar_wait_bounded(bar0 + 8u * st, (unsigned)(it >> 1) & 1u)) {
       s_abort = 1;
       atomicExch(err, 1);
@@ -640,88 +628,78 @@ __global__ void __launch_bounds__(NTHR, 1)
     }
     __syncthreads();
     if (s_abort) break;
-    // (2) this warp's term over its cell half (or both halves)
-    float c[32];
+    // (2) this warp's 16 x 32 block of its term over its cell half (or both halves)
+    float c[16];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) c[q] = 0.f;
+    for (int q = 0; q < 16; ++q) c[q] = 0.f;
     for (int hh = hfirst; hh < hlast; ++hh) {
       const unsigned fh = base + sbo + hh * L.half;
-      float sd[4][2][4];
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) sd[kk][i][e] = 0.f;
-      if (xb)
-        build_side<0>(sd, fh, Hs + hh * 32, e0, e1, loffA, poffA, tq);
-      else if (yb)
-        build_side<1>(sd, fh, Hs + hh * 32, e0, e1, loffB, poffB, tq);
+      const float* hr = Hs + hh * 32 + 2 * tq;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
-        uint32_t av[2][4], bv[2][4];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          if (xb) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) av[i][e] = __float_as_uint(sd[kk][i][e]);
-          } else {
-            ldsm_x4(fh + xoff + loffA[i] + poffA[kk], av[i]);
+        uint32_t av[4], bv[2][4];
+        if (xb) {
+          // built side sum_(c,h) F_c(b, x) H_h(x) for this lane's fragment cells
+          float s4[4] = {0.f, 0.f, 0.f, 0.f};
+          for (int e = e0; e < e1; ++e) {
+            uint32_t v[4];
+            ldsm_x4(fh + (unsigned)J.s_ent[e][0] * 4096u + loffA + poffA[kk], v);
+            const float2 hv = *reinterpret_cast<const float2*>(hr + J.s_ent[e][1] * PR_CH + 8 * kk);
+            s4[0] = fmaf(__uint_as_float(v[0]), hv.x, s4[0]);
+            s4[1] = fmaf(__uint_as_float(v[1]), hv.x, s4[1]);
+            s4[2] = fmaf(__uint_as_float(v[2]), hv.y, s4[2]);
+            s4[3] = fmaf(__uint_as_float(v[3]), hv.y, s4[3]);
           }
-          if (yb) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) bv[i][e] = __float_as_uint(sd[kk][i][e]);
-          } else {
-            ldsm_x4(fh + yoff + loffB[i] + poffB[kk], bv[i]);
-          }
+          for (int e = 0; e < 4; ++e) av[e] = __float_as_uint(s4[e]);
+        } else {
+          ldsm_x4(fh + xoff + loffA + poffA[kk], av);
         }
-        uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) ldsm_x4(fh + yoff + loffB[i] + poffB[kk], bv[i]);
+        uint32_t ah[4], al[4], bh[4][2], bl[4][2];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_tf32(av[e], ah[e], al[e]);
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            split_tf32(av[i][e], ah[i][e], al[i][e]);
-            split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
-          }
+          for (int e = 0; e < 4; ++e) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
         // small products first, pass-major so that consecutive MMAs are independent
 #pragma unroll
-        for (int mi = 0; mi < 2; ++mi)
+        for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
 #pragma unroll
-          for (int ni = 0; ni < 4; ++ni) mma_tf32(c + (mi * 4 + ni) * 4, al[mi], bh[ni]);
+        for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
 #pragma unroll
-        for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-          for (int ni = 0; ni < 4; ++ni) mma_tf32(c + (mi * 4 + ni) * 4, ah[mi], bl[ni]);
-#pragma unroll
-        for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-          for (int ni = 0; ni < 4; ++ni) mma_tf32(c + (mi * 4 + ni) * 4, ah[mi], bh[ni]);
+        for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
       }
     }
 #pragma unroll
-    for (int q = 0; q < 32; ++q) run[q] += c[q];
-    if (++since_flush == PR_FLUSH || ch + gridDim.x >= nchunk) {
-      since_flush = 0;
-      // compensated (Kahan) FP32 sum per slot: (s, e) with the true sum s - e
+    for (int q = 0; q < 16; ++q) run[q] += c[q];
+    // round-robin flush: each FP32 running sum covers at most 16 chunks (1024 cells)
+    {
+      float x = 0.f;
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        float2 v = slot[q];
-        const float y = run[q] - v.y;
-        const float tt = v.x + y;
-        v.y = (tt - v.x) - y;
-        v.x = tt;
-        slot[q] = v;
-        run[q] = 0.f;
-      }
+      for (int q = 0; q < 16; ++q)
+        if (q == fg) {
+          x = run[q];
+          run[q] = 0.f;
+        }
+      kahan_add(pre, x);
+      slot[fg] = pre;
     }
     __syncthreads();
+  }
+  // the running sums not flushed since their last turn
+  if (!s_abort) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) kahan_add(slot[q], run[q]);
   }
   // after an abort the prefetched stage may still be in flight: wait for it (bounded)
   if (tid == 0 && s_abort) mbar_wait_bounded(bar0 + 8u * ((it + 1) & 1), (unsigned)((it + 1) >> 1) & 1u);
 }
 
 static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) {
-  if (j.nb > 32 || j.nterm > TMA_MAXWARP || j.ng < 1 || j.ng > 256 || j.ncomp < 1) return false;
+  if (j.nb > 32 || 2 * j.nterm > TMA_MAXWARP || j.ng < 1 || j.ng > 256 || j.ncomp < 1) return false;
   auto r1024 = [](size_t b) { return (b + 1023) / 1024 * 1024; };
   const size_t fsz = (size_t)j.ncomp * 4096, gsz = r1024((size_t)j.ng * 128);
   const size_t half = fsz + gsz, stage = 2 * half, hs = 2 * stage;
@@ -738,8 +716,8 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   L->ncomp = j.ncomp;
   L->gbox = j.ng;
   L->tx = (unsigned)(2 * (fsz + (size_t)j.ng * 128));
-  *ksplit = 2 * j.nterm <= TMA_MAXWARP ? 2 : 1;
-  *warps = j.nterm * *ksplit;
+  *ksplit = 4 * j.nterm <= TMA_MAXWARP ? 2 : 1;
+  *warps = 2 * j.nterm * *ksplit;
   return true;
 }
 
@@ -802,30 +780,32 @@ size_t pair_scratch_bytes(const PairJob& job) {
   TmaLayout L;
   int ksplit = 1, warps = 1;
   if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps))
-    return (size_t)pair_blocks() * warps * 32 * 32 * sizeof(double) + 256;
+    return (size_t)pair_blocks() * warps * 32 * 16 * sizeof(float2) + 256;
   const PairLaunch c = pair_launch_cfg(j);
   return (size_t)c.nblk * c.warps * 32 * c.TM * c.TN * sizeof(double);
 }
 
 
-// final reduction for k_pair_tma (slots are compensated FP32 pairs): bin (b1, b2) of term t sits in warp t*ksplit+ks, lane
-// (b1%8)*4 + (b2%8)/2, register ((b1/16)*4 + b2/8)*4 + ((b1/8)%2)*2 + b2%2
+// final reduction for k_pair_tma (slots are compensated FP32 pairs (s, e), sum s - e): bin
+// (b1, b2) of term t (after the transpose (b1, b2) -> (b2, b1) of terms with T.tr) sits in warp
+// (t*ksplit + ks)*2 + b1/16, lane (b1%8)*4 + (b2%8)/2, slot (b2/8)*4 + ((b1/8)%2)*2 + b2%2
 __global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int ksplit, int nb, int nout,
                                 double* out) {
   const PairJob& J = c_pj;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= nout * nb * nb) return;
-  const int o = gw / (nb * nb), b1 = (gw / nb) % nb, b2 = gw % nb;
-  const int ln = (b1 % 8) * 4 + (b2 % 8) / 2;
-  const int q = ((b1 / 16) * 4 + b2 / 8) * 4 + ((b1 / 8) % 2) * 2 + (b2 % 2);
+  const int o = gw / (nb * nb), c1 = (gw / nb) % nb, c2 = gw % nb;
   double tot = 0.0;
   for (int e = J.out_ent_off[o]; e < J.out_ent_off[o + 1]; ++e) {
     const int t = J.out_ent_term[e];
+    const int b1 = J.term[t].tr ? c2 : c1, b2 = J.term[t].tr ? c1 : c2;
+    const int ln = (b1 % 8) * 4 + (b2 % 8) / 2;
+    const int q = (b2 / 8) * 4 + ((b1 / 8) % 2) * 2 + (b2 % 2);
     double s = 0.0;
     for (int ks = 0; ks < ksplit; ++ks) {
-      const int w = t * ksplit + ks;
+      const int w = (t * ksplit + ks) * 2 + b1 / 16;
       for (int c = lane; c < nblk; c += 32) {
-        const float2 v = reinterpret_cast<const float2*>(partials)[(((size_t)c * warps + w) * 32 + ln) * 32 + q];
+        const float2 v = reinterpret_cast<const float2*>(partials)[(((size_t)c * warps + w) * 32 + ln) * 16 + q];
         s += (double)v.x - (double)v.y;
       }
     }
@@ -870,8 +850,23 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
   TmaLayout L;
   int ksplit = 1, warps = 1;
   if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) {
+    // the tensor-core kernel builds only A operands: a term with a built Y side is computed
+    // transposed (Y X^T) and read back transposed by the final reduction
+    PairJob jt = j;
+    for (int t = 0; t < jt.nterm; ++t) {
+      PairTermDesc& T = jt.term[t];
+      T.tr = 0;
+      if (T.yslot >= 0) {
+        std::swap(T.xoff, T.yoff);
+        std::swap(T.xcnt, T.ycnt);
+        std::swap(T.xdir, T.ydir);
+        std::swap(T.xslot, T.yslot);
+        T.tr = 1;
+      }
+    }
+    BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &jt, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
     const int nblk = pair_blocks();
-    const size_t need = (size_t)nblk * warps * 32 * 32 * sizeof(double);
+    const size_t need = (size_t)nblk * warps * 32 * 16 * sizeof(float2);
     int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + need);
     BISP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb);
