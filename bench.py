@@ -130,6 +130,10 @@ def run_gpu(args, w, rank, world):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
     g_dev = {k: t(v) for k, v in gal.items()}
     r_dev = {k: t(v) for k, v in ran.items()} if ran is not None else None
+    # end-to-end inputs live in pinned host memory (copied in by the library every step)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
+    gal = {k: pin(v) for k, v in gal.items()}
+    ran = {k: pin(v) for k, v in ran.items()} if ran is not None else None
     stream = torch.cuda.Stream()
     plan = bisp.Plan(w["N"], w["L"], w["edges"], w["ells"], los="local" if w["kind"] == "survey" else "global",
                      observer=w.get("observer", (0, 0, 0)), mas=w["mas"], interlace=w["interlace"],
@@ -188,7 +192,8 @@ def run_gpu(args, w, rank, world):
     nbins = n_bins_output(w)
     ms_step = ms / args.steps
     value = world * nbins / (ms_step / 1e3)
-    h2d = sum(v.nbytes for v in gal.values()) + (sum(v.nbytes for v in ran.values()) if ran else 0)
+    h2d = sum(v.numel() * v.element_size() for v in gal.values()) + (
+        sum(v.numel() * v.element_size() for v in ran.values()) if ran else 0)
     d2h = (4 if w["window"] else 2) * len(w["ells"]) * (len(w["edges"]) - 1) ** 2 * 8 + (len(w["edges"]) - 1) * 8
     peaks = {}
     try:

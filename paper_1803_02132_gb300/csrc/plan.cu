@@ -207,6 +207,7 @@ struct bisp_plan {
   Catalog cat[2];
   // measurement buffers
   DBuf pass_spec[2], gf[2], qf, pool, invscr, pairscr, pairout, zpart;
+  DBuf ws;  // assignment workspace (grow-only)
   size_t bytes = 0;
   // bookkeeping
   double alpha = 0.0, normI = 0.0;
@@ -551,17 +552,56 @@ void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const 
   const int nchan = (int)ch.size();
   if (nchan > 32) fail(BISP_EUNSUPPORTED, "too many channels");
   const int ilv = P->interlace ? 1 : 0;
-  // temporaries
-  size_t tb = 0;
-  DBuf din, keys, idx, frac, vals, skeys, perm, sfrac, svals, sortscr, cells, scanscr, part, bad, mesh1;
+  // workspace: one grow-only device arena kept by the plan (no allocation once it is large
+  // enough).  Region 1 holds what is dead after the particle gather (host input copy, unsorted
+  // keys, indices, offsets, channel values, sort scratch) and is then reused for the
+  // interlaced mesh; region 2 holds what the deposit still reads.
+  const int64_t nn = std::max<int64_t>(n, 1);
+  const int nsum = 1 + (int)P->dch.size();
+  const int pblk = prep_blocks(n);
   const size_t sortb = radix_sort_scratch_bytes(n);
-  const size_t need = (ptr_is_device ? 0 : (size_t)n * 20) + (size_t)n * (4 * 4 + 16 * 2 + 8 * nchan) + sortb +
-                      (size_t)(Ng + 2) * 8 + scan_scratch_bytes(Ng + 1) + (size_t)nchan * Ng * 4 * (1 + ilv);
-  admit(P, need > C.spec.n ? need - C.spec.n : 0);
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_din = ptr_is_device ? 0 : al((size_t)n * 4 * (3 + (w ? 1 : 0) + (nbar ? 1 : 0)));
+  const size_t b_keys = al(nn * 4), b_frac = al(nn * 16), b_vals = al((size_t)nn * 4 * nchan), b_sort = al(sortb);
+  const size_t r1a = b_din + 2 * b_keys + b_frac + b_vals + b_sort;
+  const size_t b_mesh1 = ilv ? al((size_t)nchan * Ng * 4) : 0;
+  const size_t r1 = std::max(r1a, b_mesh1);
+  const size_t b_cells = al((size_t)(Ng + 1) * 4 * 2), b_scan = al(scan_scratch_bytes(Ng + 1));
+  const size_t b_part = al(std::max<size_t>((size_t)pblk * nsum * 8, 1024 * 8));
+  const size_t r2 = 2 * b_keys + b_cells + b_scan + b_frac + b_vals + b_part + 256;
+  // The field pool of the measurement is idle during an assignment (calls on a plan never
+  // overlap), so the arena borrows it when it is large enough.
+  const size_t spec_need = (size_t)nchan * Ng * 4;
+  const bool in_pool = P->pool.n >= r1 + r2;
+  admit(P, (!in_pool && r1 + r2 > P->ws.n ? r1 + r2 - P->ws.n : 0) +
+               (spec_need > C.spec.n ? spec_need - C.spec.n : 0));
+  if (!in_pool) P->ws.ensure(r1 + r2, &P->bytes);
+  unsigned char* const arena = in_pool ? P->pool.as<unsigned char>() : P->ws.as<unsigned char>();
+  unsigned char* wp = arena;
+  unsigned char* const mesh1p = wp;  // overlays region 1 after the gather
+  auto take = [&](size_t bytes) {
+    unsigned char* q = wp;
+    wp += bytes;
+    return q;
+  };
+  float* dinp = reinterpret_cast<float*>(take(b_din));
+  uint32_t* keysp = reinterpret_cast<uint32_t*>(take(b_keys));
+  uint32_t* idxp = reinterpret_cast<uint32_t*>(take(b_keys));
+  float4* fracp = reinterpret_cast<float4*>(take(b_frac));
+  float* valsp = reinterpret_cast<float*>(take(b_vals));
+  void* sortp = take(b_sort);
+  wp = arena + r1;
+  uint32_t* skeysp = reinterpret_cast<uint32_t*>(take(b_keys));
+  uint32_t* permp = reinterpret_cast<uint32_t*>(take(b_keys));
+  uint32_t* cellsp = reinterpret_cast<uint32_t*>(take(b_cells));
+  void* scanp = take(b_scan);
+  float4* sfracp = reinterpret_cast<float4*>(take(b_frac));
+  float* svalsp = reinterpret_cast<float*>(take(b_vals));
+  double* partp = reinterpret_cast<double*>(take(b_part));
+  int* badp = reinterpret_cast<int*>(take(256));
   const float *dxyz = xyz, *dw = w, *dnb = nbar;
   if (!ptr_is_device && n > 0) {
-    din.ensure((size_t)n * 4 * (3 + (w ? 1 : 0) + (nbar ? 1 : 0)), &tb);
-    float* q = din.as<float>();
+    float* q = dinp;
     BISP_CUDA(cudaMemcpyAsync(q, xyz, (size_t)n * 12, cudaMemcpyHostToDevice, s));
     dxyz = q;
     q += 3 * n;
@@ -575,16 +615,7 @@ void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const 
       dnb = q;
     }
   }
-  const int64_t nn = std::max<int64_t>(n, 1);
-  keys.ensure(nn * 4, &tb);
-  idx.ensure(nn * 4, &tb);
-  frac.ensure(nn * 16, &tb);
-  vals.ensure((size_t)nn * 4 * nchan, &tb);
-  const int nsum = 1 + (int)P->dch.size();
-  const int pblk = prep_blocks(n);
-  part.ensure((size_t)pblk * nsum * 8, &tb);
-  bad.ensure(64, &tb);
-  BISP_CUDA(cudaMemsetAsync(bad.p, 0, 64, s));
+  BISP_CUDA(cudaMemsetAsync(badp, 0, sizeof(int), s));
   PrepArgs a{};
   a.xyz = dxyz;
   a.w = dw;
@@ -600,13 +631,13 @@ void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const 
   a.nchan = nchan;
   for (int c = 0; c < nchan; ++c) a.chan[c] = ch[c];
   a.ynorm = P->ynorm.as<float>();
-  a.keys = keys.as<uint32_t>();
-  a.idx = idx.as<uint32_t>();
-  a.frac = frac.as<float4>();
-  a.vals = vals.as<float>();
-  a.partials = part.as<double>();
+  a.keys = keysp;
+  a.idx = idxp;
+  a.frac = fracp;
+  a.vals = valsp;
+  a.partials = partp;
   a.nsum = nsum;
-  a.bad = bad.as<int>();
+  a.bad = badp;
   if (n > 0) {
     launch_prep(a, s);
     ++launches;
@@ -614,8 +645,8 @@ void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const 
   int nbad = 0;
   std::vector<double> hp((size_t)pblk * nsum, 0.0);
   if (n > 0) {
-    BISP_CUDA(cudaMemcpyAsync(&nbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    BISP_CUDA(cudaMemcpyAsync(hp.data(), part.p, hp.size() * 8, cudaMemcpyDeviceToHost, s));
+    BISP_CUDA(cudaMemcpyAsync(&nbad, badp, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BISP_CUDA(cudaMemcpyAsync(hp.data(), partp, hp.size() * 8, cudaMemcpyDeviceToHost, s));
     BISP_CUDA(cudaStreamSynchronize(s));
   }
   if (nbad) {
@@ -630,75 +661,49 @@ void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const 
   // sort by home cell
   int bits = 0;
   while ((1LL << bits) < Ng) ++bits;
-  skeys.ensure(nn * 4, &tb);
-  perm.ensure(nn * 4, &tb);
-  sortscr.ensure(sortb, &tb);
-  radix_sort(keys.as<uint32_t>(), idx.as<uint32_t>(), skeys.as<uint32_t>(), perm.as<uint32_t>(), n, bits, sortscr.p,
-             s, &launches);
+  radix_sort(keysp, idxp, skeysp, permp, n, bits, sortp, s, &launches);
   // cell starts
-  cells.ensure((size_t)(Ng + 1) * 4 * 2, &tb);
-  uint32_t* counts = cells.as<uint32_t>();
+  uint32_t* counts = cellsp;
   uint32_t* cstart = counts + (Ng + 1);
   BISP_CUDA(cudaMemsetAsync(counts, 0, (size_t)(Ng + 1) * 4, s));
-  launch_count_cells(skeys.as<uint32_t>(), n, counts, s);
+  launch_count_cells(skeysp, n, counts, s);
   ++launches;
-  scanscr.ensure(scan_scratch_bytes(Ng + 1), &tb);
-  exclusive_scan_u32(counts, cstart, Ng + 1, scanscr.p, s, &launches);
+  exclusive_scan_u32(counts, cstart, Ng + 1, scanp, s, &launches);
   // particles in sorted order
-  sfrac.ensure(nn * 16, &tb);
-  svals.ensure((size_t)nn * 4 * nchan, &tb);
-  launch_gather_particles(perm.as<uint32_t>(), n, frac.as<float4>(), vals.as<float>(), nchan, sfrac.as<float4>(),
-                          svals.as<float>(), s);
+  launch_gather_particles(permp, n, fracp, valsp, nchan, sfracp, svalsp, s);
   ++launches;
-  keys.release(&tb);
-  idx.release(&tb);
-  frac.release(&tb);
-  vals.release(&tb);
-  sortscr.release(&tb);
-  din.release(&tb);
-  // deposit onto the meshes; mesh 0 becomes the spectrum storage
-  C.spec.ensure((size_t)nchan * Ng * 4, &P->bytes);
-  if (ilv) mesh1.ensure((size_t)nchan * Ng * 4, &tb);
+  // deposit onto the meshes; mesh 0 becomes the spectrum storage, mesh 1 overlays region 1
+  C.spec.ensure(spec_need, &P->bytes);
+  float* mesh1 = ilv ? reinterpret_cast<float*>(mesh1p) : nullptr;
   DepositArgs da{};
   da.cell_start = cstart;
-  da.keys = skeys.as<uint32_t>();
-  da.frac = sfrac.as<float4>();
-  da.vals = svals.as<float>();
+  da.keys = skeysp;
+  da.frac = sfracp;
+  da.vals = svalsp;
   da.n = n;
   da.N = N;
   da.mas = P->mas;
   da.interlace = ilv;
   da.nchan = nchan;
   da.mesh0 = C.spec.as<float>();
-  da.mesh1 = ilv ? mesh1.as<float>() : nullptr;
+  da.mesh1 = mesh1;
   launch_deposit(da, s, &launches);
-  sfrac.release(&tb);
-  svals.release(&tb);
-  cells.release(&tb);
-  scanscr.release(&tb);
-  skeys.release(&tb);
-  perm.release(&tb);
   if (P->debug_mesh) {
     C.dbg_mesh.ensure((size_t)nchan * Ng * 4, &P->bytes);
     BISP_CUDA(cudaMemcpyAsync(C.dbg_mesh.p, C.spec.p, (size_t)nchan * Ng * 4, cudaMemcpyDeviceToDevice, s));
   }
   C.sumR3 = 0.0;
   if (which == BISP_RANDOMS) {
-    part.ensure(1024 * 8, &tb);
-    const int nbk = launch_sum_cubes(C.spec.as<float>() + (size_t)P->d00 * Ng, Ng, part.as<double>(), s);
+    const int nbk = launch_sum_cubes(C.spec.as<float>() + (size_t)P->d00 * Ng, Ng, partp, s);
     ++launches;
     std::vector<double> hr(nbk);
-    BISP_CUDA(cudaMemcpyAsync(hr.data(), part.p, nbk * 8, cudaMemcpyDeviceToHost, s));
+    BISP_CUDA(cudaMemcpyAsync(hr.data(), partp, nbk * 8, cudaMemcpyDeviceToHost, s));
     BISP_CUDA(cudaStreamSynchronize(s));
     for (double v : hr) C.sumR3 += v;
   }
-  forward_fft(C.spec.as<float>(), ilv ? mesh1.as<float>() : nullptr, nchan, N, P->mas, P->tw.as<float2>(),
-              P->winv.as<float>(), s, &launches);
+  forward_fft(C.spec.as<float>(), mesh1, nchan, N, P->mas, P->tw.as<float2>(), P->winv.as<float>(), s, &launches);
   BISP_CUDA(cudaEventRecord(P->ev1, s));
   BISP_CUDA(cudaStreamSynchronize(s));
-  mesh1.release(&tb);
-  part.release(&tb);
-  bad.release(&tb);
   float ms = 0.f;
   BISP_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
   C.ms = ms;
@@ -859,7 +864,10 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
       add(P->gf[k], (size_t)nD * Ng * 4);
     }
     add(P->qf, (size_t)npass * nD * Ng * 4);
-    add(P->pool, (size_t)nb * P->comps.size() * Ng * 4);
+    const size_t pool_need = (size_t)nb * P->comps.size() * Ng * 4;
+    // the assignment arena moves into the pool from now on: free it before admission
+    if (pool_need > P->pool.n) P->ws.release(&P->bytes);
+    add(P->pool, pool_need);
     admit(P, need);
   }
   PassState ps[2];
@@ -1082,7 +1090,7 @@ void destroy(bisp_plan* P) {
   if (!P) return;
   size_t* t = &P->bytes;
   for (auto* d : {&P->tw, &P->winv, &P->ynorm, &P->cw2, &P->qlo_d, &P->qhi_d, &P->zmodes, &P->zmode_off, &P->pool, &P->invscr, &P->pairscr,
-                  &P->pairout, &P->zpart})
+                  &P->pairout, &P->zpart, &P->ws})
     d->release(t);
   for (int k = 0; k < 2; ++k) {
     P->cat[k].spec.release(t);
