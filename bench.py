@@ -212,7 +212,7 @@ def run_gpu(args, w, rank, world):
         "e2e": {"value": world * nbins / (ms_e2e / args.steps / 1e3), "unit": "bins/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": "k_pair_tc (mesh sum of F F G, Eq. bi_estimator_FFTs)",
+        "roofline": {"bound": "hbm", "kernel": "k_pair_tma (mesh sum of F F G, Eq. bi_estimator_FFTs)",
                      "achieved": pair_gbs, "peak": hbm, "unit": "GB/s",
                      "frac": (pair_gbs / hbm) if pair_gbs else None,
                      "traffic": pair_traffic(pair_bytes / max(pair_launches, 1)),
@@ -243,12 +243,12 @@ def config_of(name, w, world):
 
 
 def pair_traffic(alg_bytes_per_launch):
-    """DRAM bytes per k_pair_tc launch: the measured DRAM/algorithmic ratio of a small-case
+    """DRAM bytes per k_pair_tma launch: the measured DRAM/algorithmic ratio of a small-case
     ncu capture of the same kernel, times this launch's algorithmic bytes (traffic grows with
     the number of mesh cells).  None when the kernel source changed since the capture."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "k_pair_tc_traffic.json")))
-        src = open(os.path.join(ROOT, "paper_1803_02132_gb300", "csrc", "measure.cu"), "rb").read()
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_pair_tma_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_1803_02132_gb300", "csrc", "pair.cu"), "rb").read()
         if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
             return None
         return rec["dram_bytes_per_algorithmic_byte"] * alg_bytes_per_launch
@@ -280,11 +280,15 @@ def cpu_baseline(args, w):
         gal, ran = {"xyz": synthcat.periodic_catalog(N, L, int(w["n_p"] * frac), 7)}, None
         p = E.Params(N=N, L=L, edges=edges, ells=w["ells"], los="global",
                      mas={"NGP": 1, "CIC": 2, "TSC": 3}[w["mas"]], interlace=w["interlace"])
+    # repeat the sample until about 10 s of CPU work (at most 6 repetitions)
     t0 = time.perf_counter()
     c0 = time.process_time()
-    E.measure(p, gal, ran)
-    dt = time.perf_counter() - t0
-    cpu = time.process_time() - c0
+    reps = 0
+    while reps < 6 and (reps == 0 or time.perf_counter() - t0 < 10.0):
+        E.measure(p, gal, ran)
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    cpu = (time.process_time() - c0) / reps
     nb = len(edges) - 1
     nbins = sum(nb * (nb + 1) // 2 if l1 == l2 else nb * nb for (l1, l2, _) in w["ells"]) * (2 if w["window"] else 1)
     # threads actually used: process CPU time over wall time (numpy's FFT and bincount run on
@@ -294,7 +298,7 @@ def cpu_baseline(args, w):
     # cells, so the sample's rate is scaled by the cell ratio to the workload's mesh
     return {"value": nbins / dt * frac, "unit": "bins/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle on the same recipe at {N}^3 (1/{int(round(1 / frac))} of the cells and particles), "
-                      f"{nb} bins below that mesh's Nyquist, {nbins} bins in {dt:.1f} s "
+                      f"{nb} bins below that mesh's Nyquist, {nbins} bins in {dt:.1f} s (mean of {reps} runs) "
                       f"({nbins / dt:.3g} bins/s at {N}^3); value = that rate x {N}^3/{w['N']}^3",
             "sample_bins_per_s": nbins / dt, "seconds": dt, "cpu_seconds": cpu}
 
