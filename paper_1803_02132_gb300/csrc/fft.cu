@@ -388,7 +388,9 @@ struct RegZ {
   static constexpr int NH = N / 2;
   static constexpr int A = regz_a(NH);  // threads per row
   static constexpr int B = NH / A;      // values per thread (a multiple of A)
-  static constexpr int ROWS = 256 / A;  // rows per CTA (256 threads)
+  static constexpr int ROWS = 256 / A;  // rows per group (256 threads)
+  // row groups per CTA (the twiddle tables are built once per CTA); N^2 / ROWS is a power of two
+  static constexpr int GROUPS = (N * N / ROWS) >= 8 ? 8 : (N * N / ROWS);
   // transpose buffer, then e^{2 pi i j / NH} (NH entries) and e^{2 pi i j / N} (NH entries)
   static constexpr size_t SMEM = ((size_t)ROWS * B * (A + 1) + 2 * NH) * sizeof(float2);
 };
@@ -410,44 +412,48 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
   const InvGeo g = inv_geo(N, Bt.P, Geo<N>::LB);
   const int f = blockIdx.y;
   const int l = threadIdx.x / A, a = threadIdx.x % A;
-  const size_t row = (size_t)blockIdx.x * ROWS + l;
-  const float2* x = t2all + (size_t)f * g.t2 + row * g.Pz;
-  const int P = Bt.P;
-  float2 v[B];
+  constexpr int GROUPS = RegZ<N>::GROUPS;
+  for (int grp = 0; grp < GROUPS; ++grp) {
+    const size_t row = ((size_t)blockIdx.x * GROUPS + grp) * ROWS + l;
+    const float2* x = t2all + (size_t)f * g.t2 + row * g.Pz;
+    const int P = Bt.P;
+    float2 v[B];
 #pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int n = a + A * b;
-    // X[k], k <= P (and X[0] real); X[NH] = 0 (Nyquist dropped)
-    float2 xa = n <= P ? x[n] : make_float2(0.f, 0.f);
-    const int nm = NH - n;
-    float2 xb = (n > 0 && nm <= P) ? x[nm] : make_float2(0.f, 0.f);
-    if (n == 0) xa.y = 0.f;
-    // Z[n] = (X[n] + X*[NH-n]) + i (X[n] - X*[NH-n]) e^{2 pi i n / N}
-    const float2 sp = make_float2(xa.x + xb.x, xa.y - xb.y);
-    const float2 dm = make_float2(xa.x - xb.x, xa.y + xb.y);
-    const float2 t = cmul(dm, wN[n]);
-    v[b] = make_float2(sp.x - t.y, sp.y + t.x);
-  }
-  DftReg<B, +1>::run(v, tw);
-  // twiddle e^{+2 pi i a kb / NH} and transpose: element (a, kb) -> sbuf[l][kb][a]
+    for (int b = 0; b < B; ++b) {
+      const int n = a + A * b;
+      // X[k], k <= P (and X[0] real); X[NH] = 0 (Nyquist dropped)
+      float2 xa = n <= P ? x[n] : make_float2(0.f, 0.f);
+      const int nm = NH - n;
+      float2 xb = (n > 0 && nm <= P) ? x[nm] : make_float2(0.f, 0.f);
+      if (n == 0) xa.y = 0.f;
+      // Z[n] = (X[n] + X*[NH-n]) + i (X[n] - X*[NH-n]) e^{2 pi i n / N}
+      const float2 sp = make_float2(xa.x + xb.x, xa.y - xb.y);
+      const float2 dm = make_float2(xa.x - xb.x, xa.y + xb.y);
+      const float2 t = cmul(dm, wN[n]);
+      v[b] = make_float2(sp.x - t.y, sp.y + t.x);
+    }
+    DftReg<B, +1>::run(v, tw);
+    if (grp > 0) __syncthreads();  // the previous group's stage 2 has read the transpose buffer
+    // twiddle e^{+2 pi i a kb / NH} and transpose: element (a, kb) -> sbuf[l][kb][a]
 #pragma unroll
-  for (int kb = 0; kb < B; ++kb) {
-    sbuf[(l * B + kb) * LDT + a] = cmul(v[kb], wNH[(a * kb) & (NH - 1)]);
-  }
-  __syncthreads();
-  // stage 2: thread a handles kb = a + A r, r < B / A, an A-point DFT over a' each
-  float* out = Bt.f[f].out + row * N;
+    for (int kb = 0; kb < B; ++kb) {
+      sbuf[(l * B + kb) * LDT + a] = cmul(v[kb], wNH[(a * kb) & (NH - 1)]);
+    }
+    __syncthreads();
+    // stage 2: thread a handles kb = a + A r, r < B / A, an A-point DFT over a' each
+    float* out = Bt.f[f].out + row * N;
 #pragma unroll
-  for (int r = 0; r < B / A; ++r) {
-    const int kb = a + A * r;
-    float2 u[A];
+    for (int r = 0; r < B / A; ++r) {
+      const int kb = a + A * r;
+      float2 u[A];
 #pragma unroll
-    for (int aa = 0; aa < A; ++aa) u[aa] = sbuf[(l * B + kb) * LDT + aa];
-    DftReg<A, +1>::run(u, tw);
+      for (int aa = 0; aa < A; ++aa) u[aa] = sbuf[(l * B + kb) * LDT + aa];
+      DftReg<A, +1>::run(u, tw);
 #pragma unroll
-    for (int ka = 0; ka < A; ++ka) {
-      const int m = kb + B * ka;
-      reinterpret_cast<float2*>(out)[m] = u[ka];
+      for (int ka = 0; ka < A; ++ka) {
+        const int m = kb + B * ka;
+        reinterpret_cast<float2*>(out)[m] = u[ka];
+      }
     }
   }
 }
@@ -548,7 +554,7 @@ static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStr
   BISP_CHECK_LAUNCH();
   using RZ = RegZ<N>;
   smem_attr(k_inv_z_reg<N>, RZ::SMEM);
-  k_inv_z_reg<N><<<dim3(N * N / RZ::ROWS, b.nf), 256, RZ::SMEM, s>>>(t2, tw);
+  k_inv_z_reg<N><<<dim3(N * N / (RZ::ROWS * RZ::GROUPS), b.nf), 256, RZ::SMEM, s>>>(t2, tw);
   BISP_CHECK_LAUNCH();
   if (launches) *launches += 3;
 }
