@@ -44,7 +44,7 @@ class _Info(C.Structure):
                 ("n_data", C.c_int64), ("n_randoms", C.c_int64), ("device_bytes", C.c_size_t),
                 ("kernel_launches", C.c_int), ("ms_assign_data", C.c_double), ("ms_assign_randoms", C.c_double),
                 ("ms_measure", C.c_double), ("ms_pair", C.c_double), ("pair_bytes", C.c_double),
-                ("pair_launches", C.c_int)]
+                ("pair_launches", C.c_int), ("pair_kernel", C.c_int)]
 
 
 def _load():

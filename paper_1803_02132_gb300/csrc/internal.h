@@ -149,7 +149,8 @@ struct PairTermDesc {
   int xoff, xcnt, yoff, ycnt;  // recipe entries of the two sides
   int xdir, ydir;              // side is a bare component field (index), or -1
   int xslot, yslot;            // shared-memory slot of a side built per chunk, or -1
-  int tr;                      // 1: computed as Y X^T (tensor-core kernel), read back transposed
+  int tr;                      // 1: computed as Y X^T (tensor-core kernels), read back transposed
+  int grp, quad;               // tcgen05 kernel: M = 128 tile and its 32-row quarter
 };
 struct PairJob {
   const float* fields;    // component field (b, c) at fields + (b*ncomp + c) * Ng
@@ -179,7 +180,9 @@ struct PairJob {
 };
 // Result: out[o][b1][b2] = sum_x sum_{t in o} X_t(x;b1) Y_t(x;b2)   (FP64)
 void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scratch_bytes,
-                 cudaStream_t s, int* launches);
+                 cudaStream_t s, int* launches, int* kernel = nullptr);
 size_t pair_scratch_bytes(const PairJob& job);
+// true when the pair kernel in use prefers one launch per G set (at most 8 terms a launch)
+bool pair_split_gsets();
 
 }  // namespace bisp

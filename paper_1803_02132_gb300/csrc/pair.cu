@@ -14,7 +14,9 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -698,6 +700,309 @@ __global__ void __launch_bounds__(NTHR, 1)
   if (tid == 0 && s_abort) mbar_wait_bounded(bar0 + 8u * ((it + 1) & 1), (unsigned)((it + 1) >> 1) & 1u);
 }
 
+// ------------------------------------------------------------------------------------
+// 5th-generation tensor-core variant (tcgen05; nb <= 32, at most 4 bare components and 8
+// terms per launch).  Chunks of 32 cells are staged by the same TMA tensor maps as
+// k_pair_tma.  Terms are normalised so that the built side is X and the bare side Y.  One
+// tcgen05.mma per k step and pass covers the whole launch: A (M = 128) stacks the bare
+// components (32 bins each), B (N = 32 x terms) stacks the built sides, and the useful
+// 32 x 32 blocks of D (TMEM: lane = A row, column = B row) are those pairing a term's built
+// side with its own bare component.  Per chunk every warp (1) forms the H rows, (2) builds
+// X = sum_(c,h) F_c H_h and splits it, and the bare sides, into TF32 hi/lo tiles in the
+// K-major 128-byte-swizzled layout the MMA reads; then one thread issues 4 k steps x 3
+// passes (lo.hi, hi.lo, hi.hi) into a TMEM accumulator double-buffered over chunks.  While
+// the tensor cores work on chunk i the warps read chunk i-1 back with tcgen05.ld (the warp
+// of a term sits in the TMEM lane quarter of its bare component) into FP32 running sums
+// over at most UM_FLUSH chunks, which go round robin into lane-owned Kahan (sum,
+// compensation) slots.  The accumulator restarts every chunk.  Measured on GB300: an
+// M = 128 kind::tf32 MMA costs ~48 cycles up to N = 64 and reaches ~2000 MAC/cycle from
+// N = 128, so few wide MMAs beat many narrow ones.  Every wait is bounded in time; TMEM is
+// freed on every path.  On the 512^3 survey jobs this kernel is bound by shared-memory
+// bandwidth (the three TF32 passes need materialised hi/lo tiles: ~230 KB of shared-memory
+// traffic per 32-cell chunk between the side builds and the MMA operand reads) and runs
+// slower than k_pair_tma, which keeps the split in registers; it is therefore opt-in.
+// ------------------------------------------------------------------------------------
+constexpr int UM_WARPS = 16;
+constexpr int UM_CH = 32;     // cells per chunk
+constexpr int UM_FLUSH = 32;  // chunks per FP32 running sum (1024 cells)
+constexpr int UM_MAXB = 4;    // bare components (A = 4 x 32 rows)
+constexpr int UM_MAXS = 8;    // terms (B = 8 x 32 rows at most)
+
+struct UmmaPlan {
+  int nslots, nbare;
+  int bare_comp[UM_MAXB];  // component of each 32-row A block
+  int slot_side[UM_MAXS];  // side (s_off index) built into B block k
+  int warp_slot[UM_WARPS];  // term slot read back by each warp, or -1
+};
+__constant__ UmmaPlan c_um;
+
+struct UmmaLayout {
+  unsigned fsz, stage;               // F blocks (ncomp x 4096), raw stage (F + G block)
+  unsigned ob, obsz;                 // operand buffers: offset, bytes each
+  unsigned a_hi, a_lo, b_hi, b_lo;   // tiles within an operand buffer
+  unsigned hs, bar, tptr, bytes, tx, tcols;
+  unsigned idesc, dcols;             // instruction descriptor (N = 32 x terms), columns per D
+  int ncomp, nob;
+};
+
+__device__ __forceinline__ uint64_t umma_sdesc(unsigned addr) {
+  // K-major, 128-byte swizzle: start >> 4, stride between 8-row groups 1024 B, version 1
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// kind::tf32, FP32 accumulate, K-major A and B, M = 128, N = n
+__host__ __device__ constexpr uint32_t umma_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(unsigned dcol, uint64_t da, uint64_t db, unsigned idesc, unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld32(unsigned ta, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float4 split_hi4(float4 v) {
+  return make_float4(__uint_as_float(__float_as_uint(v.x) & 0xffffe000u), __uint_as_float(__float_as_uint(v.y) & 0xffffe000u),
+                     __uint_as_float(__float_as_uint(v.z) & 0xffffe000u), __uint_as_float(__float_as_uint(v.w) & 0xffffe000u));
+}
+
+__global__ void __launch_bounds__(UM_WARPS * 32, 1)
+    k_pair_umma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const UmmaLayout L,
+                float2* slots, int* err) {
+  const PairJob& J = c_pj;
+  const UmmaPlan& U = c_um;
+  extern __shared__ unsigned char dsm[];
+  __shared__ int s_abort;
+  const unsigned raw0 = smem_u32(dsm);
+  const unsigned base = (raw0 + 1023u) & ~1023u;
+  unsigned char* const gb = dsm + (base - raw0);
+  float* const Hs = reinterpret_cast<float*>(gb + L.hs);
+  const unsigned barF = base + L.bar, barM = barF + 16;  // TMA stages full[2], MMA done[2]
+  const int64_t nchunk = J.Ng / UM_CH;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(base + L.tptr), "r"(L.tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  unsigned long long pol = 0;
+  if (tid == 0) {
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    for (int k = 0; k < 4; ++k) mbar_init(barF + 8u * k, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  const unsigned tmem = *reinterpret_cast<const unsigned*>(gb + L.tptr);
+  auto issue = [&](int64_t ch, int st) {  // thread 0 only
+    const unsigned bar = barF + 8u * st;
+    mbar_expect_tx(bar, L.tx);
+    const unsigned rb = base + st * L.stage;
+    const int x = (int)(ch * UM_CH);
+    for (int c = 0; c < L.ncomp; ++c) tma_load_3d(rb + (unsigned)c * 4096u, &tmF, x, c, 0, bar, pol);
+    tma_load_2d(rb + L.fsz, &tmG, x, 0, bar, pol);
+  };
+  // readout role: the warp of term slot k sits in the lane quarter of its bare component
+  // (lane = bin of the bare side, run[] = bins of the built side)
+  const int rslot = U.warp_slot[warp];
+  const bool reader = rslot >= 0;
+  float2* slot = slots + (((size_t)blockIdx.x * UM_WARPS + warp) * 32 + lane) * 32;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) slot[q] = make_float2(0.f, 0.f);
+  float run[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) run[q] = 0.f;
+  auto readout = [&](int itr) {  // chunk with iteration index itr, all reader lanes
+    uint32_t r[32];
+    tmem_ld32(tmem + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(itr & 1) * L.dcols + (unsigned)rslot * 32u, r);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) run[q] += __uint_as_float(r[q]);
+  };
+  const unsigned mnb = (unsigned)((0x100000000ull + 8 * J.nb - 1) / (8 * J.nb));  // j / (8 nb) = umulhi(j, mnb)
+  int it = 0, tma_issued = 0;
+  if (tid == 0) {
+    if (blockIdx.x < nchunk) issue(blockIdx.x, 0), ++tma_issued;
+    if (blockIdx.x + gridDim.x < nchunk) issue(blockIdx.x + gridDim.x, 1), ++tma_issued;
+  }
+  for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x, ++it) {
+    const int st = it & 1;
+    const unsigned obase = base + L.ob + (unsigned)(L.nob == 2 ? st : 0) * L.obsz;
+    unsigned char* const og = gb + (obase - base);
+    if (!mbar_wait_bounded(barF + 8u * st, (unsigned)(it >> 1) & 1u)) {
+      s_abort = 1;
+      atomicExch(err, 1);
+    }
+    const unsigned char* const rs = gb + st * L.stage;  // raw stage (generic pointer)
+    const int fq = it & (UM_FLUSH - 1);
+    float2 pre = reader ? slot[fq] : make_float2(0.f, 0.f);
+    // (1) H rows of this chunk: [h][32 cells]
+    for (int i = tid; i < (J.nh << 3); i += blockDim.x) {
+      const int h = i >> 3, p = i & 7;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int e = J.h_off[h]; e < J.h_off[h + 1]; ++e) {
+        const PairRecipe R = J.h_ent[e];
+        if (R.g >= 0) {
+          const float4 gv = *reinterpret_cast<const float4*>(rs + L.fsz + swz(R.g, p));
+          v.x = fmaf(R.coef, gv.x, v.x);
+          v.y = fmaf(R.coef, gv.y, v.y);
+          v.z = fmaf(R.coef, gv.z, v.z);
+          v.w = fmaf(R.coef, gv.w, v.w);
+        } else {
+          v.x += R.coef;
+          v.y += R.coef;
+          v.z += R.coef;
+          v.w += R.coef;
+        }
+      }
+      *reinterpret_cast<float4*>(Hs + h * UM_CH + 4 * p) = v;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    // (2) with a single operand buffer, the previous chunk's MMAs must have read it
+    if (L.nob == 1 && it > 0 && !mbar_wait_bounded(barM + 8u * ((it - 1) & 1), (unsigned)((it - 1) >> 1) & 1u)) {
+      s_abort = 1;
+      atomicExch(err, 2);
+    }
+    // built sides, split into TF32 hi / lo tiles: one thread per (slot, bin, 4-cell piece)
+    for (int i = tid; i < U.nslots * J.nb * 8; i += blockDim.x) {
+      const int k = (int)__umulhi((unsigned)i, mnb);
+      const int rem = i - k * J.nb * 8, b = rem >> 3, p = rem & 7;
+      const int sd = U.slot_side[k];
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int e = J.s_off[sd]; e < J.s_off[sd + 1]; ++e) {
+        const float4 f = *reinterpret_cast<const float4*>(rs + J.s_ent[e][0] * 4096 + swz(b, p));
+        const float4 h = *reinterpret_cast<const float4*>(Hs + J.s_ent[e][1] * UM_CH + 4 * p);
+        v.x = fmaf(f.x, h.x, v.x);
+        v.y = fmaf(f.y, h.y, v.y);
+        v.z = fmaf(f.z, h.z, v.z);
+        v.w = fmaf(f.w, h.w, v.w);
+      }
+      const float4 hi = split_hi4(v);
+      const unsigned o = (unsigned)k * 4096u + swz(b, p);
+      *reinterpret_cast<float4*>(og + L.b_hi + o) = hi;
+      *reinterpret_cast<float4*>(og + L.b_lo + o) = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+    }
+    // bare sides
+    for (int i = tid; i < U.nbare * J.nb * 8; i += blockDim.x) {
+      const int u = (int)__umulhi((unsigned)i, mnb);
+      const int rem = i - u * J.nb * 8, b = rem >> 3, p = rem & 7;
+      const float4 v = *reinterpret_cast<const float4*>(rs + U.bare_comp[u] * 4096 + swz(b, p));
+      const float4 hi = split_hi4(v);
+      const unsigned o = (unsigned)u * 4096u + swz(b, p);
+      *reinterpret_cast<float4*>(og + L.a_hi + o) = hi;
+      *reinterpret_cast<float4*>(og + L.a_lo + o) = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_before();
+    __syncthreads();
+    tc_after();
+    if (s_abort) break;
+    // (3) this chunk's MMAs, then the TMA of chunk it+2 into the stage the build has consumed
+    if (tid == 0) {
+      const unsigned dc = tmem + (unsigned)st * L.dcols;
+      const unsigned ah = obase + L.a_hi, al = obase + L.a_lo, bh = obase + L.b_hi, bl = obase + L.b_lo;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        umma_tf32(dc, umma_sdesc(al + 32 * kk), umma_sdesc(bh + 32 * kk), L.idesc, kk > 0);
+        umma_tf32(dc, umma_sdesc(ah + 32 * kk), umma_sdesc(bl + 32 * kk), L.idesc, 1u);
+        umma_tf32(dc, umma_sdesc(ah + 32 * kk), umma_sdesc(bh + 32 * kk), L.idesc, 1u);
+      }
+      umma_commit(barM + 8u * st);
+      if (ch + 2 * (int64_t)gridDim.x < nchunk) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(ch + 2 * (int64_t)gridDim.x, st);
+        ++tma_issued;
+      }
+    }
+    // (4) read back the previous chunk while the tensor cores work on this one
+    if (it > 0 && reader) {
+      if (__all_sync(0xffffffffu, mbar_wait_bounded(barM + 8u * ((it - 1) & 1), (unsigned)((it - 1) >> 1) & 1u))) {
+        tc_after();
+        readout(it - 1);
+      } else {
+        s_abort = 1;
+        atomicExch(err, 3);
+      }
+    }
+    // round-robin compensated flush of one running sum
+    if (reader) {
+      float x = 0.f;
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (q == fq) {
+          x = run[q];
+          run[q] = 0.f;
+        }
+      kahan_add(pre, x);
+      slot[fq] = pre;
+    }
+    tc_before();
+  }
+  // last chunk's read-back and the remaining running sums
+  if (!s_abort && it > 0 && reader) {
+    if (__all_sync(0xffffffffu, mbar_wait_bounded(barM + 8u * ((it - 1) & 1), (unsigned)((it - 1) >> 1) & 1u))) {
+      tc_after();
+      readout(it - 1);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) kahan_add(slot[q], run[q]);
+    } else {
+      atomicExch(err, 4);
+    }
+  }
+  // after an abort: let in-flight TMA copies and MMAs finish (bounded) before freeing TMEM
+  if (tid == 0 && s_abort) {
+    // the loop leaves before issuing chunk it's MMAs: chunk it-1's are the last ones
+    if (it > 0) mbar_wait_bounded(barM + 8u * ((it - 1) & 1), (unsigned)((it - 1) >> 1) & 1u);
+    for (int k = it; k < tma_issued; ++k) mbar_wait_bounded(barF + 8u * (k & 1), (unsigned)(k >> 1) & 1u);
+  }
+  tc_before();
+  __syncthreads();
+  tc_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L.tcols));
+}
+
+// out[o][b1][b2] from the compensated slots of k_pair_umma: term t lives in warp
+// 4 grp + quad, lane = bin of its bare side, slot = bin of its built side (T.tr says which of
+// the output's two bins is the lane); fixed-order sums over CTAs.
+__global__ void k_pair_umma_final(const float2* slots, int nblk, int nb, int nout, double* out) {
+  const PairJob& J = c_pj;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= nout * nb * nb) return;
+  const int o = gw / (nb * nb), c1 = (gw / nb) % nb, c2 = gw % nb;
+  double tot = 0.0;
+  for (int e = J.out_ent_off[o]; e < J.out_ent_off[o + 1]; ++e) {
+    const PairTermDesc& T = J.term[J.out_ent_term[e]];
+    const int b1 = T.tr ? c2 : c1, b2 = T.tr ? c1 : c2;
+    const int w = 4 * T.grp + T.quad;
+    double s = 0.0;
+    for (int c = lane; c < nblk; c += 32) {
+      const float2 v = slots[(((size_t)c * UM_WARPS + w) * 32 + b1) * 32 + b2];
+      s += (double)v.x - (double)v.y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    tot += J.out_ent_mult[e] * s;
+  }
+  if (lane == 0) out[gw] = tot;
+}
+
 static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) {
   if (j.nb > 32 || 2 * j.nterm > TMA_MAXWARP || j.ng < 1 || j.ng > 256 || j.ncomp < 1) return false;
   auto r1024 = [](size_t b) { return (b + 1023) / 1024 * 1024; };
@@ -719,6 +1024,116 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   *ksplit = 4 * j.nterm <= TMA_MAXWARP ? 2 : 1;
   *warps = 2 * j.nterm * *ksplit;
   return true;
+}
+
+// Layout of k_pair_umma for a job whose built sides are all X: the bare Y components become
+// the 32-row blocks of A, the built sides the 32-row blocks of B; a term whose X is bare gets
+// a built side with the single entry (component, H row of ones).  Fills T.grp / T.quad (the
+// reading warp is 4 grp + quad, quad = the term's bare block) and flips T.tr (the lane holds
+// the bin of the bare side).
+static bool umma_plan(PairJob& j, UmmaPlan* U, UmmaLayout* L) {
+  if (j.nb > 32 || j.ng < 1 || j.ng > 256 || j.ncomp < 1 || j.nterm > UM_MAXS) return false;
+  std::memset(U, 0, sizeof(*U));
+  int hone = -1;
+  for (int t = 0; t < j.nterm; ++t) {
+    PairTermDesc& T = j.term[t];
+    if (T.ydir < 0 || (T.xdir < 0 && T.xslot < 0)) return false;
+    if (T.xslot < 0) {  // bare X: built side c * 1
+      if (hone < 0) {
+        if (j.nh >= 128 || j.h_off[j.nh] >= 512) return false;
+        hone = j.nh;
+        j.h_ent[j.h_off[j.nh]] = {0, -1, 1.0f};
+        j.h_off[j.nh + 1] = j.h_off[j.nh] + 1;
+        ++j.nh;
+      }
+      if (j.nslot >= 64 || j.s_off[j.nslot] >= 512) return false;
+      j.s_ent[j.s_off[j.nslot]][0] = T.xdir;
+      j.s_ent[j.s_off[j.nslot]][1] = hone;
+      j.s_off[j.nslot + 1] = j.s_off[j.nslot] + 1;
+      T.xslot = j.nslot++;
+      T.xdir = -1;
+    }
+  }
+  int per_bare[UM_MAXB] = {0, 0, 0, 0};
+  for (int w = 0; w < UM_WARPS; ++w) U->warp_slot[w] = -1;
+  for (int t = 0; t < j.nterm; ++t) {
+    PairTermDesc& T = j.term[t];
+    int u = -1;
+    for (int v = 0; v < U->nbare; ++v)
+      if (U->bare_comp[v] == T.ydir) u = v;
+    if (u < 0) {
+      if (U->nbare == UM_MAXB) return false;
+      u = U->nbare++;
+      U->bare_comp[u] = T.ydir;
+    }
+    if (per_bare[u] == UM_WARPS / 4) return false;
+    U->slot_side[t] = T.xslot;
+    T.grp = per_bare[u]++;
+    T.quad = u;
+    T.tr = !T.tr;
+    U->warp_slot[4 * T.grp + u] = t;
+  }
+  U->nslots = j.nterm;
+  auto r1024 = [](size_t b) { return (b + 1023) / 1024 * 1024; };
+  const size_t fsz = (size_t)j.ncomp * 4096, gsz = r1024((size_t)j.ng * 128), stage = fsz + gsz;
+  // A: always 128 rows (blocks beyond nbare are never written: they only feed unread lanes)
+  const size_t a_lo = 4 * 4096, b_hi = 2 * a_lo, b_lo = b_hi + (size_t)U->nslots * 4096;
+  const size_t obsz = b_lo + (size_t)U->nslots * 4096;
+  for (int nob = 2; nob >= 1; --nob) {
+    const size_t ob = 2 * stage, hs = ob + nob * obsz;
+    const size_t bar = (hs + (size_t)j.nh * UM_CH * 4 + 15) / 16 * 16;
+    const size_t tptr = bar + 32, bytes = tptr + 16 + 1024;
+    if (bytes > 227 * 1024 - 256) continue;
+    L->fsz = (unsigned)fsz;
+    L->stage = (unsigned)stage;
+    L->ob = (unsigned)ob;
+    L->obsz = (unsigned)obsz;
+    L->a_hi = 0;
+    L->a_lo = (unsigned)a_lo;
+    L->b_hi = (unsigned)b_hi;
+    L->b_lo = (unsigned)b_lo;
+    L->hs = (unsigned)hs;
+    L->bar = (unsigned)bar;
+    L->tptr = (unsigned)tptr;
+    L->bytes = (unsigned)bytes;
+    L->tx = (unsigned)(fsz + (size_t)j.ng * 128);
+    L->dcols = 32u * (unsigned)U->nslots;
+    L->idesc = umma_idesc(32 * U->nslots);
+    unsigned tc = 32;
+    while (tc < 2 * L->dcols) tc *= 2;
+    L->tcols = tc;
+    L->ncomp = j.ncomp;
+    L->nob = nob;
+    return true;
+  }
+  return false;
+}
+
+// the tensor-core path runs k_pair_tma (mma.sync) unless BISP_PAIR_KERNEL=tcgen05 selects
+// k_pair_umma, which is correct but slower on these jobs (see its header comment)
+static bool pair_use_umma() {
+  const char* e = getenv("BISP_PAIR_KERNEL");
+  return e && std::string(e) == "tcgen05";
+}
+
+bool pair_split_gsets() { return pair_use_umma(); }
+
+// a job with its terms normalised for the tensor-core kernels: the built side is X (a term
+// with a built Y is computed as Y X^T and read back transposed)
+static PairJob normalised(const PairJob& j) {
+  PairJob jt = j;
+  for (int t = 0; t < jt.nterm; ++t) {
+    PairTermDesc& T = jt.term[t];
+    T.tr = 0;
+    if (T.yslot >= 0) {
+      std::swap(T.xoff, T.yoff);
+      std::swap(T.xcnt, T.ycnt);
+      std::swap(T.xdir, T.ydir);
+      std::swap(T.xslot, T.yslot);
+      T.tr = 1;
+    }
+  }
+  return jt;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -777,6 +1192,12 @@ static int pair_blocks() {
 
 size_t pair_scratch_bytes(const PairJob& job) {
   const PairJob j = classify(job);
+  if (pair_use_tc(j) && pair_use_umma()) {
+    PairJob jt = normalised(j);
+    UmmaPlan U;
+    UmmaLayout UL;
+    if (umma_plan(jt, &U, &UL)) return (size_t)pair_blocks() * UM_WARPS * 32 * 32 * sizeof(float2) + 256;
+  }
   TmaLayout L;
   int ksplit = 1, warps = 1;
   if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps))
@@ -841,29 +1262,46 @@ __global__ void k_pair_final(const double* partials, int nblk, int warps, int ks
 }
 
 void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scratch_bytes, cudaStream_t s,
-                 int* launches) {
+                 int* launches, int* kernel) {
   const PairJob j = classify(job);
   if (scratch_bytes < pair_scratch_bytes(job)) throw Error{2, "pair reduction scratch too small"};
   if (j.Ng % PR_CH) throw Error{6, "mesh size not a multiple of the chunk"};
   BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &j, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
   double* partials = reinterpret_cast<double*>(scratch);
+  if (pair_use_tc(j) && pair_use_umma()) {
+    PairJob jt = normalised(j);
+    UmmaPlan U;
+    UmmaLayout UL;
+    if (umma_plan(jt, &U, &UL)) {
+      BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &jt, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
+      BISP_CUDA(cudaMemcpyToSymbolAsync(c_um, &U, sizeof(UmmaPlan), 0, cudaMemcpyHostToDevice, s));
+      const int nblk = pair_blocks();
+      float2* slots = reinterpret_cast<float2*>(scratch);
+      int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) +
+                                        (size_t)nblk * UM_WARPS * 32 * 32 * sizeof(float2));
+      BISP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+      const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb);
+      const CUtensorMap mg = g_map(j.gfields, j.Ng, j.ng);
+      BISP_CUDA(cudaFuncSetAttribute(k_pair_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UL.bytes));
+      k_pair_umma<<<nblk, UM_WARPS * 32, UL.bytes, s>>>(mf, mg, UL, slots, err);
+      BISP_CHECK_LAUNCH();
+      const int nout = j.nout * j.nb * j.nb;
+      k_pair_umma_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(slots, nblk, j.nb, j.nout, out_dev);
+      BISP_CHECK_LAUNCH();
+      int herr = 0;
+      BISP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      BISP_CUDA(cudaStreamSynchronize(s));
+      if (herr) throw Error{5, "pair reduction: a TMA stage or an MMA batch did not complete within 2 s"};
+      if (launches) *launches += 2;
+      if (kernel) *kernel = 2;
+      return;
+    }
+  }
   TmaLayout L;
   int ksplit = 1, warps = 1;
   if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) {
-    // the tensor-core kernel builds only A operands: a term with a built Y side is computed
-    // transposed (Y X^T) and read back transposed by the final reduction
-    PairJob jt = j;
-    for (int t = 0; t < jt.nterm; ++t) {
-      PairTermDesc& T = jt.term[t];
-      T.tr = 0;
-      if (T.yslot >= 0) {
-        std::swap(T.xoff, T.yoff);
-        std::swap(T.xcnt, T.ycnt);
-        std::swap(T.xdir, T.ydir);
-        std::swap(T.xslot, T.yslot);
-        T.tr = 1;
-      }
-    }
+    // the mma.sync kernel builds only A operands (see normalised)
+    PairJob jt = normalised(j);
     BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &jt, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
     const int nblk = pair_blocks();
     const size_t need = (size_t)nblk * warps * 32 * 16 * sizeof(float2);
@@ -883,6 +1321,7 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
     BISP_CUDA(cudaStreamSynchronize(s));
     if (herr) throw Error{5, "pair reduction: a TMA stage did not arrive within 2 s"};
     if (launches) *launches += 2;
+    if (kernel) *kernel = 1;
     return;
   }
   const PairLaunch c = pair_launch_cfg(j);
@@ -910,6 +1349,7 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
                                                        j.nout, out_dev);
   BISP_CHECK_LAUNCH();
   if (launches) *launches += 2;
+  if (kernel) *kernel = 0;
 }
 
 }  // namespace bisp

@@ -211,7 +211,7 @@ struct bisp_plan {
   size_t bytes = 0;
   // bookkeeping
   double alpha = 0.0, normI = 0.0;
-  int launches_measure = 0, pair_launches = 0;
+  int launches_measure = 0, pair_launches = 0, pair_kernel = -1;
   double ms_measure = 0.0, ms_pair = 0.0, pair_bytes = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
@@ -780,7 +780,7 @@ void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstrid
   BISP_CUDA(cudaEventCreate(&e0));
   BISP_CUDA(cudaEventCreate(&e1));
   BISP_CUDA(cudaEventRecord(e0, P->stream));
-  pair_reduce(J, P->pairout.as<double>(), P->pairscr.p, P->pairscr.n, P->stream, launches);
+  pair_reduce(J, P->pairout.as<double>(), P->pairscr.p, P->pairscr.n, P->stream, launches, &P->pair_kernel);
   BISP_CUDA(cudaEventRecord(e1, P->stream));
   out.resize((size_t)J.nout * P->nb * P->nb);
   BISP_CUDA(cudaMemcpyAsync(out.data(), P->pairout.p, ob, cudaMemcpyDeviceToHost, P->stream));
@@ -1019,7 +1019,16 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
   std::vector<double> cU, cD, cW;
   // i = j != k shot term: unit shells, q fields of every pass
   shell_fields(P, nullptr, true, &launches);
-  run_pair(P, all, npass, nD, P->qf.as<float>(), cU, &launches);
+  if (npass > 1 && pair_split_gsets()) {
+    // one launch per G set: outputs [gset][mult][b1][b2] as with a single launch
+    for (int gs = 0; gs < npass; ++gs) {
+      std::vector<double> part;
+      run_pair(P, all, 1, nD, P->qf.as<float>() + (size_t)gs * nD * Ng, part, &launches);
+      cU.insert(cU.end(), part.begin(), part.end());
+    }
+  } else {
+    run_pair(P, all, npass, nD, P->qf.as<float>(), cU, &launches);
+  }
   // data
   shell_fields(P, P->pass_spec[0].as<float2>() + (size_t)P->d00 * Nk, false, &launches);
   run_pair(P, all, 1, nD, P->gf[0].as<float>(), cD, &launches);
@@ -1231,6 +1240,7 @@ bisp_status bisp_plan_query(const bisp_plan* P, bisp_plan_info* info) {
   info->ms_pair = P->ms_pair;
   info->pair_bytes = P->pair_bytes;
   info->pair_launches = P->pair_launches;
+  info->pair_kernel = P->pair_kernel;
   return BISP_OK;
 }
 

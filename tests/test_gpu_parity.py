@@ -145,6 +145,55 @@ def test_estimator_parity_small(case):
         assert_close(out["window_shot"], ref["window_shot"], what="window shot")
 
 
+@pytest.mark.parametrize("case,ells", [("survey_local", None),
+                                       ("box_cic", [(0, 0, 0), (2, 0, 2), (1, 1, 0)])])
+def test_estimator_parity_tcgen05(case, ells, monkeypatch):
+    """The opt-in tcgen05 contraction kernel against the oracle (jobs of at most 8 terms on
+    at most 4 bare components: the survey set B000, B202, B112 and a box set)."""
+    monkeypatch.setenv("BISP_PAIR_KERNEL", "tcgen05")
+    c = CASES[case]
+    N, L = c["N"], c["L"]
+    ells = ells or c["ells"]
+    kf = 2 * np.pi / L
+    edges = kf * np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5, 11.0, 15.5])
+    if c["los"] == "global":
+        gal = {"xyz": synthcat.periodic_catalog(N, L, c["np_"], seed=100 + N)}
+        ran = None
+        p = E.Params(N=N, L=L, edges=edges, ells=ells, los="global", mas=c["mas"], interlace=c["interlace"])
+    else:
+        gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+        p = E.Params(N=N, L=L, edges=edges, ells=ells, los="local", observer=obs, mas=c["mas"],
+                     interlace=c["interlace"], P0=1e4, window=True)
+    ref = E.measure(p, gal, ran)
+    with _plan(p) as plan:
+        _assign(plan, 0, gal)
+        if ran is not None:
+            _assign(plan, 1, ran)
+        out = plan.measure()
+        out2 = plan.measure()
+        info = plan.info()
+    assert info["pair_kernel"] == 2
+    assert_close(out["B"], ref["B"], what="B")
+    assert_close(out["shot"], ref["shot"], what="shot")
+    assert np.array_equal(out["B"], out2["B"])
+    if ran is not None:
+        assert_close(out["window"], ref["window"], what="window")
+        assert_close(out["window_shot"], ref["window_shot"], what="window shot")
+
+
+def test_default_pair_kernel_is_mma_sync(monkeypatch):
+    monkeypatch.delenv("BISP_PAIR_KERNEL", raising=False)
+    c = CASES["box_cic"]
+    N, L = c["N"], c["L"]
+    gal = {"xyz": synthcat.periodic_catalog(N, L, c["np_"], seed=100 + N)}
+    edges = 2 * np.pi / L * np.array([1.0, 2.5, 4.0, 5.5])
+    p = E.Params(N=N, L=L, edges=edges, ells=[(0, 0, 0)], los="global", mas=2, interlace=False)
+    with _plan(p) as plan:
+        _assign(plan, 0, gal)
+        plan.measure()
+        assert plan.info()["pair_kernel"] == 1
+
+
 def test_cfg1_box_64_cic_fp():
     # 1000 Mpc/h box, 64^3, 2e5 particles, CIC, no interlacing, global LOS, B000 and B202 on
     # 10 bins with edges 0.01..0.21 h/Mpc
