@@ -389,33 +389,83 @@ struct RegZ {
   static constexpr int A = regz_a(NH);  // threads per row
   static constexpr int B = NH / A;      // values per thread (a multiple of A)
   static constexpr int ROWS = 256 / A;  // rows per group (256 threads)
+  // input tiles of the row groups, double-buffered (bulk copies), at most NH complex per row
+  static constexpr size_t IN_BYTES = (size_t)2 * ROWS * NH * sizeof(float2);
   // row groups per CTA (the twiddle tables are built once per CTA); N^2 / ROWS is a power of two
   static constexpr int GROUPS = (N * N / ROWS) >= 8 ? 8 : (N * N / ROWS);
-  // transpose buffer, then e^{2 pi i j / NH} (NH entries) and e^{2 pi i j / N} (NH entries)
-  static constexpr size_t SMEM = ((size_t)ROWS * B * (A + 1) + 2 * NH) * sizeof(float2);
+  // transpose buffer, e^{2 pi i j / NH} (NH entries), e^{2 pi i j / N} (NH entries), the two
+  // input tiles and two mbarriers
+  static constexpr size_t SMEM = ((size_t)ROWS * B * (A + 1) + 2 * NH) * sizeof(float2) + IN_BYTES + 16;
 };
 
+__device__ __forceinline__ unsigned fft_su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ bool fft_wait(unsigned bar, unsigned parity) {
+  unsigned ok = 0;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  do {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  } while (t - t0 < 2000000000ull);
+  return false;
+}
+// one contiguous global range into shared memory (16-byte aligned, multiple of 16 bytes)
+__device__ __forceinline__ void fft_bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 template <int N>
-__global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const float2* __restrict__ tw,
+                                                   int* err) {
   constexpr int NH = N / 2, A = RegZ<N>::A, B = RegZ<N>::B, ROWS = RegZ<N>::ROWS;
   constexpr int LDT = A + 1;  // padded transpose row
   static_assert(B % A == 0, "B must be a multiple of A");
   extern __shared__ float2 sbuf[];
   float2* wNH = sbuf + ROWS * B * LDT;  // e^{+2 pi i j / NH}
   float2* wN = wNH + NH;                // e^{+2 pi i j / N}, j < NH
+  float2* tin = wN + NH;                // two input tiles [ROWS][Pz]
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(tin + 2 * ROWS * NH);
+  const InvBatch& Bt = c_inv;
+  const InvGeo g = inv_geo(N, Bt.P, Geo<N>::LB);
+  const int f = blockIdx.y;
+  constexpr int GROUPS = RegZ<N>::GROUPS;
+  const unsigned tile_bytes = (unsigned)(ROWS * g.Pz * sizeof(float2));
+  const float2* src0 = t2all + (size_t)f * g.t2 + (size_t)blockIdx.x * GROUPS * ROWS * g.Pz;
+  const unsigned bar0 = fft_su32(bars);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the first group's rows (contiguous: ROWS consecutive T2 rows)
+    fft_bulk_load(fft_su32(tin), src0, tile_bytes, bar0);
+  }
   for (int j = threadIdx.x; j < NH; j += blockDim.x) {
     wNH[j] = cconj(tw[(j * (BISP_TWN / NH)) & (BISP_TWN - 1)]);
     wN[j] = cconj(tw[(j * (BISP_TWN / N)) & (BISP_TWN - 1)]);
   }
   __syncthreads();
-  const InvBatch& Bt = c_inv;
-  const InvGeo g = inv_geo(N, Bt.P, Geo<N>::LB);
-  const int f = blockIdx.y;
   const int l = threadIdx.x / A, a = threadIdx.x % A;
-  constexpr int GROUPS = RegZ<N>::GROUPS;
+  bool ok = true;
   for (int grp = 0; grp < GROUPS; ++grp) {
+    const int cur = grp & 1;
+    // prefetch the next group's rows into the other tile (its previous reader, group grp-1,
+    // finished before the barrier that ended it)
+    if (threadIdx.x == 0 && grp + 1 < GROUPS) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      fft_bulk_load(fft_su32(tin + (cur ^ 1) * ROWS * NH), src0 + (size_t)(grp + 1) * ROWS * g.Pz, tile_bytes,
+                    bar0 + 8u * (cur ^ 1));
+    }
+    if (!fft_wait(bar0 + 8u * cur, (unsigned)(grp >> 1) & 1u)) {
+      ok = false;
+      atomicExch(err, 1);
+    }
     const size_t row = ((size_t)blockIdx.x * GROUPS + grp) * ROWS + l;
-    const float2* x = t2all + (size_t)f * g.t2 + row * g.Pz;
+    const float2* x = tin + cur * ROWS * NH + l * g.Pz;
     const int P = Bt.P;
     float2 v[B];
 #pragma unroll
@@ -439,7 +489,7 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
     for (int kb = 0; kb < B; ++kb) {
       sbuf[(l * B + kb) * LDT + a] = cmul(v[kb], wNH[(a * kb) & (NH - 1)]);
     }
-    __syncthreads();
+    __syncthreads();  // also: every thread has read input tile cur
     // stage 2: thread a handles kb = a + A r, r < B / A, an A-point DFT over a' each
     float* out = Bt.f[f].out + row * N;
 #pragma unroll
@@ -452,7 +502,7 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
 #pragma unroll
       for (int ka = 0; ka < A; ++ka) {
         const int m = kb + B * ka;
-        reinterpret_cast<float2*>(out)[m] = u[ka];
+        if (ok) reinterpret_cast<float2*>(out)[m] = u[ka];
       }
     }
   }
@@ -554,7 +604,7 @@ static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStr
   BISP_CHECK_LAUNCH();
   using RZ = RegZ<N>;
   smem_attr(k_inv_z_reg<N>, RZ::SMEM);
-  k_inv_z_reg<N><<<dim3(N * N / (RZ::ROWS * RZ::GROUPS), b.nf), 256, RZ::SMEM, s>>>(t2, tw);
+  k_inv_z_reg<N><<<dim3(N * N / (RZ::ROWS * RZ::GROUPS), b.nf), 256, RZ::SMEM, s>>>(t2, tw, b.err);
   BISP_CHECK_LAUNCH();
   if (launches) *launches += 3;
 }

@@ -117,6 +117,7 @@ struct InvBatch {
   const float* ynorm;
   const float* cw2_1d;    // QSHOT: per-axis tables (E, O, W) packed, see fft.cu
   int interlace;
+  int* err;               // set (never cleared) when a bounded wait gives up
 };
 size_t inverse_scratch_bytes(int N, int P, int nf);
 void inverse_fft(const InvBatch& b, const float2* tw, void* scratch, cudaStream_t s, int* launches);

@@ -1,7 +1,7 @@
 // Measurement kernels:
 //  * k_axpby: the spectra of one estimator pass, delta n = D_gal - alpha D_ran (Eq. dn)
 //    and N = N_gal + alpha^2 N_ran (Eq. ShotNoise definitions);
-//  * k_zsum: FP64 shell sums (1/N_mode) sum_shell y_l^{m*}(k) [D(k) N_L^{M*}(k) -
+//  * k_zsum: shell sums (1/N_mode) sum_shell y_l^{m*}(k) [D(k) N_L^{M*}(k) -
 //    Sbar_L^M C(k)/W^2(k)] of the i!=j=k and i=k!=j shot-noise terms (Eq. ShotNoise);
 //  (the mesh sum of Eq. bi_estimator_FFTs is in pair.cu).
 #include <algorithm>
@@ -47,14 +47,25 @@ constexpr int ZS_MAXLM = 9;
 
 __device__ __forceinline__ float2 ystar(int l, int m, float x, float y, float z, const float* ynorm);
 
+// FP32 per-mode arithmetic (FMA-contracted, relative error ~1e-7 of |D N*| per mode) with
+// Kahan-compensated FP32 sums per thread; FP64 above the thread level.  GB300's FP64 rate
+// is a small fraction of its FP32 rate, so FP64 per-mode arithmetic bound this kernel.
+__device__ __forceinline__ void zs_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 __global__ void __launch_bounds__(ZS_THREADS) k_zsum() {
   const ZsumArgs& A = c_zs;
   const int b = blockIdx.y;
   const int N = A.N, NH = N / 2;
   const int64_t m0 = A.mode_off[b], m1 = A.mode_off[b + 1];
-  double acc[ZS_MAXLM][2];
+  float acc[ZS_MAXLM][2], cmp[ZS_MAXLM][2];
 #pragma unroll
-  for (int q = 0; q < ZS_MAXLM; ++q) acc[q][0] = acc[q][1] = 0.0;
+  for (int q = 0; q < ZS_MAXLM; ++q) acc[q][0] = acc[q][1] = cmp[q][0] = cmp[q][1] = 0.f;
+  const float sr = (float)A.sbar_re, si = (float)A.sbar_im;
   for (int64_t i = m0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m1; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t code = A.modes[i];
     const int sx = (int)(code & 1023u) - 512, sy = (int)((code >> 10) & 1023u) - 512, nz = (int)(code >> 20);
@@ -64,31 +75,32 @@ __global__ void __launch_bounds__(ZS_THREADS) k_zsum() {
     const float2 nr = A.NR[gi];
     const float2 ni = A.NI ? A.NI[gi] : make_float2(0.f, 0.f);
     // N(k) = NR + i NI ; N(-k) = conj(NR) + i conj(NI)
-    const double nkr = (double)nr.x - (double)ni.y, nki = (double)nr.y + (double)ni.x;
-    const double nmr = (double)nr.x + (double)ni.y, nmi = -(double)nr.y + (double)ni.x;
-    double cw = (double)A.cw2_1d[jx] * A.cw2_1d[jy] * A.cw2_1d[nz];
-    if (A.interlace) cw = 0.5 * (cw + (double)A.cw2_1d[N + jx] * A.cw2_1d[N + jy] * A.cw2_1d[N + nz]);
+    const float nkr = nr.x - ni.y, nki = nr.y + ni.x;
+    const float nmr = nr.x + ni.y, nmi = ni.x - nr.y;
+    float cw = A.cw2_1d[jx] * A.cw2_1d[jy] * A.cw2_1d[nz];
+    if (A.interlace) cw = 0.5f * (cw + A.cw2_1d[N + jx] * A.cw2_1d[N + jy] * A.cw2_1d[N + nz]);
     // T(k) = D(k) conj(N(k)) - Sbar C/W^2
-    const double dr = d.x, di = d.y;
-    const double tkr = dr * nkr + di * nki - A.sbar_re * cw;
-    const double tki = di * nkr - dr * nki - A.sbar_im * cw;
+    const float dr = d.x, di = d.y;
+    const float tkr = fmaf(dr, nkr, fmaf(di, nki, -sr * cw));
+    const float tki = fmaf(di, nkr, fmaf(-dr, nki, -si * cw));
     // T(-k) = conj(D(k)) conj(N(-k)) - Sbar C/W^2
-    const double tmr = dr * nmr - di * nmi - A.sbar_re * cw;
-    const double tmi = -di * nmr - dr * nmi - A.sbar_im * cw;
+    const float tmr = fmaf(dr, nmr, fmaf(-di, nmi, -sr * cw));
+    const float tmi = fmaf(-di, nmr, fmaf(-dr, nmi, -si * cw));
     const bool pair = nz > 0;
 #pragma unroll
     for (int t = 0; t < ZS_MAXLM; ++t) {
       if (t < A.nlm) {
         const int l = A.lm[t][0], m = A.lm[t][1];
         const float2 ys = ystar(l, m, (float)sx, (float)sy, (float)nz, A.ynorm);
-        double yr = ys.x, yi = ys.y;
-        acc[t][0] += yr * tkr - yi * tki;
-        acc[t][1] += yr * tki + yi * tkr;
+        const float yr = ys.x, yi = ys.y;
+        float cr = fmaf(yr, tkr, -yi * tki), ci = fmaf(yr, tki, yi * tkr);
         if (pair) {  // y*(-k) = (-1)^l y*(k)
-          const double sg = (l & 1) ? -1.0 : 1.0;
-          acc[t][0] += sg * (yr * tmr - yi * tmi);
-          acc[t][1] += sg * (yr * tmi + yi * tmr);
+          const float sg = (l & 1) ? -1.f : 1.f;
+          cr = fmaf(sg, fmaf(yr, tmr, -yi * tmi), cr);
+          ci = fmaf(sg, fmaf(yr, tmi, yi * tmr), ci);
         }
+        zs_add(acc[t][0], cmp[t][0], cr);
+        zs_add(acc[t][1], cmp[t][1], ci);
       }
     }
   }
@@ -98,7 +110,7 @@ __global__ void __launch_bounds__(ZS_THREADS) k_zsum() {
     if (t >= A.nlm) break;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      double v = acc[t][c];
+      double v = (double)acc[t][c] - (double)cmp[t][c];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;

@@ -208,6 +208,7 @@ struct bisp_plan {
   // measurement buffers
   DBuf pass_spec[2], gf[2], qf, pool, invscr, pairscr, pairout, zpart;
   DBuf ws;  // assignment workspace (grow-only)
+  DBuf flags;  // device error flags of the measurement kernels
   size_t bytes = 0;
   // bookkeeping
   double alpha = 0.0, normI = 0.0;
@@ -800,6 +801,7 @@ void run_inverse(bisp_plan* P, InvBatch& b, int* launches) {
   b.ynorm = P->ynorm.as<float>();
   b.cw2_1d = P->cw2.as<float>();
   b.interlace = P->interlace;
+  b.err = P->flags.as<int>();
   const size_t need = inverse_scratch_bytes(P->N, b.P, b.nf);
   if (need > P->invscr.n) {
     admit(P, need - P->invscr.n);
@@ -845,6 +847,8 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
   P->pair_launches = 0;
   P->pair_bytes = 0.0;
   BISP_CUDA(cudaEventRecord(P->ev0, s));
+  P->flags.ensure(256, &P->bytes);
+  BISP_CUDA(cudaMemsetAsync(P->flags.p, 0, 256, s));
   const int nD = (int)P->dch.size(), nN = (int)P->nch.size();
   const int64_t Ng = P->Ng, Nk = P->Nk;
   const bool have_r = R.assigned;
@@ -1037,7 +1041,10 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
     run_pair(P, all, 1, nD, P->gf[1].as<float>(), cW, &launches);
   }
   BISP_CUDA(cudaEventRecord(P->ev1, s));
+  int flag = 0;
+  BISP_CUDA(cudaMemcpyAsync(&flag, P->flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   BISP_CUDA(cudaStreamSynchronize(s));
+  if (flag) fail(BISP_ETIMEOUT, "inverse FFT: a staged row group did not arrive within 2 s");
   float ms = 0.f;
   BISP_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
   P->ms_measure = ms;
@@ -1099,7 +1106,7 @@ void destroy(bisp_plan* P) {
   if (!P) return;
   size_t* t = &P->bytes;
   for (auto* d : {&P->tw, &P->winv, &P->ynorm, &P->cw2, &P->qlo_d, &P->qhi_d, &P->zmodes, &P->zmode_off, &P->pool, &P->invscr, &P->pairscr,
-                  &P->pairout, &P->zpart, &P->ws})
+                  &P->pairout, &P->zpart, &P->ws, &P->flags})
     d->release(t);
   for (int k = 0; k < 2; ++k) {
     P->cat[k].spec.release(t);
