@@ -41,6 +41,11 @@ WORKLOADS = {
     # bins and B000 only, a few GB on the device
     "box512_2bins": dict(kind="box", N=512, L=3000.0, n_gen=256, n_p=1_000_000, edges=[0.24, 0.25, 0.26],
                          ells=[(0, 0, 0)], mas="TSC", interlace=True, P0=0.0, window=False),
+    # profiling case: shell batches of nine components with the 512^3 survey's prune ratio
+    # (shells up to 0.26 h/Mpc at half the mesh and half the box), about 3 GB on the device
+    "box256_l2_2bins": dict(kind="box", N=256, L=1500.0, n_gen=256, n_p=1_000_000, edges=[0.24, 0.25, 0.26],
+                            ells=[(0, 0, 0), (2, 0, 2), (1, 1, 2)], mas="TSC", interlace=True, P0=0.0,
+                            window=False),
     "box256": dict(kind="box", N=256, L=1000.0, n_gen=256, n_p=4_000_000,
                    edges=list(np.round(np.linspace(0.01, 0.21, 21), 6)),
                    ells=[(0, 0, 0), (1, 1, 0), (2, 2, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2)], mas="TSC",

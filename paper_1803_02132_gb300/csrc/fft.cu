@@ -247,48 +247,79 @@ __host__ __device__ __forceinline__ InvGeo inv_geo(int N, int P, int LB) {
 
 template <int N>
 __global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(float2* t1all, const float2* __restrict__ tw) {
-  constexpr int NH = N / 2, LB = Geo<N>::LB;
+  constexpr int NH = N / 2, LB = Geo<N>::LB, TS = Geo<N>::TS;
+  constexpr int EPT = N * LB / TS;  // elements per thread
   extern __shared__ float2 s[];
   const InvBatch& B = c_inv;
   const InvGeo g = inv_geo(N, B.P, LB);
   const int nz0 = blockIdx.x * LB, iy = blockIdx.y;
   const int sy = iy - g.P;
   const int jy = sy & (N - 1);
-  for (int f = 0; f < B.nf; ++f) {
-    const InvField& F = B.f[f];
-    for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+  // shell batches: every field filters the same spectrum over the same shell, so the spectrum
+  // values and the shell mask are loaded once, before the field loop
+  const bool shell = B.f[0].kind == SRC_SHELL;
+  float2 av[EPT];
+  unsigned inmask = 0;
+  if (shell) {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int i = threadIdx.x + k * TS;
       const int l = i % LB, e = i / LB;
       const int nz = nz0 + l;
       const int sx = sgn_idx(e, N);
-      float2 v = make_float2(0.f, 0.f);
+      av[k] = make_float2(0.f, 0.f);
       if (sx <= g.P && sx >= -g.P && nz <= g.P) {
-        const size_t gi = ((size_t)e * N + jy) * NH + nz;
-        if (F.kind == SRC_PLAIN) {
-          v = cscale(F.A[gi], F.scale);
-        } else if (F.kind == SRC_QSHOT) {
-          const float2 a = F.A[gi], b = F.B[gi];
-          v = cmul(a, cconj(b));
-          const float c = F.sbar * cw2_val(B.cw2_1d, N, e, jy, nz, B.interlace);
-          v = make_float2((v.x - c) * F.scale, v.y * F.scale);
-        } else {
-          const long long q = (long long)sx * sx + (long long)sy * sy + (long long)nz * nz;
-          if (q >= B.qlo && q < B.qhi) {
-            const float2 y = ylm_one(F.l, F.m, (float)sx, (float)sy, (float)nz, B.ynorm);
-            // part of y_l^{m*}: Re y or -Im y
-            float c = (F.part ? -y.y : y.x) * B.inv_nmodes;
-            float2 a = F.unit ? make_float2(1.f, 0.f) : F.A[gi];
-            // times (-i)^l
-            float2 t = make_float2(a.x * c, a.y * c);
-            switch (F.l & 3) {
-              case 0: v = t; break;
-              case 1: v = make_float2(t.y, -t.x); break;
-              case 2: v = make_float2(-t.x, -t.y); break;
-              default: v = make_float2(-t.y, t.x); break;
-            }
-          }
+        const long long q = (long long)sx * sx + (long long)sy * sy + (long long)nz * nz;
+        if (q >= B.qlo && q < B.qhi) {
+          inmask |= 1u << k;
+          av[k] = B.f[0].unit ? make_float2(1.f, 0.f) : B.f[0].A[((size_t)e * N + jy) * NH + nz];
         }
       }
-      s[i] = v;
+    }
+  }
+  for (int f = 0; f < B.nf; ++f) {
+    const InvField& F = B.f[f];
+    if (shell) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int i = threadIdx.x + k * TS;
+        float2 v = make_float2(0.f, 0.f);
+        if (inmask & (1u << k)) {
+          const int l = i % LB, e = i / LB;
+          const int nz = nz0 + l;
+          const int sx = sgn_idx(e, N);
+          const float2 y = ylm_one(F.l, F.m, (float)sx, (float)sy, (float)nz, B.ynorm);
+          // part of y_l^{m*}: Re y or -Im y, times (-i)^l
+          const float c = (F.part ? -y.y : y.x) * B.inv_nmodes;
+          const float2 t = make_float2(av[k].x * c, av[k].y * c);
+          switch (F.l & 3) {
+            case 0: v = t; break;
+            case 1: v = make_float2(t.y, -t.x); break;
+            case 2: v = make_float2(-t.x, -t.y); break;
+            default: v = make_float2(-t.y, t.x); break;
+          }
+        }
+        s[i] = v;
+      }
+    } else {
+      for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
+        const int l = i % LB, e = i / LB;
+        const int nz = nz0 + l;
+        const int sx = sgn_idx(e, N);
+        float2 v = make_float2(0.f, 0.f);
+        if (sx <= g.P && sx >= -g.P && nz <= g.P) {
+          const size_t gi = ((size_t)e * N + jy) * NH + nz;
+          if (F.kind == SRC_PLAIN) {
+            v = cscale(F.A[gi], F.scale);
+          } else {  // SRC_QSHOT
+            const float2 a = F.A[gi], b = F.B[gi];
+            v = cmul(a, cconj(b));
+            const float c = F.sbar * cw2_val(B.cw2_1d, N, e, jy, nz, B.interlace);
+            v = make_float2((v.x - c) * F.scale, v.y * F.scale);
+          }
+        }
+        s[i] = v;
+      }
     }
     __syncthreads();
     fft_smem<N, LB, +1>(s, tw);
