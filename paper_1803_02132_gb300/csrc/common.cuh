@@ -155,10 +155,24 @@ __device__ __forceinline__ void fft_smem(float2* s, const float2* __restrict__ t
 // unnormalised, sign SIGN: X[k] = sum_n v[n] e^{SIGN 2 pi i n k / R}; tw is the twiddle
 // table e^{-2 pi i j / BISP_TWN}.
 // ---------------------------------------------------------------------------------
-// 32nd roots of unity e^{-2 pi i j / 32} for the in-register DFTs (indices are compile-time
-// constants there, so the values are read as constant-bank operands).  Each translation
-// unit has its own copy; the one that uses DftReg uploads it (upload_root32 in fft.cu).
-static __constant__ float2 c_root32[32];
+
+// o * w^j, w = e^{SIGN 2 pi i / 32}, j < 16 a compile-time constant after unrolling: the
+// trivial twiddles (1 and +-i) cost no multiplies; the others are literal constants,
+// cos(2 pi j / 32) and sin(2 pi j / 32) rounded to FP32.
+__host__ __device__ constexpr float root32_cos(int j) {
+  return j == 0 ? 1.0f : j == 1 ? 0.98078525f : j == 2 ? 0.92387953f : j == 3 ? 0.83146961f :
+         j == 4 ? 0.70710677f : j == 5 ? 0.55557024f : j == 6 ? 0.38268343f : j == 7 ? 0.19509032f :
+         j == 8 ? 0.0f : j == 9 ? -0.19509032f : j == 10 ? -0.38268343f : j == 11 ? -0.55557024f :
+         j == 12 ? -0.70710677f : j == 13 ? -0.83146961f : j == 14 ? -0.92387953f : -0.98078525f;
+}
+__host__ __device__ constexpr float root32_sin(int j) { return j <= 8 ? root32_cos(8 - j) : root32_cos(j - 8); }
+template <int SIGN>
+__device__ __forceinline__ float2 twiddle32(int j, float2 o) {
+  if (j == 0) return o;
+  if (j == 8) return SIGN > 0 ? make_float2(-o.y, o.x) : make_float2(o.y, -o.x);
+  const float c = root32_cos(j), sn = SIGN > 0 ? root32_sin(j) : -root32_sin(j);
+  return make_float2(fmaf(c, o.x, -sn * o.y), fmaf(c, o.y, sn * o.x));
+}
 
 template <int R, int SIGN>
 struct DftReg {
@@ -173,9 +187,7 @@ struct DftReg {
     DftReg<R / 2, SIGN>::run(o, tw);
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) {
-      float2 w = c_root32[k * (32 / R)];
-      if (SIGN > 0) w.y = -w.y;
-      const float2 t = cmul(w, o[k]);
+      const float2 t = twiddle32<SIGN>(k * (32 / R), o[k]);
       v[k] = cadd(e[k], t);
       v[k + R / 2] = csub(e[k], t);
     }

@@ -13,10 +13,6 @@
 
 namespace bisp {
 
-void upload_root32(const float2* host32) {
-  BISP_CUDA(cudaMemcpyToSymbol(c_root32, host32, 32 * sizeof(float2)));
-}
-
 template <int N>
 struct Geo {
   static constexpr int NH = N / 2;

@@ -91,7 +91,6 @@ void forward_fft(float* mesh0, float* mesh1, int count, int N, int mas, const fl
                  const float* winv1d, cudaStream_t s, int* launches);
 
 // 32nd roots of unity for the in-register DFTs (once per process)
-void upload_root32(const float2* host32);
 
 // Inverse transforms from half spectra to real fields, pruned to |n_i| <= P.
 enum SrcKind { SRC_PLAIN = 0, SRC_QSHOT = 1, SRC_SHELL = 2 };

@@ -488,11 +488,6 @@ void upload_tables(bisp_plan* P) {
   std::vector<float> yn((BISP_LMAX + 1) * (BISP_LMAX + 1), 0.f);
   for (int l = 0; l <= BISP_LMAX; ++l)
     for (int m = 0; m <= l; ++m) yn[l * (BISP_LMAX + 1) + m] = (float)std::exp(0.5 * (lfact(l - m) - lfact(l + m)));
-  {
-    std::vector<float2> r32(32);
-    for (int j = 0; j < 32; ++j) r32[j] = tw[j * (BISP_TWN / 32)];
-    upload_root32(r32.data());
-  }
   P->tw.ensure(tw.size() * sizeof(float2), &P->bytes);
   P->winv.ensure(winv.size() * sizeof(float), &P->bytes);
   P->cw2.ensure(cw2.size() * sizeof(float), &P->bytes);
