@@ -416,13 +416,13 @@ struct RegZ {
   static constexpr int A = regz_a(NH);  // threads per row
   static constexpr int B = NH / A;      // values per thread (a multiple of A)
   static constexpr int ROWS = 256 / A;  // rows per group (256 threads)
-  // input tiles of the row groups, double-buffered (bulk copies), at most NH complex per row
-  static constexpr size_t IN_BYTES = (size_t)2 * ROWS * NH * sizeof(float2);
+  // input tiles of the row groups, double-buffered (bulk copies): 2 ROWS rows of Pz complex
   // row groups per CTA (the twiddle tables are built once per CTA); N^2 / ROWS is a power of two
   static constexpr int GROUPS = (N * N / ROWS) >= 8 ? 8 : (N * N / ROWS);
-  // transpose buffer, e^{2 pi i j / NH} (NH entries), e^{2 pi i j / N} (NH entries), the two
-  // input tiles and two mbarriers
-  static constexpr size_t SMEM = ((size_t)ROWS * B * (A + 1) + 2 * NH) * sizeof(float2) + IN_BYTES + 16;
+  // transpose buffer, e^{2 pi i j / NH} (NH entries), e^{2 pi i j / N} (NH entries), then the
+  // two input tiles (sized per launch) and two mbarriers
+  static constexpr size_t SMEM_FIXED = ((size_t)ROWS * B * (A + 1) + 2 * NH) * sizeof(float2);
+  static size_t smem(int Pz) { return SMEM_FIXED + (size_t)2 * ROWS * Pz * sizeof(float2) + 16; }
 };
 
 __device__ __forceinline__ unsigned fft_su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -456,9 +456,9 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
   float2* wNH = sbuf + ROWS * B * LDT;  // e^{+2 pi i j / NH}
   float2* wN = wNH + NH;                // e^{+2 pi i j / N}, j < NH
   float2* tin = wN + NH;                // two input tiles [ROWS][Pz]
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(tin + 2 * ROWS * NH);
   const InvBatch& Bt = c_inv;
   const InvGeo g = inv_geo(N, Bt.P, Geo<N>::LB);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(tin + 2 * ROWS * g.Pz);
   const int f = blockIdx.y;
   constexpr int GROUPS = RegZ<N>::GROUPS;
   const unsigned tile_bytes = (unsigned)(ROWS * g.Pz * sizeof(float2));
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
     // finished before the barrier that ended it)
     if (threadIdx.x == 0 && grp + 1 < GROUPS) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      fft_bulk_load(fft_su32(tin + (cur ^ 1) * ROWS * NH), src0 + (size_t)(grp + 1) * ROWS * g.Pz, tile_bytes,
+      fft_bulk_load(fft_su32(tin + (cur ^ 1) * ROWS * g.Pz), src0 + (size_t)(grp + 1) * ROWS * g.Pz, tile_bytes,
                     bar0 + 8u * (cur ^ 1));
     }
     if (!fft_wait(bar0 + 8u * cur, (unsigned)(grp >> 1) & 1u)) {
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
       atomicExch(err, 1);
     }
     const size_t row = ((size_t)blockIdx.x * GROUPS + grp) * ROWS + l;
-    const float2* x = tin + cur * ROWS * NH + l * g.Pz;
+    const float2* x = tin + cur * ROWS * g.Pz + l * g.Pz;
     const int P = Bt.P;
     float2 v[B];
 #pragma unroll
@@ -630,8 +630,9 @@ static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStr
   k_inv_y_reg<N><<<dim3(g.Pz / G::LB, N, b.nf), RL::THREADS, RL::SMEM, s>>>(t1, t2, tw);
   BISP_CHECK_LAUNCH();
   using RZ = RegZ<N>;
-  smem_attr(k_inv_z_reg<N>, RZ::SMEM);
-  k_inv_z_reg<N><<<dim3(N * N / (RZ::ROWS * RZ::GROUPS), b.nf), 256, RZ::SMEM, s>>>(t2, tw, b.err);
+  const size_t zs = RZ::smem(g.Pz);
+  smem_attr(k_inv_z_reg<N>, RZ::smem(N / 2));
+  k_inv_z_reg<N><<<dim3(N * N / (RZ::ROWS * RZ::GROUPS), b.nf), 256, zs, s>>>(t2, tw, b.err);
   BISP_CHECK_LAUNCH();
   if (launches) *launches += 3;
 }
