@@ -128,6 +128,7 @@ def run_gpu(args, w, rank, world):
     import torch
 
     import paper_1803_02132_gb300 as bisp
+    from paper_1803_02132_gb300 import replicas
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
@@ -192,15 +193,12 @@ def run_gpu(args, w, rank, world):
         step(dev_inputs=False)
     torch.cuda.synchronize()
     ms_e2e = (time.perf_counter() - t0) * 1e3
-    if dist:
-        tt = torch.tensor([ms, ms_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, ms_e2e = tt.tolist()
+    ms, ms_e2e = replicas.max_over_ranks([ms, ms_e2e], dist, device="cuda")
     info = plan.info()
     plan.close()
     nbins = n_bins_output(w)
     ms_step = ms / args.steps
-    value = world * nbins / (ms_step / 1e3)
+    value = replicas.weak_scaling_rate(nbins, ms_step, world)
     h2d = sum(v.numel() * v.element_size() for v in gal.values()) + (
         sum(v.numel() * v.element_size() for v in ran.values()) if ran else 0)
     d2h = (4 if w["window"] else 2) * len(w["ells"]) * (len(w["edges"]) - 1) ** 2 * 8 + (len(w["edges"]) - 1) * 8
@@ -218,7 +216,7 @@ def run_gpu(args, w, rank, world):
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (FP64 accumulation)", "data": "synthetic",
         "config": config_of(args.workload, w, world),
-        "e2e": {"value": world * nbins / (ms_e2e / args.steps / 1e3), "unit": "bins/s",
+        "e2e": {"value": replicas.weak_scaling_rate(nbins, ms_e2e / args.steps, world), "unit": "bins/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": "k_pair_tma (mesh sum of F F G, Eq. bi_estimator_FFTs)",
