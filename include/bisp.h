@@ -109,6 +109,25 @@ bisp_status bisp_assign(bisp_plan* plan, int which, const float* xyz, const floa
 bisp_status bisp_measure(bisp_plan* plan, double* B, double* shot, double* window,
                          double* window_shot, double* nmodes);
 
+/* Output arrays of one plan for bisp_measure_batch: the same arrays, shapes and NULL rules as the
+ * arguments of bisp_measure. */
+typedef struct {
+  double* B;
+  double* shot;
+  double* window;
+  double* window_shot;
+  double* nmodes;
+} bisp_outputs;
+
+/* Measure a batch of plans, e.g. many independent realisations on small meshes, in one call:
+ * the result for plan i is what bisp_measure(plans[i], outs[i].B, ...) returns.  Each plan must
+ * have its catalogues assigned.  The plans are measured one after another on their own streams
+ * (the kernels' job tables live in module-wide constant memory, so plans never run
+ * concurrently); the call returns when all are done.  Errors: BISP_EINVAL for nplans < 0 or NULL
+ * arrays; otherwise the first failing plan's status, with its index in the message (later plans
+ * are not measured).  No counterpart in the paper beyond its use of many mocks (Sec. 5.4). */
+bisp_status bisp_measure_batch(bisp_plan* const* plans, const bisp_outputs* outs, int nplans);
+
 /* Free every resource of the plan (NULL is accepted). */
 bisp_status bisp_plan_destroy(bisp_plan* plan);
 

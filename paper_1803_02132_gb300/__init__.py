@@ -56,13 +56,15 @@ def _load():
     lib.bisp_plan_create.argtypes = [C.POINTER(vp), C.POINTER(_Params), vp]
     lib.bisp_assign.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int64, C.c_int]
     lib.bisp_measure.argtypes = [vp, dp, dp, dp, dp, dp]
+    lib.bisp_measure_batch.argtypes = [vp, vp, C.c_int]
     lib.bisp_plan_destroy.argtypes = [vp]
     lib.bisp_last_error.restype = C.c_char_p
     lib.bisp_plan_query.argtypes = [vp, C.POINTER(_Info)]
     lib.bisp_cell_order.argtypes = [C.c_int, C.c_double, C.c_int, vp, C.c_int64, vp, vp, vp]
     lib.bisp_debug_fetch.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, C.c_size_t]
     lib.bisp_cell_order_noalloc.argtypes = [C.c_int, C.c_double, C.c_int, vp, C.c_int64, vp, vp, vp]
-    for f in ("bisp_plan_create", "bisp_assign", "bisp_measure", "bisp_plan_destroy", "bisp_plan_query",
+    for f in ("bisp_plan_create", "bisp_assign", "bisp_measure", "bisp_measure_batch", "bisp_plan_destroy",
+              "bisp_plan_query",
               "bisp_cell_order", "bisp_debug_fetch", "bisp_cell_order_noalloc"):
         getattr(lib, f).restype = C.c_int
     return lib
@@ -166,6 +168,14 @@ class Plan:
         _check(lib().bisp_measure(self._h, *args))
         return out
 
+    def _out_arrays(self):
+        shape = (self.n_mult, self.nbins, self.nbins)
+        out = {k: np.zeros(shape) for k in ("B", "shot")}
+        if self.info()["n_randoms"] > 0 and self.want_window:
+            out.update(window=np.zeros(shape), window_shot=np.zeros(shape))
+        out["nmodes"] = np.zeros(self.nbins)
+        return out
+
     def info(self):
         i = _Info()
         _check(lib().bisp_plan_query(self._h, C.byref(i)))
@@ -214,3 +224,20 @@ def cell_order(nmesh, box_len, mas, xyz, stream=None):
     _check(lib().bisp_cell_order(int(nmesh), float(box_len), MAS[mas], C.c_void_p(xyz.data_ptr()), n,
                                  C.c_void_p(keys.data_ptr()), C.c_void_p(order.data_ptr()), s))
     return keys, order
+
+
+class _Outputs(C.Structure):
+    _fields_ = [(k, C.POINTER(C.c_double)) for k in ("B", "shot", "window", "window_shot", "nmodes")]
+
+
+def measure_batch(plans):
+    """bisp_measure_batch over a list of Plans: one output dict per plan (as Plan.measure)."""
+    outs = [p._out_arrays() for p in plans]
+    arr = (_Outputs * max(len(plans), 1))()
+    dp = C.POINTER(C.c_double)
+    for i, o in enumerate(outs):
+        for k in ("B", "shot", "window", "window_shot", "nmodes"):
+            setattr(arr[i], k, o[k].ctypes.data_as(dp) if k in o else None)
+    handles = (C.c_void_p * max(len(plans), 1))(*[p._h.value for p in plans])
+    _check(lib().bisp_measure_batch(handles, arr, len(plans)))
+    return outs

@@ -1211,6 +1211,26 @@ bisp_status bisp_measure(bisp_plan* plan, double* B, double* shot, double* windo
   return guarded([&] { do_measure(plan, B, shot, window, window_shot, nmodes); });
 }
 
+bisp_status bisp_measure_batch(bisp_plan* const* plans, const bisp_outputs* outs, int nplans) {
+  if (nplans < 0 || (nplans > 0 && (!plans || !outs))) {
+    g_err = "bisp_measure_batch: nplans < 0 or NULL arrays";
+    return BISP_EINVAL;
+  }
+  for (int i = 0; i < nplans; ++i) {
+    if (!plans[i]) {
+      g_err = "bisp_measure_batch: plan " + std::to_string(i) + " is NULL";
+      return BISP_EINVAL;
+    }
+    const bisp_outputs& o = outs[i];
+    const bisp_status st = guarded([&] { do_measure(plans[i], o.B, o.shot, o.window, o.window_shot, o.nmodes); });
+    if (st != BISP_OK) {
+      g_err = "bisp_measure_batch: plan " + std::to_string(i) + ": " + g_err;
+      return st;
+    }
+  }
+  return BISP_OK;
+}
+
 bisp_status bisp_plan_destroy(bisp_plan* plan) {
   destroy(plan);
   return BISP_OK;
