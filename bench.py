@@ -147,7 +147,8 @@ def run_gpu(args, w, rank, world):
     stream = torch.cuda.Stream()
     plan = bisp.Plan(w["N"], w["L"], w["edges"], w["ells"], los="local" if w["kind"] == "survey" else "global",
                      observer=w.get("observer", (0, 0, 0)), mas=w["mas"], interlace=w["interlace"],
-                     fkp_P0=w["P0"], want_window=w["window"], stream=stream)
+                     fkp_P0=w["P0"], want_window=w["window"], stream=stream, precision=args.precision)
+    f64 = args.precision == "fp64"
 
     def step(dev_inputs=True):
         if dev_inputs:
@@ -186,13 +187,16 @@ def run_gpu(args, w, rank, world):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    # end to end through the public API with host buffers (H2D and D2H inside)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step(dev_inputs=False)
-    torch.cuda.synchronize()
-    ms_e2e = (time.perf_counter() - t0) * 1e3
+    # end to end through the public API with host buffers (H2D and D2H inside); the plain
+    # FP64 comparison line leaves it out (its device time already runs to tens of seconds)
+    ms_e2e = 0.0
+    if not f64:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(dev_inputs=False)
+        torch.cuda.synchronize()
+        ms_e2e = (time.perf_counter() - t0) * 1e3
     ms, ms_e2e = replicas.max_over_ranks([ms, ms_e2e], dist, device="cuda")
     info = plan.info()
     plan.close()
@@ -214,15 +218,16 @@ def run_gpu(args, w, rank, world):
         "metric": metric_name(w),
         "value": value, "unit": "bins/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (FP64 accumulation)", "data": "synthetic",
+        "dtype": "f64" if f64 else "f32 (FP64 accumulation)", "data": "synthetic",
         "config": config_of(args.workload, w, world),
-        "e2e": {"value": replicas.weak_scaling_rate(nbins, ms_e2e / args.steps, world), "unit": "bins/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": None if f64 else {"value": replicas.weak_scaling_rate(nbins, ms_e2e / args.steps, world),
+                                 "unit": "bins/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": "k_pair_tma (mesh sum of F F G, Eq. bi_estimator_FFTs)",
+        "roofline": {"bound": "hbm", "kernel": "k_f64_dot3 (plain FP64 mesh sum, one per bin pair and 3j term)"
+                     if f64 else "k_pair_tma (mesh sum of F F G, Eq. bi_estimator_FFTs)",
                      "achieved": pair_gbs, "peak": hbm, "unit": "GB/s",
                      "frac": (pair_gbs / hbm) if pair_gbs else None,
-                     "traffic": pair_traffic(pair_bytes / max(pair_launches, 1)),
+                     "traffic": None if f64 else pair_traffic(pair_bytes / max(pair_launches, 1)),
                      "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
                      else "of fallback 6800 GB/s"},
         "stages_ms": {"assign_data": info["ms_assign_data"], "assign_randoms": info["ms_assign_randoms"],
@@ -318,6 +323,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="survey512", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="fp64: the plain FP64 form of the estimator (comparison line)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", 0))

@@ -59,6 +59,15 @@ typedef enum { BISP_NGP = 1, BISP_CIC = 2, BISP_TSC = 3 } bisp_mas;
 
 typedef enum { BISP_DATA = 0, BISP_RANDOMS = 1 } bisp_catalog;
 
+/* Arithmetic of bisp_measure after the forward transform.  BISP_FP32: the fused path
+ * (FP32 filtered fields, pruned FFTs, tensor-core mesh sums with FP64 accumulation).
+ * BISP_FP64: the plain FP64 form of the same estimator (Eq. bi_estimator_FFTs), kept as a
+ * speed and accuracy baseline: every filtered field is a full cuFFT Z2D transform of an
+ * FP64 half spectrum, and every 3j term of every bin pair is its own FP64 mesh sum that
+ * re-reads its three fields.  Both share mass assignment, the forward transform (FP32
+ * spectra, upcast) and the shell averages of the shot-noise terms. */
+typedef enum { BISP_FP32 = 0, BISP_FP64 = 1 } bisp_precision;
+
 typedef struct {
   int nmesh;               /* N, a power of two, 16..1024 */
   double box_len;          /* L [Mpc/h]; the mesh covers [0, L)^3 */
@@ -76,6 +85,7 @@ typedef struct {
   double fkp_P0;           /* > 0: FKP weight w/(1 + nbar P0) when nbar is given (Sec. 5.2) */
   size_t max_device_bytes; /* 0: free device memory minus a reserve; else the admission cap */
   int want_window;         /* 1: also the randoms-only window bispectrum (needs randoms) */
+  int precision;           /* bisp_precision (0: BISP_FP32) */
 } bisp_params;
 
 /* Create a plan.  Validates params (BISP_EINVAL names the offending field), computes the
@@ -148,7 +158,8 @@ typedef struct {
   int pair_launches;
   int pair_kernel;         /* kernel of the last pair reduction: 0 FP32 FMA (more than 32 bins),
                               1 mma.sync TF32 (default), 2 tcgen05 TF32 (BISP_PAIR_KERNEL=tcgen05
-                              in the environment, for jobs it covers) */
+                              in the environment, for jobs it covers), 3 FP64 unfused mesh sums
+                              (BISP_FP64 plans) */
 } bisp_plan_info;
 
 bisp_status bisp_plan_query(const bisp_plan* plan, bisp_plan_info* info);

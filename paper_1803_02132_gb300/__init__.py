@@ -23,6 +23,7 @@ STATUS_NAMES = ["BISP_OK", "BISP_EINVAL", "BISP_ENOMEM", "BISP_ECUDA", "BISP_EST
 LOS = {"global": 0, "local": 1}
 MAS = {"NGP": 1, "CIC": 2, "TSC": 3, 1: 1, 2: 2, 3: 3}
 DATA, RANDOMS = 0, 1
+PRECISION = {"fp32": 0, "fp64": 1, 0: 0, 1: 1}
 
 
 class BispError(RuntimeError):
@@ -35,7 +36,7 @@ class _Params(C.Structure):
     _fields_ = [("nmesh", C.c_int), ("box_len", C.c_double), ("k_edges", C.POINTER(C.c_double)),
                 ("nbins", C.c_int), ("ells", C.POINTER(C.c_int)), ("n_mult", C.c_int), ("los", C.c_int),
                 ("observer", C.c_double * 3), ("mas", C.c_int), ("interlace", C.c_int), ("fkp_P0", C.c_double),
-                ("max_device_bytes", C.c_size_t), ("want_window", C.c_int)]
+                ("max_device_bytes", C.c_size_t), ("want_window", C.c_int), ("precision", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -113,7 +114,8 @@ class Plan:
     """A measurement plan: mesh, bins, multipoles, line of sight, assignment scheme."""
 
     def __init__(self, nmesh, box_len, k_edges, ells, los="global", observer=(0.0, 0.0, 0.0), mas="TSC",
-                 interlace=False, fkp_P0=0.0, want_window=False, max_device_bytes=0, stream=None):
+                 interlace=False, fkp_P0=0.0, want_window=False, max_device_bytes=0, stream=None,
+                 precision="fp32"):
         self._edges = np.ascontiguousarray(k_edges, dtype=np.float64)
         self._ells = np.ascontiguousarray(np.asarray(ells, dtype=np.int32).reshape(-1))
         p = _Params()
@@ -130,6 +132,7 @@ class Plan:
         p.fkp_P0 = float(fkp_P0)
         p.max_device_bytes = int(max_device_bytes)
         p.want_window = 1 if want_window else 0
+        p.precision = PRECISION[precision]
         self.nbins = p.nbins
         self.want_window = bool(want_window)
         self.n_mult = p.n_mult

@@ -6,6 +6,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import shutil
 import subprocess
 import sys
 
@@ -13,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbisp.so")
-SOURCES = ["assign.cu", "fft.cu", "measure.cu", "pair.cu", "plan.cu", "noalloc.cu"]
+SOURCES = ["assign.cu", "fft.cu", "measure.cu", "pair.cu", "plan.cu", "noalloc.cu", "fp64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(os.path.dirname(HERE), "include")]
@@ -54,7 +55,10 @@ def build(force=False, verbose=False):
             sys.stderr.write(log)
     objs = [o for o, _ in res]
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    # cuFFT serves only the plain FP64 comparison form (precision BISP_FP64)
+    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(shutil.which(nvcc()) or nvcc()))),
+                          "lib64")
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft", "-Xlinker", f"-rpath={libdir}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")

@@ -185,4 +185,37 @@ size_t pair_scratch_bytes(const PairJob& job);
 // true when the pair kernel in use prefers one launch per G set (at most 8 terms a launch)
 bool pair_split_gsets();
 
+// ---- plain FP64 form (fp64.cu) -----------------------------------------------------
+// One FP64 half spectrum [N][N][N/2+1] built from the FP32 half spectra [N][N][N/2]:
+//   SRC_PLAIN  scale * A;   SRC_QSHOT  scale * (A conj(B) - sbar C/W^2);
+//   SRC_SHELL  mask_b(k) inv_nmodes (-i)^l part(y_l^{m*}(k)) (A(k), or 1 if unit)
+struct F64Spec {
+  int kind;
+  const float2* A;
+  const float2* B;
+  double scale, sbar;
+  int l, m, part, unit;
+  long long qlo, qhi;
+  double inv_nmodes;
+};
+struct F64Tables {
+  const double* ynorm;    // sqrt((l-m)!/(l+m)!) at [l * (BISP_LMAX + 1) + m]
+  const double* cw2;      // per-axis E/W^2 (N values) then O/W^2 (N values)
+  int interlace;
+};
+void f64_spectrum(const F64Spec& s, const F64Tables& t, int N, double2* out, cudaStream_t st);
+struct F64Fft {
+  long long handle = -1;  // cufftHandle of an N^3 Z2D plan (work area supplied by the caller)
+  size_t work_bytes = 0;
+};
+F64Fft f64_fft_create(int N);
+void f64_fft_c2r(const F64Fft& f, void* work, double2* in, double* out, cudaStream_t s);
+void f64_fft_destroy(F64Fft& f);
+// mesh sum of a b c over n doubles: nblk block partials, then out[d] = sum of row d of
+// partial [nd][nblk] (both in a fixed order)
+int f64_dot_blocks();
+void f64_dot3(const double* a, const double* b, const double* c, int64_t n, double* partial, int nblk,
+              cudaStream_t s);
+void f64_dot_final(const double* partial, int nblk, int nd, double* out, cudaStream_t s);
+
 }  // namespace bisp

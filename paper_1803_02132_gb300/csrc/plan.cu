@@ -175,7 +175,7 @@ void bisp::set_last_error(const std::string& m) { g_err = m; }
 
 struct bisp_plan {
   // parameters
-  int N = 0, NH = 0, nb = 0, nmult = 0, los = 0, mas = 2, interlace = 0, want_window = 0;
+  int N = 0, NH = 0, nb = 0, nmult = 0, los = 0, mas = 2, interlace = 0, want_window = 0, precision = 0;
   double L = 0, H = 0, kF = 0, V = 0, P0 = 0, obs[3] = {0, 0, 0};
   size_t max_bytes = 0;
   int64_t Ng = 0, Nk = 0;
@@ -202,6 +202,12 @@ struct bisp_plan {
     std::vector<PairRecipe> x, y;
   };
   std::vector<std::vector<Term>> terms;
+  // the same expansion as plain FP64 terms per multipole: sum_x coef F_c1(b1) F_c2(b2) G_g
+  struct Tri {
+    int c1, c2, g;
+    double coef;
+  };
+  std::vector<std::vector<Tri>> tri64;
   // device constants
   DBuf tw, winv, ynorm, cw2, qlo_d, qhi_d, zmodes, zmode_off;
   Catalog cat[2];
@@ -209,6 +215,9 @@ struct bisp_plan {
   DBuf pass_spec[2], gf[2], qf, pool, invscr, pairscr, pairout, zpart;
   DBuf ws;  // assignment workspace (grow-only)
   DBuf flags;  // device error flags of the measurement kernels
+  // plain FP64 form (precision BISP_FP64)
+  DBuf ynorm_d, cw2_d, f64work, f64spec, f64g, f64q, f64shell, f64part, f64out;
+  F64Fft fft64;
   size_t bytes = 0;
   // bookkeeping
   double alpha = 0.0, normI = 0.0;
@@ -260,6 +269,7 @@ void validate(const bisp_params* p) {
   }
   if (p->los != BISP_LOS_GLOBAL_Z && p->los != BISP_LOS_LOCAL) fail(BISP_EINVAL, "los");
   if (p->mas < 1 || p->mas > 3) fail(BISP_EINVAL, "mas must be 1 (NGP), 2 (CIC) or 3 (TSC)");
+  if (p->precision != BISP_FP32 && p->precision != BISP_FP64) fail(BISP_EINVAL, "precision must be BISP_FP32 or BISP_FP64");
   if (!std::isfinite(p->fkp_P0) || p->fkp_P0 < 0) fail(BISP_EINVAL, "fkp_P0");
   if (p->los == BISP_LOS_LOCAL)
     for (int k = 0; k < 3; ++k)
@@ -389,6 +399,7 @@ void build_shells(bisp_plan* P) {
 // grouped into pair-kernel terms on the side with fewer components.
 void build_recipes(bisp_plan* P) {
   P->terms.clear();
+  P->tri64.clear();
   const bool glob = P->los == BISP_LOS_GLOBAL_Z;
   for (auto& e : P->ells) {
     const int l1 = e[0], l2 = e[1], L = e[2];
@@ -428,9 +439,11 @@ void build_recipes(bisp_plan* P) {
     double mx = 0.0;
     for (auto& kv : tri) mx = std::max(mx, std::fabs(kv.second));
     std::map<int, std::vector<std::tuple<int, int, double>>> by1, by2;
+    std::vector<bisp_plan::Tri> t64;
     for (auto& kv : tri) {
       if (std::fabs(kv.second) <= 1e-13 * mx) continue;
       const int c1 = std::get<0>(kv.first), c2 = std::get<1>(kv.first), g = std::get<2>(kv.first);
+      t64.push_back({c1, c2, g, kv.second});
       by1[c1].push_back({c2, g, kv.second});
       by2[c2].push_back({c1, g, kv.second});
     }
@@ -451,6 +464,7 @@ void build_recipes(bisp_plan* P) {
       }
     }
     P->terms.push_back(ts);
+    P->tri64.push_back(t64);
   }
 }
 
@@ -463,6 +477,7 @@ void upload_tables(bisp_plan* P) {
   }
   // deconvolution 1/W per axis, alias-sum tables C/W^2 (even and alternating images)
   std::vector<float> winv(N), cw2(2 * N);
+  std::vector<double> cw2d(2 * N);
   const int p = P->mas;
   for (int j = 0; j < N; ++j) {
     const int n = j < N / 2 ? j : j - N;
@@ -482,12 +497,18 @@ void upload_tables(bisp_plan* P) {
       E = 1.0 - s2 + 2.0 / 15.0 * s2 * s2;
       O = c * (61.0 + 58.0 * c2 + c2 * c2) / 120.0;
     }
-    cw2[j] = (float)(E / (w * w));
-    cw2[N + j] = (float)(O / (w * w));
+    cw2d[j] = E / (w * w);
+    cw2d[N + j] = O / (w * w);
+    cw2[j] = (float)cw2d[j];
+    cw2[N + j] = (float)cw2d[N + j];
   }
   std::vector<float> yn((BISP_LMAX + 1) * (BISP_LMAX + 1), 0.f);
+  std::vector<double> ynd(yn.size(), 0.0);
   for (int l = 0; l <= BISP_LMAX; ++l)
-    for (int m = 0; m <= l; ++m) yn[l * (BISP_LMAX + 1) + m] = (float)std::exp(0.5 * (lfact(l - m) - lfact(l + m)));
+    for (int m = 0; m <= l; ++m) {
+      ynd[l * (BISP_LMAX + 1) + m] = std::exp(0.5 * (lfact(l - m) - lfact(l + m)));
+      yn[l * (BISP_LMAX + 1) + m] = (float)ynd[l * (BISP_LMAX + 1) + m];
+    }
   P->tw.ensure(tw.size() * sizeof(float2), &P->bytes);
   P->winv.ensure(winv.size() * sizeof(float), &P->bytes);
   P->cw2.ensure(cw2.size() * sizeof(float), &P->bytes);
@@ -505,6 +526,13 @@ void upload_tables(bisp_plan* P) {
   BISP_CUDA(cudaMemcpy(P->ynorm.p, yn.data(), yn.size() * sizeof(float), cudaMemcpyHostToDevice));
   BISP_CUDA(cudaMemcpy(P->qlo_d.p, P->qlo.data(), P->nb * sizeof(long long), cudaMemcpyHostToDevice));
   BISP_CUDA(cudaMemcpy(P->qhi_d.p, P->qhi.data(), P->nb * sizeof(long long), cudaMemcpyHostToDevice));
+  if (P->precision == BISP_FP64) {
+    P->ynorm_d.ensure(ynd.size() * 8, &P->bytes);
+    P->cw2_d.ensure(cw2d.size() * 8, &P->bytes);
+    BISP_CUDA(cudaMemcpy(P->ynorm_d.p, ynd.data(), ynd.size() * 8, cudaMemcpyHostToDevice));
+    BISP_CUDA(cudaMemcpy(P->cw2_d.p, cw2d.data(), cw2d.size() * 8, cudaMemcpyHostToDevice));
+    P->fft64 = f64_fft_create(N);
+  }
 }
 
 void admit(bisp_plan* P, size_t extra) {
@@ -829,6 +857,140 @@ void shell_fields(bisp_plan* P, const float2* D00, bool unit, int* launches) {
   }
 }
 
+// ---------------------------------------------------------------------------------
+// plain FP64 form (precision BISP_FP64): full cuFFT Z2D transforms of FP64 half
+// spectra, one FP64 mesh sum per (bin pair, 3j term), nothing fused
+// ---------------------------------------------------------------------------------
+constexpr int F64_MAX_PENDING = 4096;  // mesh sums per partials buffer
+
+void f64_field(bisp_plan* P, const F64Spec& sp, double* out, int* launches) {
+  const F64Tables t{P->ynorm_d.as<double>(), P->cw2_d.as<double>(), P->interlace};
+  f64_spectrum(sp, t, P->N, P->f64spec.as<double2>(), P->stream);
+  f64_fft_c2r(P->fft64, P->f64work.p, P->f64spec.as<double2>(), out, P->stream);
+  *launches += 2;
+}
+
+// shell fields of bins [b0, b1), component c of bin b at dst + ((b - b0) * ncomp + c) * Ng
+void f64_shells(bisp_plan* P, const float2* D00, bool unit, int b0, int b1, double* dst, int* launches) {
+  const int nc = (int)P->comps.size();
+  for (int b = b0; b < b1; ++b)
+    for (int c = 0; c < nc; ++c) {
+      F64Spec sp{};
+      sp.kind = SRC_SHELL;
+      sp.A = D00;
+      sp.unit = unit ? 1 : 0;
+      sp.l = P->comps[c].l;
+      sp.m = P->comps[c].m;
+      sp.part = P->comps[c].part;
+      sp.qlo = P->qlo[b];
+      sp.qhi = P->qhi[b];
+      sp.inv_nmodes = P->nmodes[b] > 0 ? 1.0 / P->nmodes[b] : 0.0;
+      sp.scale = 1.0;
+      f64_field(P, sp, dst + ((size_t)(b - b0) * nc + c) * P->Ng, launches);
+    }
+}
+
+// out[((gs * nmult + mu) * nb + b1) * nb + b2] = sum over the terms of multipole mu of
+// coef * sum_x F_c1(x; b1) F_c2(x; b2) G_{gs, g}(x).  Shell fields are held for two blocks
+// of nbk bins at a time (one block when every bin fits) and recomputed per block pair.
+void f64_pairs(bisp_plan* P, const float2* D00, bool unit, const double* gbase, int gsets, int nbk,
+               std::vector<double>& out, int* launches) {
+  const int nb = P->nb, nmult = P->nmult, nc = (int)P->comps.size(), nD = (int)P->dch.size();
+  const int64_t Ng = P->Ng;
+  out.assign((size_t)gsets * nmult * nb * nb, 0.0);
+  const size_t fb = (size_t)nc * Ng;
+  double* slotA = P->f64shell.as<double>();
+  double* slotB = slotA + (size_t)nbk * fb;
+  const int nblk = f64_dot_blocks();
+  struct Pend {
+    size_t o;
+    double coef;
+  };
+  std::vector<Pend> pend;
+  cudaEvent_t e0, e1;
+  BISP_CUDA(cudaEventCreate(&e0));
+  BISP_CUDA(cudaEventCreate(&e1));
+  auto flush = [&]() {
+    if (pend.empty()) return;
+    f64_dot_final(P->f64part.as<double>(), nblk, (int)pend.size(), P->f64out.as<double>(), P->stream);
+    ++*launches;
+    BISP_CUDA(cudaEventRecord(e1, P->stream));
+    std::vector<double> v(pend.size());
+    BISP_CUDA(cudaMemcpyAsync(v.data(), P->f64out.p, v.size() * 8, cudaMemcpyDeviceToHost, P->stream));
+    BISP_CUDA(cudaStreamSynchronize(P->stream));
+    float ms = 0.f;
+    BISP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    P->ms_pair += ms;
+    for (size_t i = 0; i < pend.size(); ++i) out[pend[i].o] += pend[i].coef * v[i];
+    pend.clear();
+  };
+  auto dot = [&](const double* a, const double* b, const double* g, size_t o, double coef) {
+    if (pend.empty()) BISP_CUDA(cudaEventRecord(e0, P->stream));
+    f64_dot3(a, b, g, Ng, P->f64part.as<double>() + pend.size() * nblk, nblk, P->stream);
+    ++*launches;
+    P->pair_launches += 1;
+    P->pair_bytes += 3.0 * 8.0 * (double)Ng;
+    pend.push_back({o, coef});
+    if ((int)pend.size() == F64_MAX_PENDING) flush();
+  };
+  const int nblocks = (nb + nbk - 1) / nbk;
+  for (int I = 0; I < nblocks; ++I) {
+    const int i0 = I * nbk, i1 = std::min(nb, i0 + nbk);
+    f64_shells(P, D00, unit, i0, i1, slotA, launches);
+    for (int J = I; J < nblocks; ++J) {
+      const int j0 = J * nbk, j1 = std::min(nb, j0 + nbk);
+      if (J != I) f64_shells(P, D00, unit, j0, j1, slotB, launches);
+      auto field = [&](int b, int c) -> const double* {
+        if (b >= i0 && b < i1) return slotA + (size_t)(b - i0) * fb + (size_t)c * Ng;
+        return slotB + (size_t)(b - j0) * fb + (size_t)c * Ng;
+      };
+      auto pair = [&](int b1, int b2) {
+        for (int gs = 0; gs < gsets; ++gs)
+          for (int mu = 0; mu < nmult; ++mu)
+            for (const auto& t : P->tri64[mu])
+              dot(field(b1, t.c1), field(b2, t.c2), gbase + ((size_t)gs * nD + t.g) * Ng,
+                  (((size_t)gs * nmult + mu) * nb + b1) * nb + b2, t.coef);
+      };
+      for (int b1 = i0; b1 < i1; ++b1)
+        for (int b2 = j0; b2 < j1; ++b2) {
+          pair(b1, b2);
+          if (J != I) pair(b2, b1);
+        }
+      flush();
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->pair_kernel = 3;
+}
+
+// bins per resident block of FP64 shell fields: every bin if they fit, else what two
+// blocks fit in the device memory left (free memory minus a reserve, or the plan's cap)
+int f64_block_bins(bisp_plan* P) {
+  const size_t per_bin = P->comps.size() * (size_t)P->Ng * 8;
+  size_t fre = 0, tot = 0;
+  BISP_CUDA(cudaMemGetInfo(&fre, &tot));
+  const size_t reserve = (size_t)2 << 30;
+  size_t cap = (fre > reserve ? fre - reserve : 0) + P->f64shell.n;
+  if (P->max_bytes) {
+    const size_t held = P->bytes - P->f64shell.n;
+    cap = std::min(cap, P->max_bytes > held ? P->max_bytes - held : 0);
+  }
+  // BISP_FP64_BLOCK_BINS=n in the environment caps the block at n bins (tests of the blocking)
+  const char* env = std::getenv("BISP_FP64_BLOCK_BINS");
+  const int force = env ? std::atoi(env) : 0;
+  if ((size_t)P->nb * per_bin <= cap && (force <= 0 || force >= P->nb)) return P->nb;
+  int nbk = (int)std::min<size_t>(P->nb, cap / (2 * per_bin));
+  if (force > 0) nbk = std::min(nbk, force);
+  if (nbk < 1) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "admission: FP64 shell fields need %.3f GB, %.3f GB available", 2.0 * per_bin / 1e9,
+             cap / 1e9);
+    fail(BISP_ENOMEM, buf);
+  }
+  return nbk;
+}
+
 void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, double* outWS, double* outNm) {
   Catalog& G = P->cat[BISP_DATA];
   Catalog& R = P->cat[BISP_RANDOMS];
@@ -854,20 +1016,40 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
   else P->normI = G.sumw * G.sumw * G.sumw / (P->V * P->V);
   const int npass = (P->want_window && have_r) ? 2 : 1;
   const int nb = P->nb, nmult = P->nmult;
+  const bool f64 = P->precision == BISP_FP64;
   // memory admission for the measurement buffers
   {
     size_t need = 0;
     auto add = [&](DBuf& d, size_t b) { need += b > d.n ? b - d.n : 0; };
     for (int k = 0; k < npass; ++k) {
       add(P->pass_spec[k], (size_t)(nD + nN) * Nk * 8);
-      add(P->gf[k], (size_t)nD * Ng * 4);
+      if (!f64) add(P->gf[k], (size_t)nD * Ng * 4);
     }
-    add(P->qf, (size_t)npass * nD * Ng * 4);
-    const size_t pool_need = (size_t)nb * P->comps.size() * Ng * 4;
-    // the assignment arena moves into the pool from now on: free it before admission
-    if (pool_need > P->pool.n) P->ws.release(&P->bytes);
-    add(P->pool, pool_need);
+    if (!f64) {
+      add(P->qf, (size_t)npass * nD * Ng * 4);
+      const size_t pool_need = (size_t)nb * P->comps.size() * Ng * 4;
+      // the assignment arena moves into the pool from now on: free it before admission
+      if (pool_need > P->pool.n) P->ws.release(&P->bytes);
+      add(P->pool, pool_need);
+    } else {
+      P->ws.release(&P->bytes);
+      add(P->f64spec, (size_t)P->N * P->N * (P->N / 2 + 1) * 16);
+      add(P->f64work, P->fft64.work_bytes);
+      add(P->f64g, (size_t)npass * nD * Ng * 8);
+      add(P->f64q, (size_t)npass * nD * Ng * 8);
+      add(P->f64part, (size_t)F64_MAX_PENDING * f64_dot_blocks() * 8);
+      add(P->f64out, (size_t)F64_MAX_PENDING * 8);
+      add(P->f64shell, 2 * P->comps.size() * (size_t)Ng * 8);
+    }
     admit(P, need);
+  }
+  if (f64) {
+    P->f64spec.ensure((size_t)P->N * P->N * (P->N / 2 + 1) * 16, &P->bytes);
+    P->f64work.ensure(std::max<size_t>(P->fft64.work_bytes, 256), &P->bytes);
+    P->f64g.ensure((size_t)npass * nD * Ng * 8, &P->bytes);
+    P->f64q.ensure((size_t)npass * nD * Ng * 8, &P->bytes);
+    P->f64part.ensure((size_t)F64_MAX_PENDING * f64_dot_blocks() * 8, &P->bytes);
+    P->f64out.ensure((size_t)F64_MAX_PENDING * 8, &P->bytes);
   }
   PassState ps[2];
   for (int k = 0; k < npass; ++k) {
@@ -926,34 +1108,55 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
         ps[k].sbar[{L, M}] = v;
       }
     // G fields: c2r of each delta n channel
-    P->gf[k].ensure((size_t)nD * Ng * 4, &P->bytes);
-    P->qf.ensure((size_t)npass * nD * Ng * 4, &P->bytes);
-    {
-      InvBatch B{};
-      B.P = P->N / 2 - 1;
-      B.nf = nD;
+    if (f64) {
       for (int c = 0; c < nD; ++c) {
-        B.f[c].kind = SRC_PLAIN;
-        B.f[c].A = Dp + c * Nk;
-        B.f[c].scale = 1.f;
-        B.f[c].out = P->gf[k].as<float>() + (size_t)c * Ng;
+        F64Spec sp{};
+        sp.kind = SRC_PLAIN;
+        sp.A = Dp + c * Nk;
+        sp.scale = 1.0;
+        f64_field(P, sp, P->f64g.as<double>() + ((size_t)k * nD + c) * Ng, &launches);
       }
-      run_inverse(P, B, &launches);
-      // q fields: c2r of D_c conj(N_00) - Sbar_part C/W^2
-      InvBatch Q{};
-      Q.P = P->N / 2 - 1;
-      Q.nf = nD;
       for (int c = 0; c < nD; ++c) {
         const Chan& ch = P->dch[c];
         const cplx sbv = ps[k].sbar.at({local ? ch.L : 0, local ? ch.M : 0});
-        Q.f[c].kind = SRC_QSHOT;
-        Q.f[c].A = Dp + c * Nk;
-        Q.f[c].B = Np + (size_t)P->n00 * Nk;
-        Q.f[c].sbar = (float)(ch.part ? sbv.i : sbv.r);
-        Q.f[c].scale = 1.f;
-        Q.f[c].out = P->qf.as<float>() + ((size_t)k * nD + c) * Ng;
+        F64Spec sp{};
+        sp.kind = SRC_QSHOT;
+        sp.A = Dp + c * Nk;
+        sp.B = Np + (size_t)P->n00 * Nk;
+        sp.sbar = ch.part ? sbv.i : sbv.r;
+        sp.scale = 1.0;
+        f64_field(P, sp, P->f64q.as<double>() + ((size_t)k * nD + c) * Ng, &launches);
       }
-      run_inverse(P, Q, &launches);
+    } else {
+      P->gf[k].ensure((size_t)nD * Ng * 4, &P->bytes);
+      P->qf.ensure((size_t)npass * nD * Ng * 4, &P->bytes);
+      {
+        InvBatch B{};
+        B.P = P->N / 2 - 1;
+        B.nf = nD;
+        for (int c = 0; c < nD; ++c) {
+          B.f[c].kind = SRC_PLAIN;
+          B.f[c].A = Dp + c * Nk;
+          B.f[c].scale = 1.f;
+          B.f[c].out = P->gf[k].as<float>() + (size_t)c * Ng;
+        }
+        run_inverse(P, B, &launches);
+        // q fields: c2r of D_c conj(N_00) - Sbar_part C/W^2
+        InvBatch Q{};
+        Q.P = P->N / 2 - 1;
+        Q.nf = nD;
+        for (int c = 0; c < nD; ++c) {
+          const Chan& ch = P->dch[c];
+          const cplx sbv = ps[k].sbar.at({local ? ch.L : 0, local ? ch.M : 0});
+          Q.f[c].kind = SRC_QSHOT;
+          Q.f[c].A = Dp + c * Nk;
+          Q.f[c].B = Np + (size_t)P->n00 * Nk;
+          Q.f[c].sbar = (float)(ch.part ? sbv.i : sbv.r);
+          Q.f[c].scale = 1.f;
+          Q.f[c].out = P->qf.as<float>() + ((size_t)k * nD + c) * Ng;
+        }
+        run_inverse(P, Q, &launches);
+      }
     }
     // shell sums Z(b; l, m, L, M) for M >= 0 (FP64)
     {
@@ -1011,29 +1214,40 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
         }
     }
   }
-  // pair reductions
-  P->pool.ensure((size_t)nb * P->comps.size() * Ng * 4, &P->bytes);
-  std::vector<int> all(nmult);
-  for (int i = 0; i < nmult; ++i) all[i] = i;
   std::vector<double> cU, cD, cW;
-  // i = j != k shot term: unit shells, q fields of every pass
-  shell_fields(P, nullptr, true, &launches);
-  if (npass > 1 && pair_split_gsets()) {
-    // one launch per G set: outputs [gset][mult][b1][b2] as with a single launch
-    for (int gs = 0; gs < npass; ++gs) {
-      std::vector<double> part;
-      run_pair(P, all, 1, nD, P->qf.as<float>() + (size_t)gs * nD * Ng, part, &launches);
-      cU.insert(cU.end(), part.begin(), part.end());
-    }
+  if (f64) {
+    const int nbk = f64_block_bins(P);
+    P->f64shell.ensure((size_t)(nbk == nb ? nb : 2 * nbk) * P->comps.size() * Ng * 8, &P->bytes);
+    f64_pairs(P, nullptr, true, P->f64q.as<double>(), npass, nbk, cU, &launches);
+    f64_pairs(P, P->pass_spec[0].as<float2>() + (size_t)P->d00 * Nk, false, P->f64g.as<double>(), 1, nbk, cD,
+              &launches);
+    if (npass == 2)
+      f64_pairs(P, P->pass_spec[1].as<float2>() + (size_t)P->d00 * Nk, false, P->f64g.as<double>() + (size_t)nD * Ng,
+                1, nbk, cW, &launches);
   } else {
-    run_pair(P, all, npass, nD, P->qf.as<float>(), cU, &launches);
-  }
-  // data
-  shell_fields(P, P->pass_spec[0].as<float2>() + (size_t)P->d00 * Nk, false, &launches);
-  run_pair(P, all, 1, nD, P->gf[0].as<float>(), cD, &launches);
-  if (npass == 2) {
-    shell_fields(P, P->pass_spec[1].as<float2>() + (size_t)P->d00 * Nk, false, &launches);
-    run_pair(P, all, 1, nD, P->gf[1].as<float>(), cW, &launches);
+    // pair reductions
+    P->pool.ensure((size_t)nb * P->comps.size() * Ng * 4, &P->bytes);
+    std::vector<int> all(nmult);
+    for (int i = 0; i < nmult; ++i) all[i] = i;
+    // i = j != k shot term: unit shells, q fields of every pass
+    shell_fields(P, nullptr, true, &launches);
+    if (npass > 1 && pair_split_gsets()) {
+      // one launch per G set: outputs [gset][mult][b1][b2] as with a single launch
+      for (int gs = 0; gs < npass; ++gs) {
+        std::vector<double> part;
+        run_pair(P, all, 1, nD, P->qf.as<float>() + (size_t)gs * nD * Ng, part, &launches);
+        cU.insert(cU.end(), part.begin(), part.end());
+      }
+    } else {
+      run_pair(P, all, npass, nD, P->qf.as<float>(), cU, &launches);
+    }
+    // data
+    shell_fields(P, P->pass_spec[0].as<float2>() + (size_t)P->d00 * Nk, false, &launches);
+    run_pair(P, all, 1, nD, P->gf[0].as<float>(), cD, &launches);
+    if (npass == 2) {
+      shell_fields(P, P->pass_spec[1].as<float2>() + (size_t)P->d00 * Nk, false, &launches);
+      run_pair(P, all, 1, nD, P->gf[1].as<float>(), cW, &launches);
+    }
   }
   BISP_CUDA(cudaEventRecord(P->ev1, s));
   int flag = 0;
@@ -1101,8 +1315,10 @@ void destroy(bisp_plan* P) {
   if (!P) return;
   size_t* t = &P->bytes;
   for (auto* d : {&P->tw, &P->winv, &P->ynorm, &P->cw2, &P->qlo_d, &P->qhi_d, &P->zmodes, &P->zmode_off, &P->pool, &P->invscr, &P->pairscr,
-                  &P->pairout, &P->zpart, &P->ws, &P->flags})
+                  &P->pairout, &P->zpart, &P->ws, &P->flags, &P->ynorm_d, &P->cw2_d, &P->f64work, &P->f64spec,
+                  &P->f64g, &P->f64q, &P->f64shell, &P->f64part, &P->f64out})
     d->release(t);
+  f64_fft_destroy(P->fft64);
   for (int k = 0; k < 2; ++k) {
     P->cat[k].spec.release(t);
     P->cat[k].dbg_mesh.release(t);
@@ -1168,6 +1384,7 @@ bisp_status bisp_plan_create(bisp_plan** out, const bisp_params* p, void* stream
     P->P0 = p->fkp_P0;
     P->max_bytes = p->max_device_bytes;
     P->want_window = p->want_window ? 1 : 0;
+    P->precision = p->precision;
     const char* dbg = std::getenv("BISP_DEBUG");
     P->debug_mesh = dbg && std::strstr(dbg, "BISP_DEBUG_KEEP_MESH");
     int dev = 0;

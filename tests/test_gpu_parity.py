@@ -181,6 +181,48 @@ def test_estimator_parity_tcgen05(case, ells, monkeypatch):
         assert_close(out["window_shot"], ref["window_shot"], what="window shot")
 
 
+@pytest.mark.parametrize("case,block", [("box_cic", 0), ("box_tsc_ilv", 0), ("survey_local", 0),
+                                        ("survey_local", 3)])
+def test_estimator_parity_fp64(case, block, monkeypatch):
+    """The plain FP64 form (cuFFT Z2D fields, one FP64 mesh sum per bin pair and 3j term)
+    against the oracle and against the fused FP32 path; block > 0 holds shell fields for
+    blocks of that many bins (7 bins: a ragged last block)."""
+    if block:
+        monkeypatch.setenv("BISP_FP64_BLOCK_BINS", str(block))
+    else:
+        monkeypatch.delenv("BISP_FP64_BLOCK_BINS", raising=False)
+    c = CASES[case]
+    N, L = c["N"], c["L"]
+    kf = 2 * np.pi / L
+    edges = kf * np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5, 11.0, 15.5])
+    if c["los"] == "global":
+        gal = {"xyz": synthcat.periodic_catalog(N, L, c["np_"], seed=100 + N)}
+        ran = None
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="global", mas=c["mas"], interlace=c["interlace"])
+    else:
+        gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="local", observer=obs, mas=c["mas"],
+                     interlace=c["interlace"], P0=1e4, window=True)
+    ref = E.measure(p, gal, ran)
+    outs = {}
+    for prec in ("fp64", "fp32"):
+        with _plan(p, precision=prec) as plan:
+            _assign(plan, 0, gal)
+            if ran is not None:
+                _assign(plan, 1, ran)
+            outs[prec] = plan.measure()
+            if prec == "fp64":
+                again = plan.measure()
+                assert plan.info()["pair_kernel"] == 3
+                assert np.array_equal(outs[prec]["B"], again["B"])  # fixed-order sums
+    o64, o32 = outs["fp64"], outs["fp32"]
+    assert np.array_equal(o64["nmodes"], ref["nmodes"])
+    keys = ["B", "shot"] + (["window", "window_shot"] if ran is not None else [])
+    for k in keys:
+        assert_close(o64[k], ref[k], what=f"fp64 {k}")
+        assert_close(o32[k], o64[k], what=f"fp32 vs fp64 {k}")
+
+
 def test_default_pair_kernel_is_mma_sync(monkeypatch):
     monkeypatch.delenv("BISP_PAIR_KERNEL", raising=False)
     c = CASES["box_cic"]
