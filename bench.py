@@ -201,6 +201,10 @@ def run_gpu(args, w, rank, world):
     info = plan.info()
     plan.close()
     nbins = n_bins_output(w)
+    fp64 = None
+    if not f64 and world == 1 and not args.no_fp64_baseline:
+        fp64 = fp64_step(bisp, w, g_dev, r_dev, nbins)
+        fp64["speedup"] = (nbins / (ms / args.steps / 1e3)) / fp64["value"]
     ms_step = ms / args.steps
     value = replicas.weak_scaling_rate(nbins, ms_step, world)
     h2d = sum(v.numel() * v.element_size() for v in gal.values()) + (
@@ -234,7 +238,37 @@ def run_gpu(args, w, rank, world):
                       "measure": info["ms_measure"], "pair": info["ms_pair"]},
         "clocks": clk,
     }
+    if fp64:
+        out["fp64_gpu_baseline"] = fp64
     return out
+
+
+def fp64_step(bisp, w, g, r, nbins):
+    """One step of the plain FP64 form (cuFFT Z2D fields, one FP64 mesh sum per bin pair and
+    3j term) on the same device-resident inputs, timed with CUDA events on its stream."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    plan = bisp.Plan(w["N"], w["L"], w["edges"], w["ells"], los="local" if w["kind"] == "survey" else "global",
+                     observer=w.get("observer", (0, 0, 0)), mas=w["mas"], interlace=w["interlace"],
+                     fkp_P0=w["P0"], want_window=w["window"], stream=stream, precision="fp64")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plan.assign(bisp.DATA, g["xyz"], None, g.get("nbar"))
+    if r is not None:
+        plan.assign(bisp.RANDOMS, r["xyz"], None, r.get("nbar"))
+    plan.measure()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    inf = plan.info()
+    plan.close()
+    gbs = inf["pair_bytes"] / (inf["ms_pair"] / 1e3) / 1e9 if inf["ms_pair"] > 0 else None
+    return {"value": nbins / (ms / 1e3), "unit": "bins/s", "ms_per_step": ms, "steps": 1, "warmup": 0,
+            "dtype": "f64", "form": "plain FP64: cuFFT Z2D fields, one FP64 mesh sum per bin pair and 3j term",
+            "ms_measure": inf["ms_measure"], "mesh_sum_kernel": "k_f64_dot3", "mesh_sum_gbs": gbs}
 
 
 def metric_name(w):
@@ -323,6 +357,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="survey512", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-baseline", action="store_true",
+                    help="skip the one-step timing of the plain FP64 form beside the FP32 line")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="fp64: the plain FP64 form of the estimator (comparison line)")
     args = ap.parse_args()

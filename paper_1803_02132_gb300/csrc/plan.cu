@@ -1224,6 +1224,9 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
     if (npass == 2)
       f64_pairs(P, P->pass_spec[1].as<float2>() + (size_t)P->d00 * Nk, false, P->f64g.as<double>() + (size_t)nD * Ng,
                 1, nbk, cW, &launches);
+    // the shell blocks take what memory was free: give it back for the next assignment
+    BISP_CUDA(cudaStreamSynchronize(s));
+    P->f64shell.release(&P->bytes);
   } else {
     // pair reductions
     P->pool.ensure((size_t)nb * P->comps.size() * Ng * 4, &P->bytes);
