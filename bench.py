@@ -54,6 +54,12 @@ WORKLOADS = {
                    edges=list(np.round(np.linspace(0.01, 0.21, 21), 6)),
                    ells=[(0, 0, 0), (1, 1, 0), (2, 2, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2)], mas="TSC",
                    interlace=True, P0=0.0, window=False),
+    # large periodic box: fields of the 40 bins (1.5 TB) do not fit; the shell fields are held in
+    # blocks of bins sized from the free device memory
+    "box1024": dict(kind="box", N=1024, L=2000.0, n_gen=256, n_p=120_000_000,
+                    edges=list(np.round(np.linspace(0.005, 0.405, 41), 6)),
+                    ells=[(0, 0, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2)], mas="TSC", interlace=True, P0=0.0,
+                    window=False),
     "box64": dict(kind="box", N=64, L=1000.0, n_gen=64, n_p=200_000, edges=list(np.round(np.linspace(0.01, 0.21, 11), 6)),
                   ells=[(0, 0, 0), (2, 0, 2)], mas="CIC", interlace=False, P0=0.0, window=False),
 }
@@ -190,7 +196,7 @@ def run_gpu(args, w, rank, world):
     # end to end through the public API with host buffers (H2D and D2H inside); the plain
     # FP64 comparison line leaves it out (its device time already runs to tens of seconds)
     ms_e2e = 0.0
-    if not f64:
+    if not f64 and not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -224,7 +230,7 @@ def run_gpu(args, w, rank, world):
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if f64 else "f32 (FP64 accumulation)", "data": "synthetic",
         "config": config_of(args.workload, w, world),
-        "e2e": None if f64 else {"value": replicas.weak_scaling_rate(nbins, ms_e2e / args.steps, world),
+        "e2e": None if (f64 or args.no_e2e) else {"value": replicas.weak_scaling_rate(nbins, ms_e2e / args.steps, world),
                                  "unit": "bins/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": "k_f64_dot3 (plain FP64 mesh sum, one per bin pair and 3j term)"
@@ -357,6 +363,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="survey512", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) leg")
     ap.add_argument("--no-fp64-baseline", action="store_true",
                     help="skip the one-step timing of the plain FP64 form beside the FP32 line")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],

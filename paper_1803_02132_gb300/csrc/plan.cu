@@ -759,14 +759,15 @@ struct PassState {
   std::map<std::tuple<int, int, int, int>, std::vector<cplx>> Z;
 };
 
-void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstride, const float* gbase,
+// pair reduction over the first nbu bins held in the field pool
+void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstride, const float* gbase, int nbu,
               std::vector<double>& out, int* launches) {
   // build a pair job with nout = mults.size() * gsets outputs
   PairJob J{};
   J.fields = P->pool.as<float>();
   J.gfields = gbase;
   J.Ng = P->Ng;
-  J.nb = P->nb;
+  J.nb = nbu;
   J.ncomp = (int)P->comps.size();
   J.ng = gsets * gstride;
   J.nout = (int)mults.size() * gsets;
@@ -798,7 +799,7 @@ void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstrid
   const size_t sb = pair_scratch_bytes(J);
   admit(P, sb > P->pairscr.n ? sb - P->pairscr.n : 0);
   P->pairscr.ensure(sb, &P->bytes);
-  const size_t ob = (size_t)J.nout * P->nb * P->nb * 8;
+  const size_t ob = (size_t)J.nout * J.nb * J.nb * 8;
   P->pairout.ensure(ob, &P->bytes);
   cudaEvent_t e0, e1;
   BISP_CUDA(cudaEventCreate(&e0));
@@ -806,7 +807,7 @@ void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstrid
   BISP_CUDA(cudaEventRecord(e0, P->stream));
   pair_reduce(J, P->pairout.as<double>(), P->pairscr.p, P->pairscr.n, P->stream, launches, &P->pair_kernel);
   BISP_CUDA(cudaEventRecord(e1, P->stream));
-  out.resize((size_t)J.nout * P->nb * P->nb);
+  out.resize((size_t)J.nout * J.nb * J.nb);
   BISP_CUDA(cudaMemcpyAsync(out.data(), P->pairout.p, ob, cudaMemcpyDeviceToHost, P->stream));
   BISP_CUDA(cudaStreamSynchronize(P->stream));
   float ms = 0.f;
@@ -833,9 +834,10 @@ void run_inverse(bisp_plan* P, InvBatch& b, int* launches) {
   inverse_fft(b, P->tw.as<float2>(), P->invscr.p, P->stream, launches);
 }
 
-void shell_fields(bisp_plan* P, const float2* D00, bool unit, int* launches) {
+// shell fields of bins [b0, b1) into the pool, bin b at pool bin slot b - b0 + slot
+void shell_fields(bisp_plan* P, const float2* D00, bool unit, int b0, int b1, int slot, int* launches) {
   const int nc = (int)P->comps.size();
-  for (int b = 0; b < P->nb; ++b) {
+  for (int b = b0; b < b1; ++b) {
     InvBatch B{};
     B.P = P->Pb[b];
     B.nf = nc;
@@ -851,10 +853,91 @@ void shell_fields(bisp_plan* P, const float2* D00, bool unit, int* launches) {
       f.part = P->comps[c].part;
       f.unit = unit ? 1 : 0;
       f.scale = 1.f;
-      f.out = P->pool.as<float>() + ((size_t)b * nc + c) * P->Ng;
+      f.out = P->pool.as<float>() + ((size_t)(b - b0 + slot) * nc + c) * P->Ng;
     }
     run_inverse(P, B, launches);
   }
+}
+
+// Shell fields of one set (unit shells, data or window) and their pair reductions, out laid
+// out [gset][mult][b1][b2].  When the pool holds fewer than n_b bins (nbk < n_b), the bins are
+// taken in blocks of nbk: block I sits in the pool's first slots and block J > I after it, and
+// one pair launch covers their union; a pair (b1, b2) is kept from exactly one union (cross
+// pairs from (I, J), a block's own pairs from (I, I + 1), the last block's from the last union).
+void pair_set(bisp_plan* P, const float2* D00, bool unit, int gsets, const float* gbase, int nbk,
+              std::vector<double>& out, int* launches) {
+  const int nb = P->nb, nmult = P->nmult, nD = (int)P->dch.size();
+  std::vector<int> all(nmult);
+  for (int i = 0; i < nmult; ++i) all[i] = i;
+  auto pairs = [&](int nbu, std::vector<double>& res) {
+    if (gsets > 1 && pair_split_gsets()) {
+      // one launch per G set: outputs [gset][mult][b1][b2] as with a single launch
+      res.clear();
+      for (int gs = 0; gs < gsets; ++gs) {
+        std::vector<double> part;
+        run_pair(P, all, 1, nD, gbase + (size_t)gs * nD * P->Ng, nbu, part, launches);
+        res.insert(res.end(), part.begin(), part.end());
+      }
+    } else {
+      run_pair(P, all, gsets, nD, gbase, nbu, res, launches);
+    }
+  };
+  if (nbk >= nb) {
+    shell_fields(P, D00, unit, 0, nb, 0, launches);
+    pairs(nb, out);
+    return;
+  }
+  const int nout = gsets * nmult, nblocks = (nb + nbk - 1) / nbk;
+  out.assign((size_t)nout * nb * nb, 0.0);
+  std::vector<double> res;
+  for (int I = 0; I + 1 < nblocks; ++I) {
+    const int i0 = I * nbk, ni = std::min(nbk, nb - i0);
+    shell_fields(P, D00, unit, i0, i0 + ni, 0, launches);
+    for (int J = I + 1; J < nblocks; ++J) {
+      const int j0 = J * nbk, nj = std::min(nbk, nb - j0), nbu = ni + nj;
+      shell_fields(P, D00, unit, j0, j0 + nj, ni, launches);
+      pairs(nbu, res);
+      const bool own_i = J == I + 1, own_j = J == nblocks - 1 && I == nblocks - 2;
+      for (int o = 0; o < nout; ++o)
+        for (int u1 = 0; u1 < nbu; ++u1)
+          for (int u2 = 0; u2 < nbu; ++u2) {
+            const bool in1 = u1 < ni, in2 = u2 < ni;
+            if (in1 == in2 && !(in1 ? own_i : own_j)) continue;
+            const int b1 = in1 ? i0 + u1 : j0 + u1 - ni, b2 = in2 ? i0 + u2 : j0 + u2 - ni;
+            out[((size_t)o * nb + b1) * nb + b2] = res[((size_t)o * nbu + u1) * nbu + u2];
+          }
+    }
+  }
+}
+
+// Bins per resident block of FP32 shell fields: all n_b when they fit and n_b <= 32 (a pair
+// launch covers at most 32 bins), else blocks of at most 16 with two resident.  other_need is
+// the device memory the measurement still has to allocate besides the pool.
+// BISP_BLOCK_BINS=n in the environment caps the block at n bins (tests of the blocking).
+int fp32_block_bins(bisp_plan* P, size_t other_need) {
+  const size_t per_bin = P->comps.size() * (size_t)P->Ng * 4;
+  size_t fre = 0, tot = 0;
+  BISP_CUDA(cudaMemGetInfo(&fre, &tot));
+  const size_t reserve = (size_t)2 << 30;
+  const size_t movable = P->pool.n + P->ws.n;  // the pool is re-sized, the arena released
+  size_t cap = (fre > reserve ? fre - reserve : 0) + movable;
+  cap = cap > other_need ? cap - other_need : 0;
+  if (P->max_bytes) {
+    const size_t held = P->bytes - movable + other_need;
+    cap = std::min(cap, P->max_bytes > held ? P->max_bytes - held : 0);
+  }
+  const char* env = std::getenv("BISP_BLOCK_BINS");
+  const int force = env ? std::atoi(env) : 0;
+  if (P->nb <= 32 && (size_t)P->nb * per_bin <= cap && (force <= 0 || force >= P->nb)) return P->nb;
+  int nbk = (int)std::min<size_t>(16, cap / (2 * per_bin));
+  if (force > 0) nbk = std::min(nbk, force);
+  if (nbk < 1) {
+    char buf[200];
+    snprintf(buf, sizeof buf, "admission: two bins of shell fields need %.3f GB, %.3f GB available",
+             2.0 * per_bin / 1e9, cap / 1e9);
+    fail(BISP_ENOMEM, buf);
+  }
+  return std::min(nbk, P->nb);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1017,6 +1100,7 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
   const int npass = (P->want_window && have_r) ? 2 : 1;
   const int nb = P->nb, nmult = P->nmult;
   const bool f64 = P->precision == BISP_FP64;
+  int nbk = nb;  // bins per resident block of FP32 shell fields
   // memory admission for the measurement buffers
   {
     size_t need = 0;
@@ -1027,7 +1111,12 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
     }
     if (!f64) {
       add(P->qf, (size_t)npass * nD * Ng * 4);
-      const size_t pool_need = (size_t)nb * P->comps.size() * Ng * 4;
+      // inverse-transform scratch still to grow (G and Q batches, the widest shell batch)
+      const int pmax = *std::max_element(P->Pb.begin(), P->Pb.end());
+      const size_t inv = std::max(inverse_scratch_bytes(P->N, P->N / 2 - 1, nD),
+                                  inverse_scratch_bytes(P->N, pmax, (int)P->comps.size()));
+      nbk = fp32_block_bins(P, need + (inv > P->invscr.n ? inv - P->invscr.n : 0));
+      const size_t pool_need = (size_t)(nbk == nb ? nb : 2 * nbk) * P->comps.size() * Ng * 4;
       // the assignment arena moves into the pool from now on: free it before admission
       if (pool_need > P->pool.n) P->ws.release(&P->bytes);
       add(P->pool, pool_need);
@@ -1229,28 +1318,15 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
     P->f64shell.release(&P->bytes);
   } else {
     // pair reductions
-    P->pool.ensure((size_t)nb * P->comps.size() * Ng * 4, &P->bytes);
-    std::vector<int> all(nmult);
-    for (int i = 0; i < nmult; ++i) all[i] = i;
+    P->pool.ensure((size_t)(nbk == nb ? nb : 2 * nbk) * P->comps.size() * Ng * 4, &P->bytes);
     // i = j != k shot term: unit shells, q fields of every pass
-    shell_fields(P, nullptr, true, &launches);
-    if (npass > 1 && pair_split_gsets()) {
-      // one launch per G set: outputs [gset][mult][b1][b2] as with a single launch
-      for (int gs = 0; gs < npass; ++gs) {
-        std::vector<double> part;
-        run_pair(P, all, 1, nD, P->qf.as<float>() + (size_t)gs * nD * Ng, part, &launches);
-        cU.insert(cU.end(), part.begin(), part.end());
-      }
-    } else {
-      run_pair(P, all, npass, nD, P->qf.as<float>(), cU, &launches);
-    }
+    pair_set(P, nullptr, true, npass, P->qf.as<float>(), nbk, cU, &launches);
     // data
-    shell_fields(P, P->pass_spec[0].as<float2>() + (size_t)P->d00 * Nk, false, &launches);
-    run_pair(P, all, 1, nD, P->gf[0].as<float>(), cD, &launches);
-    if (npass == 2) {
-      shell_fields(P, P->pass_spec[1].as<float2>() + (size_t)P->d00 * Nk, false, &launches);
-      run_pair(P, all, 1, nD, P->gf[1].as<float>(), cW, &launches);
-    }
+    pair_set(P, P->pass_spec[0].as<float2>() + (size_t)P->d00 * Nk, false, 1, P->gf[0].as<float>(), nbk, cD,
+             &launches);
+    if (npass == 2)
+      pair_set(P, P->pass_spec[1].as<float2>() + (size_t)P->d00 * Nk, false, 1, P->gf[1].as<float>(), nbk, cW,
+               &launches);
   }
   BISP_CUDA(cudaEventRecord(P->ev1, s));
   int flag = 0;

@@ -223,6 +223,47 @@ def test_estimator_parity_fp64(case, block, monkeypatch):
         assert_close(o32[k], o64[k], what=f"fp32 vs fp64 {k}")
 
 
+@pytest.mark.parametrize("case,block,nbins", [("survey_local", 3, 7), ("box_tsc_ilv", 2, 7), ("box_cic", 0, 34)])
+def test_estimator_parity_blocked(case, block, nbins, monkeypatch):
+    """Shell fields held for blocks of bins (two blocks resident, one pair launch per union):
+    forced blocks of 3 (7 bins: a one-bin last block) and 2, and 34 bins (more than one pair
+    launch covers: blocks of 16), against the oracle and against the unblocked path."""
+    c = CASES[case]
+    N, L = c["N"], c["L"]
+    kf = 2 * np.pi / L
+    edges = kf * (np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5, 11.0, 15.5]) if nbins == 7
+                  else np.linspace(1.0, 15.5, nbins + 1))
+    if c["los"] == "global":
+        gal = {"xyz": synthcat.periodic_catalog(N, L, c["np_"], seed=100 + N)}
+        ran = None
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="global", mas=c["mas"], interlace=c["interlace"])
+    else:
+        gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="local", observer=obs, mas=c["mas"],
+                     interlace=c["interlace"], P0=1e4, window=True)
+    ref = E.measure(p, gal, ran)
+    outs = {}
+    for blocked in (True, False):
+        if blocked and block:
+            monkeypatch.setenv("BISP_BLOCK_BINS", str(block))
+        else:
+            monkeypatch.delenv("BISP_BLOCK_BINS", raising=False)
+        if not blocked and nbins > 32:
+            continue
+        with _plan(p) as plan:
+            _assign(plan, 0, gal)
+            if ran is not None:
+                _assign(plan, 1, ran)
+            outs[blocked] = plan.measure()
+            assert plan.info()["pair_kernel"] == 1
+    assert np.array_equal(outs[True]["nmodes"], ref["nmodes"])
+    keys = ["B", "shot"] + (["window", "window_shot"] if ran is not None else [])
+    for k in keys:
+        assert_close(outs[True][k], ref[k], what=f"blocked {k}")
+        if False in outs:
+            assert_close(outs[True][k], outs[False][k], tol=1e-6, what=f"blocked vs unblocked {k}")
+
+
 def test_default_pair_kernel_is_mma_sync(monkeypatch):
     monkeypatch.delenv("BISP_PAIR_KERNEL", raising=False)
     c = CASES["box_cic"]
