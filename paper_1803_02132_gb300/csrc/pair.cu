@@ -583,10 +583,6 @@ __global__ void __launch_bounds__(NTHR, 1)
   const int e0 = xb ? J.s_off[T.xslot] : 0, e1 = xb ? J.s_off[T.xslot + 1] : 0;
   const unsigned xoff = xb ? 0u : (unsigned)T.xdir * 4096u, yoff = (unsigned)T.ydir * 4096u;
   const int hfirst = ksplit == 2 ? ks : 0, hlast = ksplit == 2 ? ks + 1 : 2;
-  // tiles of bins >= n_b hold zeros (TMA fill): a warp whose 16 rows are all beyond n_b, and
-  // the 8-column MMA tiles beyond n_b, are skipped (jobs over few bins, e.g. block unions)
-  const bool rows_live = 16 * mi < J.nb;
-  const int ncol = J.nb;
 
   if (tid == 0 && blockIdx.x < nchunk) issue(blockIdx.x, 0);
   int it = 0;
@@ -638,7 +634,7 @@ __global__ void __launch_bounds__(NTHR, 1)
     float c[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) c[q] = 0.f;
-    for (int hh = rows_live ? hfirst : hlast; hh < hlast; ++hh) {
+    for (int hh = hfirst; hh < hlast; ++hh) {
       const unsigned fh = base + sbo + hh * L.half;
       const float* hr = Hs + hh * 32 + 2 * tq;
 #pragma unroll
@@ -662,14 +658,7 @@ __global__ void __launch_bounds__(NTHR, 1)
           ldsm_x4(fh + xoff + loffA + poffA[kk], av);
         }
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          if (16 * i < ncol) {
-            ldsm_x4(fh + yoff + loffB[i] + poffB[kk], bv[i]);
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) bv[i][e] = 0u;
-          }
-        }
+        for (int i = 0; i < 2; ++i) ldsm_x4(fh + yoff + loffB[i] + poffB[kk], bv[i]);
         uint32_t ah[4], al[4], bh[4][2], bl[4][2];
 #pragma unroll
         for (int e = 0; e < 4; ++e) split_tf32(av[e], ah[e], al[e]);
@@ -679,14 +668,11 @@ __global__ void __launch_bounds__(NTHR, 1)
           for (int e = 0; e < 4; ++e) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
         // small products first, pass-major so that consecutive MMAs are independent
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-          if (8 * ni < ncol) mma_tf32(c + ni * 4, al, bh[ni]);
+        for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-          if (8 * ni < ncol) mma_tf32(c + ni * 4, ah, bl[ni]);
+        for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-          if (8 * ni < ncol) mma_tf32(c + ni * 4, ah, bh[ni]);
+        for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
       }
     }
 #pragma unroll
