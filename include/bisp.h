@@ -68,6 +68,17 @@ typedef enum { BISP_DATA = 0, BISP_RANDOMS = 1 } bisp_catalog;
  * spectra, upcast) and the shell averages of the shot-noise terms. */
 typedef enum { BISP_FP32 = 0, BISP_FP64 = 1 } bisp_precision;
 
+/* What bisp_measure estimates.  BISP_BISPECTRUM: B_{l1 l2 L}(k1, k2) (Eq. bi_estimator_FFTs).
+ * BISP_THREEPT: the three-point-function multipoles zeta_{l1 l2 L}(r1, r2) (Sec. 4.3,
+ * Eq. reduced_xi_estimator) and, as the window output, the three-point window multipoles
+ * Q_{l1 l2 L}(r1, r2) (Sec. 6.1, Eq. Q).  For BISP_THREEPT the bins are sets of mesh
+ * separations s (integer, |s_i| <= N/2 - 1) with k_edges[a] <= H |s| < k_edges[a+1] (H the
+ * cell size, edges in Mpc/h, the first may be 0: a bin [0, e_1) with e_1 < H holds s = 0
+ * only); F_l^m(x; r_a) averages y_l^{m*}(s_hat) delta n(x + s) over the bin, applied as a
+ * k-space filter (the FFT of the separation kernel); the only shot-noise term is i = j != k,
+ * on r_a = r_b; nmodes returns the number of separations per bin.  BISP_FP32 only. */
+typedef enum { BISP_BISPECTRUM = 0, BISP_THREEPT = 1 } bisp_estimator;
+
 typedef struct {
   int nmesh;               /* N, a power of two, 16..1024 */
   double box_len;          /* L [Mpc/h]; the mesh covers [0, L)^3 */
@@ -86,6 +97,7 @@ typedef struct {
   size_t max_device_bytes; /* 0: free device memory minus a reserve; else the admission cap */
   int want_window;         /* 1: also the randoms-only window bispectrum (needs randoms) */
   int precision;           /* bisp_precision (0: BISP_FP32) */
+  int estimator;           /* bisp_estimator (0: BISP_BISPECTRUM) */
 } bisp_params;
 
 /* Create a plan.  Validates params (BISP_EINVAL names the offending field), computes the

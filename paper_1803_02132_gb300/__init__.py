@@ -24,6 +24,7 @@ LOS = {"global": 0, "local": 1}
 MAS = {"NGP": 1, "CIC": 2, "TSC": 3, 1: 1, 2: 2, 3: 3}
 DATA, RANDOMS = 0, 1
 PRECISION = {"fp32": 0, "fp64": 1, 0: 0, 1: 1}
+ESTIMATOR = {"bispectrum": 0, "threept": 1, 0: 0, 1: 1}
 
 
 class BispError(RuntimeError):
@@ -36,7 +37,8 @@ class _Params(C.Structure):
     _fields_ = [("nmesh", C.c_int), ("box_len", C.c_double), ("k_edges", C.POINTER(C.c_double)),
                 ("nbins", C.c_int), ("ells", C.POINTER(C.c_int)), ("n_mult", C.c_int), ("los", C.c_int),
                 ("observer", C.c_double * 3), ("mas", C.c_int), ("interlace", C.c_int), ("fkp_P0", C.c_double),
-                ("max_device_bytes", C.c_size_t), ("want_window", C.c_int), ("precision", C.c_int)]
+                ("max_device_bytes", C.c_size_t), ("want_window", C.c_int), ("precision", C.c_int),
+                ("estimator", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -115,7 +117,10 @@ class Plan:
 
     def __init__(self, nmesh, box_len, k_edges, ells, los="global", observer=(0.0, 0.0, 0.0), mas="TSC",
                  interlace=False, fkp_P0=0.0, want_window=False, max_device_bytes=0, stream=None,
-                 precision="fp32"):
+                 precision="fp32", estimator="bispectrum"):
+        """k_edges: k-bin edges [h/Mpc] for the bispectrum, r-bin edges [Mpc/h] for the
+        three-point function (estimator="threept"; measure() then returns zeta as "B" and the
+        window multipoles Q as "window")."""
         self._edges = np.ascontiguousarray(k_edges, dtype=np.float64)
         self._ells = np.ascontiguousarray(np.asarray(ells, dtype=np.int32).reshape(-1))
         p = _Params()
@@ -133,6 +138,7 @@ class Plan:
         p.max_device_bytes = int(max_device_bytes)
         p.want_window = 1 if want_window else 0
         p.precision = PRECISION[precision]
+        p.estimator = ESTIMATOR[estimator]
         self.nbins = p.nbins
         self.want_window = bool(want_window)
         self.n_mult = p.n_mult

@@ -8,6 +8,8 @@
 //    (-i)^l Re/Im y_l^{m*}(k) / N_mode (times the density or 1).
 // Layout: real mesh [x][y][z] (z fastest); half spectrum [nx][ny][nz], nz < N/2 (the
 // nz = N/2 plane is dropped: every spectrum is zero on the Nyquist planes).
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -225,6 +227,31 @@ __device__ __forceinline__ float cw2_val(const float* t, int N, int ix, int iy, 
   return v;
 }
 
+// separation kernels of one r-bin (three-point function), see RKernelArgs
+__global__ void __launch_bounds__(256) k_rshell_kernel(const RKernelArgs a) {
+  const int N = a.N;
+  const size_t Ng = (size_t)N * N * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t o = a.offs[i];
+    const int sx = (int)(o & 1023u) - 512, sy = (int)((o >> 10) & 1023u) - 512, sz = (int)((o >> 20) & 1023u) - 512;
+    const size_t cell = ((size_t)(sx & (N - 1)) * N + (size_t)(sy & (N - 1))) * N + (size_t)(sz & (N - 1));
+    for (int c = 0; c < a.nc; ++c) {
+      // part of y_l^{m*}(s_hat): F_l^m = A + i B with A, B the separation averages of its real
+      // and imaginary parts
+      const float2 y = ylm_one(a.l[c], a.m[c], (float)sx, (float)sy, (float)sz, a.ynorm);
+      a.mesh[c * Ng + cell] = (a.part[c] ? -y.y : y.x) * a.inv_nr;
+    }
+  }
+}
+
+void launch_rshell_kernel(const RKernelArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return;
+  if (a.nc < 1 || a.nc > 32) throw Error{1, "launch_rshell_kernel: nc out of range"};
+  const int blocks = (int)std::min<int64_t>((a.n + 255) / 256, 4096);
+  k_rshell_kernel<<<blocks, 256, 0, s>>>(a);
+  BISP_CHECK_LAUNCH();
+}
+
 // scratch layout per field: T1 [N][2P+1][Pz], T2 [N][N][Pz]
 struct InvGeo {
   int N, P, Pz, ny;
@@ -307,6 +334,10 @@ __global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(float2* t1all, const float
           const size_t gi = ((size_t)e * N + jy) * NH + nz;
           if (F.kind == SRC_PLAIN) {
             v = cscale(F.A[gi], F.scale);
+          } else if (F.kind == SRC_KERNEL) {
+            // conj(K) A: the k-space filter of the separation average (Sec. 4.3); the kernel
+            // is real, so the product is Hermitian for every l
+            v = cmul(cconj(F.K[gi]), F.unit ? make_float2(1.f, 0.f) : F.A[gi]);
           } else {  // SRC_QSHOT
             const float2 a = F.A[gi], b = F.B[gi];
             v = cmul(a, cconj(b));

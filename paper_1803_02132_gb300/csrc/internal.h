@@ -93,14 +93,17 @@ void forward_fft(float* mesh0, float* mesh1, int count, int N, int mas, const fl
 // 32nd roots of unity for the in-register DFTs (once per process)
 
 // Inverse transforms from half spectra to real fields, pruned to |n_i| <= P.
-enum SrcKind { SRC_PLAIN = 0, SRC_QSHOT = 1, SRC_SHELL = 2 };
+enum SrcKind { SRC_PLAIN = 0, SRC_QSHOT = 1, SRC_SHELL = 2, SRC_KERNEL = 3 };
 struct InvField {
   // SRC_PLAIN:  spec(k) = scale * A(k)
   // SRC_QSHOT:  spec(k) = scale * (A(k) conj(B(k)) - sbar * cw2(k))
   // SRC_SHELL:  spec(k) = mask_b(k)/Nm * (-i)^l * part(y_l^{m*}(k)) * (A(k) or 1)
+  // SRC_KERNEL: spec(k) = conj(K(k)) * (A(k) or 1), K the forward FFT of a real separation
+  //             kernel (three-point function); every mode but the Nyquist planes
   int kind;
   const float2* A;
   const float2* B;
+  const float2* K;
   float sbar;
   float scale;
   int l, m, part, unit;   // SRC_SHELL
@@ -119,6 +122,21 @@ struct InvBatch {
   int* err;               // set (never cleared) when a bounded wait gives up
 };
 size_t inverse_scratch_bytes(int N, int P, int nf);
+
+// Separation kernels of one r-bin (three-point function, Sec. 4.3): mesh c of `mesh`
+// ([nc][N][N][N] floats, zeroed by the caller) gets part_c(y_{l_c}^{m_c *}(s_hat)) * inv_nr at
+// the cell s mod N of every separation s of the list (packed (sx+512) | (sy+512) << 10 |
+// (sz+512) << 20); y(0) = delta_{l0}.
+struct RKernelArgs {
+  int N, nc;
+  int l[32], m[32], part[32];
+  float inv_nr;
+  const uint32_t* offs;
+  int64_t n;
+  const float* ynorm;
+  float* mesh;
+};
+void launch_rshell_kernel(const RKernelArgs& a, cudaStream_t s);
 void inverse_fft(const InvBatch& b, const float2* tw, void* scratch, cudaStream_t s, int* launches);
 
 // ---- shell sums and pair reduction (measure.cu) -----------------------------------
@@ -143,6 +161,11 @@ struct ZsumArgs {
   int nblk;
 };
 void launch_zsum(const ZsumArgs& a, cudaStream_t s);
+
+// out[i * nf + c] = fields[c * Ng + cell of -s_i] for the packed separations s_i (as in
+// RKernelArgs): real fields at the negated separations of the r-bins
+void launch_gather_neg(const float* fields, int64_t Ng, int nf, const uint32_t* offs, int64_t n, int N, float* out,
+                       cudaStream_t s);
 
 struct PairRecipe { int comp, g; float coef; };
 struct PairTermDesc {

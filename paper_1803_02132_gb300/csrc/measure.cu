@@ -162,4 +162,25 @@ void launch_zsum(const ZsumArgs& a, cudaStream_t s) {
   BISP_CHECK_LAUNCH();
 }
 
+
+// real fields at the negated separations of the r-bins (three-point shot noise, Sec. 4.3)
+__global__ void __launch_bounds__(256) k_gather_neg(const float* __restrict__ fields, int64_t Ng, int nf,
+                                                     const uint32_t* __restrict__ offs, int64_t n, int N,
+                                                     float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t o = offs[i];
+    const int sx = 512 - (int)(o & 1023u), sy = 512 - (int)((o >> 10) & 1023u), sz = 512 - (int)((o >> 20) & 1023u);
+    const size_t cell = ((size_t)(sx & (N - 1)) * N + (size_t)(sy & (N - 1))) * N + (size_t)(sz & (N - 1));
+    for (int c = 0; c < nf; ++c) out[i * nf + c] = fields[c * Ng + cell];
+  }
+}
+
+void launch_gather_neg(const float* fields, int64_t Ng, int nf, const uint32_t* offs, int64_t n, int N, float* out,
+                       cudaStream_t s) {
+  if (n <= 0) return;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  k_gather_neg<<<blocks, 256, 0, s>>>(fields, Ng, nf, offs, n, N, out);
+  BISP_CHECK_LAUNCH();
+}
+
 }  // namespace bisp

@@ -176,6 +176,7 @@ void bisp::set_last_error(const std::string& m) { g_err = m; }
 struct bisp_plan {
   // parameters
   int N = 0, NH = 0, nb = 0, nmult = 0, los = 0, mas = 2, interlace = 0, want_window = 0, precision = 0;
+  int estimator = 0;  // bisp_estimator
   double L = 0, H = 0, kF = 0, V = 0, P0 = 0, obs[3] = {0, 0, 0};
   size_t max_bytes = 0;
   int64_t Ng = 0, Nk = 0;
@@ -194,6 +195,10 @@ struct bisp_plan {
   std::vector<double> nmodes;
   std::vector<uint32_t> zlist;
   std::vector<int64_t> zoff;
+  // three-point function: separations of r-bin a at roff[roff_off[a] .. roff_off[a+1]), packed
+  // (sx+512) | (sy+512) << 10 | (sz+512) << 20
+  std::vector<uint32_t> roff;
+  std::vector<int64_t> roff_off;
   std::vector<Comp> comps;
   std::map<std::tuple<int, int, int>, int> comp_index;  // (l, m, part) -> index
   std::vector<std::vector<cplx>> Y;                     // [b][lm index (l, m signed)]
@@ -217,6 +222,8 @@ struct bisp_plan {
   DBuf flags;  // device error flags of the measurement kernels
   // plain FP64 form (precision BISP_FP64)
   DBuf ynorm_d, cw2_d, f64work, f64spec, f64g, f64q, f64shell, f64part, f64out;
+  // three-point function: separation lists, unit deconvolution table, kernel meshes, gathers
+  DBuf roff_d, ones, kmesh, gath;
   F64Fft fft64;
   size_t bytes = 0;
   // bookkeeping
@@ -250,9 +257,14 @@ void validate(const bisp_params* p) {
   const int N = p->nmesh;
   if (N < 16 || N > BISP_NMAX || (N & (N - 1))) fail(BISP_EINVAL, "nmesh must be a power of two in [16, 1024]");
   if (!(p->box_len > 0.0) || !std::isfinite(p->box_len)) fail(BISP_EINVAL, "box_len must be positive");
+  if (p->estimator != BISP_BISPECTRUM && p->estimator != BISP_THREEPT) fail(BISP_EINVAL, "estimator");
+  const bool three = p->estimator == BISP_THREEPT;
+  if (three && p->precision != BISP_FP32) fail(BISP_EUNSUPPORTED, "the FP64 form covers the bispectrum only");
   if (p->nbins < 1 || !p->k_edges) fail(BISP_EINVAL, "need nbins >= 1 and k_edges");
   for (int b = 0; b <= p->nbins; ++b) {
-    if (!(p->k_edges[b] > 0.0) || !std::isfinite(p->k_edges[b])) fail(BISP_EINVAL, "k_edges must be positive and finite");
+    const double e = p->k_edges[b];
+    if (!std::isfinite(e) || (three ? !(e >= 0.0) : !(e > 0.0)))
+      fail(BISP_EINVAL, three ? "r edges must be non-negative and finite" : "k_edges must be positive and finite");
     if (b && !(p->k_edges[b] > p->k_edges[b - 1])) fail(BISP_EINVAL, "k_edges must be ascending");
   }
   if (p->n_mult < 1 || !p->ells) fail(BISP_EINVAL, "need n_mult >= 1 and ells");
@@ -393,8 +405,48 @@ void build_shells(bisp_plan* P) {
       if (cnt[b] > 0) P->Y[b][i] = {S[b][i].r / cnt[b], S[b][i].i / cnt[b]};
 }
 
+// r-bins of the three-point function (Sec. 4.3): separations s, integer with |s_i| <= N/2 - 1,
+// in bin a when e_a <= H |s| < e_{a+1} (FP64); N_r(a) separations per bin.  The filtered fields
+// use every mode but the Nyquist planes (prune extent N/2 - 1).
+void build_rshells(bisp_plan* P) {
+  const int N = P->N, nb = P->nb, h = N / 2 - 1;
+  const int ext = (int)std::min<double>(h, std::floor(P->edges[nb] / P->H) + 1.0);
+  const long long qmax = 3LL * ext * ext;
+  std::vector<int> binq(qmax + 1, -1);
+  for (long long q = 0; q <= qmax; ++q) {
+    const double r = P->H * std::sqrt((double)q);
+    const auto it = std::upper_bound(P->edges.begin(), P->edges.end(), r);
+    const int a = (int)(it - P->edges.begin()) - 1;
+    if (a >= 0 && a < nb) binq[q] = a;
+  }
+  std::vector<std::vector<uint32_t>> lists(nb);
+  for (int x = -ext; x <= ext; ++x)
+    for (int y = -ext; y <= ext; ++y)
+      for (int z = -ext; z <= ext; ++z) {
+        const int a = binq[(long long)x * x + (long long)y * y + (long long)z * z];
+        if (a >= 0)
+          lists[a].push_back((uint32_t)(x + 512) | ((uint32_t)(y + 512) << 10) | ((uint32_t)(z + 512) << 20));
+      }
+  P->roff.clear();
+  P->roff_off.assign(nb + 1, 0);
+  P->nmodes.assign(nb, 0.0);
+  for (int a = 0; a < nb; ++a) {
+    P->roff_off[a] = (int64_t)P->roff.size();
+    P->roff.insert(P->roff.end(), lists[a].begin(), lists[a].end());
+    P->nmodes[a] = (double)lists[a].size();
+  }
+  P->roff_off[nb] = (int64_t)P->roff.size();
+  P->Pb.assign(nb, N / 2 - 1);
+  P->qlo.assign(nb, 1);
+  P->qhi.assign(nb, 1);
+  P->zlist.clear();
+  P->zoff.assign(nb + 1, 0);
+  const int lmax = P->ls.empty() ? 0 : P->ls.back();
+  P->Y.assign(nb, std::vector<cplx>((lmax + 1) * (lmax + 1)));
+}
+
 // Real-component expansion of Re sum_{m1 m2 M} 3j F_{l1}^{m1} F_{l2}^{m2} G_L^M with
-//   F_l^m = i^l (A + i B),  F_l^{-m} = (-1)^m i^l (A - i B),
+//   F_l^m = i^l (A + i B),  F_l^{-m} = (-1)^m i^l (A - i B)   (three-point function: no i^l),
 //   G_L^M = R + i I,        G_L^{-M} = (-1)^M (R - i I)   (global LOS: G_L^M = delta_M0 G)
 // grouped into pair-kernel terms on the side with fewer components.
 void build_recipes(bisp_plan* P) {
@@ -404,7 +456,9 @@ void build_recipes(bisp_plan* P) {
   for (auto& e : P->ells) {
     const int l1 = e[0], l2 = e[1], L = e[2];
     std::map<std::tuple<int, int, int>, double> tri;  // (c1, c2, g) -> coef
-    const double il = (((l1 + l2) / 2) & 1) ? -1.0 : 1.0;  // i^{l1+l2}
+    // i^{l1+l2}: the bispectrum's fields are F_l^m = i^l (A + i B); the three-point function's
+    // separation averages are F_l^m = A + i B (F_l^{-m} = (-1)^m conj F_l^m)
+    const double il = P->estimator == BISP_THREEPT ? 1.0 : ((((l1 + l2) / 2) & 1) ? -1.0 : 1.0);
     for (int m1 = -l1; m1 <= l1; ++m1)
       for (int m2 = -l2; m2 <= l2; ++m2) {
         const int M = -m1 - m2;
@@ -526,6 +580,14 @@ void upload_tables(bisp_plan* P) {
   BISP_CUDA(cudaMemcpy(P->ynorm.p, yn.data(), yn.size() * sizeof(float), cudaMemcpyHostToDevice));
   BISP_CUDA(cudaMemcpy(P->qlo_d.p, P->qlo.data(), P->nb * sizeof(long long), cudaMemcpyHostToDevice));
   BISP_CUDA(cudaMemcpy(P->qhi_d.p, P->qhi.data(), P->nb * sizeof(long long), cudaMemcpyHostToDevice));
+  if (P->estimator == BISP_THREEPT) {
+    P->roff_d.ensure(std::max<size_t>(P->roff.size(), 1) * 4, &P->bytes);
+    if (!P->roff.empty())
+      BISP_CUDA(cudaMemcpy(P->roff_d.p, P->roff.data(), P->roff.size() * 4, cudaMemcpyHostToDevice));
+    const std::vector<float> one(N, 1.f);
+    P->ones.ensure(N * sizeof(float), &P->bytes);
+    BISP_CUDA(cudaMemcpy(P->ones.p, one.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+  }
   if (P->precision == BISP_FP64) {
     P->ynorm_d.ensure(ynd.size() * 8, &P->bytes);
     P->cw2_d.ensure(cw2d.size() * 8, &P->bytes);
@@ -837,6 +899,49 @@ void run_inverse(bisp_plan* P, InvBatch& b, int* launches) {
 // shell fields of bins [b0, b1) into the pool, bin b at pool bin slot b - b0 + slot
 void shell_fields(bisp_plan* P, const float2* D00, bool unit, int b0, int b1, int slot, int* launches) {
   const int nc = (int)P->comps.size();
+  if (P->estimator == BISP_THREEPT) {
+    // per r-bin: the separation kernels of its nc components, their forward FFT (no
+    // deconvolution), then the full inverse transforms of conj(K) Delta
+    const size_t kb = (size_t)nc * P->Ng * 4;
+    P->kmesh.ensure(kb, &P->bytes);
+    for (int b = b0; b < b1; ++b) {
+      BISP_CUDA(cudaMemsetAsync(P->kmesh.p, 0, kb, P->stream));
+      RKernelArgs ka{};
+      ka.N = P->N;
+      ka.nc = nc;
+      for (int c = 0; c < nc; ++c) {
+        ka.l[c] = P->comps[c].l;
+        ka.m[c] = P->comps[c].m;
+        ka.part[c] = P->comps[c].part;
+      }
+      ka.n = P->roff_off[b + 1] - P->roff_off[b];
+      ka.inv_nr = ka.n > 0 ? (float)(1.0 / (double)ka.n) : 0.f;
+      ka.offs = P->roff_d.as<uint32_t>() + P->roff_off[b];
+      ka.ynorm = P->ynorm.as<float>();
+      ka.mesh = P->kmesh.as<float>();
+      launch_rshell_kernel(ka, P->stream);
+      *launches += ka.n > 0 ? 1 : 0;
+      forward_fft(P->kmesh.as<float>(), nullptr, nc, P->N, P->mas, P->tw.as<float2>(), P->ones.as<float>(), P->stream,
+                  launches);
+      InvBatch B{};
+      B.P = P->N / 2 - 1;
+      B.nf = nc;
+      for (int c = 0; c < nc; ++c) {
+        InvField& f = B.f[c];
+        f.kind = SRC_KERNEL;
+        f.A = D00;
+        f.K = reinterpret_cast<const float2*>(P->kmesh.as<float>() + (size_t)c * P->Ng);
+        f.l = P->comps[c].l;
+        f.m = P->comps[c].m;
+        f.part = P->comps[c].part;
+        f.unit = unit ? 1 : 0;
+        f.scale = 1.f;
+        f.out = P->pool.as<float>() + ((size_t)(b - b0 + slot) * nc + c) * P->Ng;
+      }
+      run_inverse(P, B, launches);
+    }
+    return;
+  }
   for (int b = b0; b < b1; ++b) {
     InvBatch B{};
     B.P = P->Pb[b];
@@ -1074,6 +1179,77 @@ int f64_block_bins(bisp_plan* P) {
   return nbk;
 }
 
+// Three-point function (Sec. 4.3, Eq. reduced_xi_estimator): zeta = (N H / I) raw / (Ng V^2)
+// from the mesh sums of unnormalised c2r fields, and on r_a = r_b the i = j != k term
+// (N H / I) sum 3j (1/N_r^2) sum_{s in a} y_{l1}^{m1*} y_{l2}^{m2*}(s_hat) (Ng / V^2) q_L^M(-s),
+// q the unnormalised c2r of Q_L^M = delta n_L^M N_0^{0*} - Sbar_L^M C/W^2 (FP64 on the host).
+void threept_combine(bisp_plan* P, int npass, const std::vector<double>& cD, const std::vector<double>& cW,
+                     const std::vector<float>* gq, double* outB, double* outShot, double* outW, double* outWS,
+                     double* outNm) {
+  const int nb = P->nb, nmult = P->nmult, nD = (int)P->dch.size();
+  const bool local = P->los == BISP_LOS_LOCAL;
+  const double Ngd = (double)P->Ng, V2 = P->V * P->V;
+  const int64_t noff = (int64_t)P->roff.size();
+  const int lmax = P->ls.empty() ? 0 : P->ls.back();
+  // y_l^{m*}(s_hat) of every separation, m signed, at [l^2 + m + l][offset]
+  std::vector<std::vector<cplx>> ys((lmax + 1) * (lmax + 1));
+  for (int l : P->ls)
+    for (int m = -l; m <= l; ++m) {
+      auto& t = ys[P->lm_index(l, m)];
+      t.resize(noff);
+      for (int64_t i = 0; i < noff; ++i) {
+        const uint32_t o = P->roff[i];
+        const double sx = (double)((int)(o & 1023u) - 512), sy = (double)((int)((o >> 10) & 1023u) - 512),
+                     sz = (double)((int)((o >> 20) & 1023u) - 512);
+        ystar_host(l, m, sx, sy, sz, &t[i].r, &t[i].i);
+      }
+    }
+  for (int k = 0; k < npass; ++k) {
+    const std::vector<double>& raw = k == 0 ? cD : cW;
+    const std::vector<float>& g = gq[k];
+    double* oB = k == 0 ? outB : outW;
+    double* oS = k == 0 ? outShot : outWS;
+    for (int mu = 0; mu < nmult; ++mu) {
+      const int l1 = P->ells[mu][0], l2 = P->ells[mu][1], L = P->ells[mu][2];
+      const double pref = (double)((2 * l1 + 1) * (2 * l2 + 1) * (2 * L + 1)) * wigner3j(l1, l2, L, 0, 0, 0) / P->normI;
+      for (int a = 0; a < nb; ++a) {
+        double shot = 0.0;
+        if (P->nmodes[a] > 0) {
+          double acc = 0.0;
+          for (int m1 = -l1; m1 <= l1; ++m1)
+            for (int m2 = -l2; m2 <= l2; ++m2) {
+              const int M = -m1 - m2;
+              if (std::abs(M) > L || (!local && M != 0)) continue;
+              const double w = wigner3j(l1, l2, L, m1, m2, M);
+              if (w == 0.0) continue;
+              const int Lz = local ? L : 0, aM = std::abs(M);
+              const int cr = P->dchan(Lz, aM, 0), ci = aM ? P->dchan(Lz, aM, 1) : -1;
+              const double sg = (M < 0 && (aM & 1)) ? -1.0 : 1.0;  // q^{-M} = (-1)^M conj(q^M)
+              const auto& y1 = ys[P->lm_index(l1, m1)];
+              const auto& y2 = ys[P->lm_index(l2, m2)];
+              for (int64_t i = P->roff_off[a]; i < P->roff_off[a + 1]; ++i) {
+                const double qr = sg * g[(size_t)i * nD + cr];
+                const double qi = ci >= 0 ? (M < 0 ? -sg : sg) * g[(size_t)i * nD + ci] : 0.0;
+                const cplx yy = cm(y1[i], y2[i]);
+                acc += w * (yy.r * qr - yy.i * qi);
+              }
+            }
+          shot = pref * acc * Ngd / V2 / (P->nmodes[a] * P->nmodes[a]);
+        }
+        for (int b = 0; b < nb; ++b) {
+          const size_t o = ((size_t)mu * nb + a) * nb + b;
+          const double s_ab = a == b ? shot : 0.0;
+          const double z = pref * raw[(size_t)mu * nb * nb + (size_t)a * nb + b] / (Ngd * V2);
+          if (oB) oB[o] = z - s_ab;
+          if (oS) oS[o] = s_ab;
+        }
+      }
+    }
+  }
+  if (outNm)
+    for (int a = 0; a < nb; ++a) outNm[a] = P->nmodes[a];
+}
+
 void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, double* outWS, double* outNm) {
   Catalog& G = P->cat[BISP_DATA];
   Catalog& R = P->cat[BISP_RANDOMS];
@@ -1100,6 +1276,7 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
   const int npass = (P->want_window && have_r) ? 2 : 1;
   const int nb = P->nb, nmult = P->nmult;
   const bool f64 = P->precision == BISP_FP64;
+  const bool three = P->estimator == BISP_THREEPT;
   int nbk = nb;  // bins per resident block of FP32 shell fields
   // memory admission for the measurement buffers
   {
@@ -1109,6 +1286,7 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
       add(P->pass_spec[k], (size_t)(nD + nN) * Nk * 8);
       if (!f64) add(P->gf[k], (size_t)nD * Ng * 4);
     }
+    if (three) add(P->kmesh, P->comps.size() * (size_t)Ng * 4);
     if (!f64) {
       add(P->qf, (size_t)npass * nD * Ng * 4);
       // inverse-transform scratch still to grow (G and Q batches, the widest shell batch)
@@ -1247,8 +1425,8 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
         run_inverse(P, Q, &launches);
       }
     }
-    // shell sums Z(b; l, m, L, M) for M >= 0 (FP64)
-    {
+    // shell sums Z(b; l, m, L, M) for M >= 0 (FP64; the bispectrum's i != j = k, i = k != j)
+    if (!three) {
       std::vector<std::pair<int, int>> lm;
       for (int l : P->ls)
         for (int m = -l; m <= l; ++m) lm.push_back({l, m});
@@ -1319,14 +1497,29 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
   } else {
     // pair reductions
     P->pool.ensure((size_t)(nbk == nb ? nb : 2 * nbk) * P->comps.size() * Ng * 4, &P->bytes);
-    // i = j != k shot term: unit shells, q fields of every pass
-    pair_set(P, nullptr, true, npass, P->qf.as<float>(), nbk, cU, &launches);
+    // i = j != k shot term: unit shells, q fields of every pass (the three-point function
+    // reads its q fields at the separations of each r-bin instead, below)
+    if (!three) pair_set(P, nullptr, true, npass, P->qf.as<float>(), nbk, cU, &launches);
     // data
     pair_set(P, P->pass_spec[0].as<float2>() + (size_t)P->d00 * Nk, false, 1, P->gf[0].as<float>(), nbk, cD,
              &launches);
     if (npass == 2)
       pair_set(P, P->pass_spec[1].as<float2>() + (size_t)P->d00 * Nk, false, 1, P->gf[1].as<float>(), nbk, cW,
                &launches);
+  }
+  std::vector<float> gq[2];
+  if (three) {
+    const int64_t noff = (int64_t)P->roff.size();
+    P->gath.ensure(std::max<size_t>((size_t)noff * nD * 4, 256), &P->bytes);
+    for (int k = 0; k < npass; ++k) {
+      launch_gather_neg(P->qf.as<float>() + (size_t)k * nD * Ng, Ng, nD, P->roff_d.as<uint32_t>(), noff, P->N,
+                        P->gath.as<float>(), s);
+      ++launches;
+      gq[k].resize((size_t)noff * nD);
+      if (noff)
+        BISP_CUDA(cudaMemcpyAsync(gq[k].data(), P->gath.p, gq[k].size() * 4, cudaMemcpyDeviceToHost, s));
+      BISP_CUDA(cudaStreamSynchronize(s));
+    }
   }
   BISP_CUDA(cudaEventRecord(P->ev1, s));
   int flag = 0;
@@ -1337,6 +1530,10 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
   BISP_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
   P->ms_measure = ms;
   P->launches_measure = launches;
+  if (three) {
+    threept_combine(P, npass, cD, cW, gq, outB, outShot, outW, outWS, outNm);
+    return;
+  }
   // host FP64: normalisation, 3j-contracted shell terms, subtraction
   const double Ngd = (double)Ng;
   for (int k = 0; k < npass; ++k) {
@@ -1395,7 +1592,8 @@ void destroy(bisp_plan* P) {
   size_t* t = &P->bytes;
   for (auto* d : {&P->tw, &P->winv, &P->ynorm, &P->cw2, &P->qlo_d, &P->qhi_d, &P->zmodes, &P->zmode_off, &P->pool, &P->invscr, &P->pairscr,
                   &P->pairout, &P->zpart, &P->ws, &P->flags, &P->ynorm_d, &P->cw2_d, &P->f64work, &P->f64spec,
-                  &P->f64g, &P->f64q, &P->f64shell, &P->f64part, &P->f64out})
+                  &P->f64g, &P->f64q, &P->f64shell, &P->f64part, &P->f64out, &P->roff_d, &P->ones,
+                  &P->kmesh, &P->gath})
     d->release(t);
   f64_fft_destroy(P->fft64);
   for (int k = 0; k < 2; ++k) {
@@ -1464,6 +1662,7 @@ bisp_status bisp_plan_create(bisp_plan** out, const bisp_params* p, void* stream
     P->max_bytes = p->max_device_bytes;
     P->want_window = p->want_window ? 1 : 0;
     P->precision = p->precision;
+    P->estimator = p->estimator;
     const char* dbg = std::getenv("BISP_DEBUG");
     P->debug_mesh = dbg && std::strstr(dbg, "BISP_DEBUG_KEEP_MESH");
     int dev = 0;
@@ -1477,7 +1676,10 @@ bisp_status bisp_plan_create(bisp_plan** out, const bisp_params* p, void* stream
     BISP_CUDA(cudaEventCreate(&P->ev0));
     BISP_CUDA(cudaEventCreate(&P->ev1));
     build_channels(P);
-    build_shells(P);
+    if (P->estimator == BISP_THREEPT)
+      build_rshells(P);
+    else
+      build_shells(P);
     build_recipes(P);
     upload_tables(P);
   });

@@ -264,6 +264,42 @@ def test_estimator_parity_blocked(case, block, nbins, monkeypatch):
             assert_close(outs[True][k], outs[False][k], tol=1e-6, what=f"blocked vs unblocked {k}")
 
 
+@pytest.mark.parametrize("case,r0", [("box_tsc_ilv", False), ("survey_local", False), ("survey_local", True)])
+def test_threept_parity(case, r0, monkeypatch):
+    """Three-point-function multipoles zeta and window multipoles Q (Sec. 4.3, Sec. 6.1)
+    against the oracle: r-bins of mesh separations (a first bin [0, H/2) holds s = 0 only),
+    shot noise on r_a = r_b, separation counts exact."""
+    from oracle import threept as T
+
+    monkeypatch.delenv("BISP_BLOCK_BINS", raising=False)
+    c = CASES[case]
+    N, L = c["N"], c["L"]
+    H = L / N
+    edges = H * np.array(([0.0, 0.5] if r0 else [0.9]) + [1.5, 2.05, 2.95, 4.1, 6.0, 8.5])
+    if c["los"] == "global":
+        gal = {"xyz": synthcat.periodic_catalog(N, L, c["np_"], seed=100 + N)}
+        ran = None
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="global", mas=c["mas"], interlace=c["interlace"])
+    else:
+        gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="local", observer=obs, mas=c["mas"],
+                     interlace=c["interlace"], P0=1e4, window=True)
+    ref = T.measure(p, gal, ran)
+    with _plan(p, estimator="threept") as plan:
+        _assign(plan, 0, gal)
+        if ran is not None:
+            _assign(plan, 1, ran)
+        out = plan.measure()
+        again = plan.measure()
+    assert np.array_equal(out["nmodes"], ref["nr"])
+    assert np.array_equal(out["B"], again["B"])
+    assert_close(out["B"], ref["zeta"], what="zeta")
+    assert_close(out["shot"], ref["shot"], what="zeta shot")
+    if ran is not None:
+        assert_close(out["window"], ref["window"], what="Q")
+        assert_close(out["window_shot"], ref["window_shot"], what="Q shot")
+
+
 def test_default_pair_kernel_is_mma_sync(monkeypatch):
     monkeypatch.delenv("BISP_PAIR_KERNEL", raising=False)
     c = CASES["box_cic"]
