@@ -60,6 +60,11 @@ WORKLOADS = {
                     edges=list(np.round(np.linspace(0.005, 0.405, 41), 6)),
                     ells=[(0, 0, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2)], mas="TSC", interlace=True, P0=0.0,
                     window=False),
+    # three-point-function multipoles and window Q on the 512^3 survey: 25 r-bins of 8 Mpc/h
+    "survey512_zeta": dict(kind="survey", N=512, L=3000.0, n_gen=256, observer=(1500.0, 1500.0, -300.0),
+                           n_gal=1_000_000, n_ran=50_000_000, edges=list(np.round(np.linspace(10.0, 210.0, 26), 6)),
+                           ells=[(0, 0, 0), (2, 0, 2), (1, 1, 2)], mas="TSC", interlace=True, P0=1e4, window=True,
+                           estimator="threept"),
     "box64": dict(kind="box", N=64, L=1000.0, n_gen=64, n_p=200_000, edges=list(np.round(np.linspace(0.01, 0.21, 11), 6)),
                   ells=[(0, 0, 0), (2, 0, 2)], mas="CIC", interlace=False, P0=0.0, window=False),
 }
@@ -153,7 +158,8 @@ def run_gpu(args, w, rank, world):
     stream = torch.cuda.Stream()
     plan = bisp.Plan(w["N"], w["L"], w["edges"], w["ells"], los="local" if w["kind"] == "survey" else "global",
                      observer=w.get("observer", (0, 0, 0)), mas=w["mas"], interlace=w["interlace"],
-                     fkp_P0=w["P0"], want_window=w["window"], stream=stream, precision=args.precision)
+                     fkp_P0=w["P0"], want_window=w["window"], stream=stream, precision=args.precision,
+                     estimator=w.get("estimator", "bispectrum"))
     f64 = args.precision == "fp64"
 
     def step(dev_inputs=True):
@@ -208,7 +214,7 @@ def run_gpu(args, w, rank, world):
     plan.close()
     nbins = n_bins_output(w)
     fp64 = None
-    if not f64 and world == 1 and not args.no_fp64_baseline:
+    if not f64 and world == 1 and not args.no_fp64_baseline and w.get("estimator", "bispectrum") == "bispectrum":
         fp64 = fp64_step(bisp, w, g_dev, r_dev, nbins)
         fp64["speedup"] = (nbins / (ms / args.steps / 1e3)) / fp64["value"]
     ms_step = ms / args.steps
@@ -279,6 +285,9 @@ def fp64_step(bisp, w, g, r, nbins):
 
 def metric_name(w):
     los = "local LOS" if w["kind"] == "survey" else "global LOS"
+    if w.get("estimator") == "threept":
+        mult = "+".join("zeta%d%d%d" % tuple(e) for e in w["ells"]) + (" + window Q" if w["window"] else "")
+        return f"zeta_l1l2L(r1,r2) bins/s at {w['N']}^3 ({los}, {mult})"
     mult = "+".join("B%d%d%d" % tuple(e) for e in w["ells"]) + (" + window" if w["window"] else "")
     return f"B_l1l2L(k1,k2) bins/s at {w['N']}^3 ({los}, {mult})"
 
@@ -311,6 +320,7 @@ def pair_traffic(alg_bytes_per_launch):
 def cpu_baseline(args, w):
     """The FP64 oracle on a bounded sample of the workload, timed on the host cores."""
     from oracle import estimator as E
+    from oracle import threept as T
 
     import synthcat
 
@@ -319,9 +329,15 @@ def cpu_baseline(args, w):
     N = 64
     L = w["L"]
     kN = np.pi * N / L
-    edges = [e for e in w["edges"] if e < 0.9 * kN]
-    if len(edges) < 3:
-        edges = list(np.linspace(w["edges"][0], 0.9 * kN, 4))
+    three = w.get("estimator") == "threept"
+    if three:  # r-bins of at least one cell of the sample's mesh
+        edges = [e for e in w["edges"] if e >= 0.9 * L / N]
+        if len(edges) < 3:
+            edges = list(np.linspace(L / N, 5 * L / N, 4))
+    else:
+        edges = [e for e in w["edges"] if e < 0.9 * kN]
+        if len(edges) < 3:
+            edges = list(np.linspace(w["edges"][0], 0.9 * kN, 4))
     frac = (N / w["N"]) ** 3
     if w["kind"] == "survey":
         gal, ran = synthcat.survey_catalogs(N, L, w["observer"], int(w["n_gal"] * frac), int(w["n_ran"] * frac), 7)
@@ -337,7 +353,7 @@ def cpu_baseline(args, w):
     c0 = time.process_time()
     reps = 0
     while reps < 6 and (reps == 0 or time.perf_counter() - t0 < 10.0):
-        E.measure(p, gal, ran)
+        (T.measure if three else E.measure)(p, gal, ran)
         reps += 1
     dt = (time.perf_counter() - t0) / reps
     cpu = (time.process_time() - c0) / reps
@@ -350,7 +366,8 @@ def cpu_baseline(args, w):
     # cells, so the sample's rate is scaled by the cell ratio to the workload's mesh
     return {"value": nbins / dt * frac, "unit": "bins/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle on the same recipe at {N}^3 (1/{int(round(1 / frac))} of the cells and particles), "
-                      f"{nb} bins below that mesh's Nyquist, {nbins} bins in {dt:.1f} s (mean of {reps} runs) "
+                      f"{nb} bins {'of at least one cell' if three else 'below that mesh' + chr(39) + 's Nyquist'}, "
+                      f"{nbins} bins in {dt:.1f} s (mean of {reps} runs) "
                       f"({nbins / dt:.3g} bins/s at {N}^3); value = that rate x {N}^3/{w['N']}^3",
             "sample_bins_per_s": nbins / dt, "seconds": dt, "cpu_seconds": cpu}
 
