@@ -150,6 +150,31 @@ typedef struct {
  * are not measured).  No counterpart in the paper beyond its use of many mocks (Sec. 5.4). */
 bisp_status bisp_measure_batch(bisp_plan* const* plans, const bisp_outputs* outs, int nplans);
 
+/* Covariance of a batch of measurements (Sec. 5.3, Eq. Covariance): X holds n_mock data
+ * vectors of n_bin values, [n_mock][n_bin] host FP64 (for example flattened bisp_measure
+ * outputs of independent realisations).  Outputs (host, caller-owned, NULL to skip): mean
+ * [n_bin]; cov [n_bin][n_bin] = 1/(n_mock - 1) sum_n (X_n - mean)^T (X_n - mean); corr
+ * [n_bin][n_bin] = cov_ij / sqrt(cov_ii cov_jj) (NaN where a variance is 0).  Host only: no
+ * device work.  Errors: BISP_EINVAL for NULL X, n_mock < 2 or n_bin < 1. */
+bisp_status bisp_covariance(const double* X, int n_mock, int n_bin, double* mean, double* cov, double* corr);
+
+/* The factors of App. E: hartlap = (n_mock - n_bin - 2)/(n_mock - 1), the factor on the inverse
+ * covariance; percival_m = (1 + B (n_bin - n_par)) / (1 + A + B (n_par + 1)), the factor on
+ * parameter variances for n_par parameters, with A = 2 / ((n_mock - n_bin - 1)(n_mock - n_bin -
+ * 4)) and B = (n_mock - n_bin - 2) / ((n_mock - n_bin - 1)(n_mock - n_bin - 4)) (App. E prints
+ * square roots in these denominators; without them M tends to 1 for infinitely many
+ * realisations, as a factor for the noise of an estimated covariance must).  Either output may be
+ * NULL.  Errors: BISP_EINVAL for n_mock < 2, n_bin < 1, n_par < 0, or a requested percival_m
+ * with n_mock <= n_bin + 4. */
+bisp_status bisp_covariance_factors(int n_mock, int n_bin, int n_par, double* hartlap, double* percival_m);
+
+/* chi^2 = (x_obs - x_theory)^T C_Hartlap^{-1} (x_obs - x_theory) (App. E) for a covariance cov
+ * [n_bin][n_bin] estimated from n_mock realisations (Cholesky solve in FP64, host only).
+ * Errors: BISP_EINVAL for NULL pointers, n_bin < 1, n_mock < 2, or a covariance that is not
+ * positive definite. */
+bisp_status bisp_chi2(const double* cov, int n_bin, int n_mock, const double* x_obs, const double* x_theory,
+                      double* chi2);
+
 /* Free every resource of the plan (NULL is accepted). */
 bisp_status bisp_plan_destroy(bisp_plan* plan);
 

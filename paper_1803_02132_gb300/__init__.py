@@ -66,9 +66,12 @@ def _load():
     lib.bisp_cell_order.argtypes = [C.c_int, C.c_double, C.c_int, vp, C.c_int64, vp, vp, vp]
     lib.bisp_debug_fetch.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, C.c_size_t]
     lib.bisp_cell_order_noalloc.argtypes = [C.c_int, C.c_double, C.c_int, vp, C.c_int64, vp, vp, vp]
+    lib.bisp_covariance.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp]
+    lib.bisp_covariance_factors.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
+    lib.bisp_chi2.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp]
     for f in ("bisp_plan_create", "bisp_assign", "bisp_measure", "bisp_measure_batch", "bisp_plan_destroy",
-              "bisp_plan_query",
-              "bisp_cell_order", "bisp_debug_fetch", "bisp_cell_order_noalloc"):
+              "bisp_plan_query", "bisp_cell_order", "bisp_debug_fetch", "bisp_cell_order_noalloc",
+              "bisp_covariance", "bisp_covariance_factors", "bisp_chi2"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -250,3 +253,33 @@ def measure_batch(plans):
     handles = (C.c_void_p * max(len(plans), 1))(*[p._h.value for p in plans])
     _check(lib().bisp_measure_batch(handles, arr, len(plans)))
     return outs
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def covariance(X, n_par=None):
+    """Covariance statistics of a batch of data vectors X [n_mock, n_bin] (Eq. Covariance,
+    App. E): dict with mean, cov, corr, hartlap and, when n_par is given, percival_m."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    nm, nb = X.shape
+    mean, cov, corr = np.zeros(nb), np.zeros((nb, nb)), np.zeros((nb, nb))
+    _check(lib().bisp_covariance(_dp(X), nm, nb, _dp(mean), _dp(cov), _dp(corr)))
+    h, m = C.c_double(), C.c_double()
+    _check(lib().bisp_covariance_factors(nm, nb, int(n_par or 0), C.byref(h),
+                                         C.byref(m) if n_par is not None else None))
+    out = {"mean": mean, "cov": cov, "corr": corr, "hartlap": h.value}
+    if n_par is not None:
+        out["percival_m"] = m.value
+    return out
+
+
+def chi2(cov, n_mock, x_obs, x_theory):
+    """(x_obs - x_theory)^T C_Hartlap^{-1} (x_obs - x_theory) (App. E)."""
+    cov = np.ascontiguousarray(cov, dtype=np.float64)
+    xo = np.ascontiguousarray(x_obs, dtype=np.float64)
+    xt = np.ascontiguousarray(x_theory, dtype=np.float64)
+    out = C.c_double()
+    _check(lib().bisp_chi2(_dp(cov), cov.shape[0], int(n_mock), _dp(xo), _dp(xt), C.byref(out)))
+    return out.value
