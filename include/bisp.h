@@ -98,6 +98,10 @@ typedef struct {
   int want_window;         /* 1: also the randoms-only window bispectrum (needs randoms) */
   int precision;           /* bisp_precision (0: BISP_FP32) */
   int estimator;           /* bisp_estimator (0: BISP_BISPECTRUM) */
+  int diagonal_only;       /* 1: only the k1 = k2 (r1 = r2) outputs, the diagonal the paper's
+                              signal-to-noise study rests on (Sec. 4.4, Sec. 5.4); every other
+                              output is NaN.  When the shell fields of all bins do not fit,
+                              each block of bins is then measured alone, with no block pairs. */
 } bisp_params;
 
 /* Create a plan.  Validates params (BISP_EINVAL names the offending field), computes the

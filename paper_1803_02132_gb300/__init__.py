@@ -38,7 +38,7 @@ class _Params(C.Structure):
                 ("nbins", C.c_int), ("ells", C.POINTER(C.c_int)), ("n_mult", C.c_int), ("los", C.c_int),
                 ("observer", C.c_double * 3), ("mas", C.c_int), ("interlace", C.c_int), ("fkp_P0", C.c_double),
                 ("max_device_bytes", C.c_size_t), ("want_window", C.c_int), ("precision", C.c_int),
-                ("estimator", C.c_int)]
+                ("estimator", C.c_int), ("diagonal_only", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -120,7 +120,7 @@ class Plan:
 
     def __init__(self, nmesh, box_len, k_edges, ells, los="global", observer=(0.0, 0.0, 0.0), mas="TSC",
                  interlace=False, fkp_P0=0.0, want_window=False, max_device_bytes=0, stream=None,
-                 precision="fp32", estimator="bispectrum"):
+                 precision="fp32", estimator="bispectrum", diagonal_only=False):
         """k_edges: k-bin edges [h/Mpc] for the bispectrum, r-bin edges [Mpc/h] for the
         three-point function (estimator="threept"; measure() then returns zeta as "B" and the
         window multipoles Q as "window")."""
@@ -142,6 +142,7 @@ class Plan:
         p.want_window = 1 if want_window else 0
         p.precision = PRECISION[precision]
         p.estimator = ESTIMATOR[estimator]
+        p.diagonal_only = 1 if diagonal_only else 0
         self.nbins = p.nbins
         self.want_window = bool(want_window)
         self.n_mult = p.n_mult

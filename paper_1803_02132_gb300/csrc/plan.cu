@@ -177,6 +177,7 @@ struct bisp_plan {
   // parameters
   int N = 0, NH = 0, nb = 0, nmult = 0, los = 0, mas = 2, interlace = 0, want_window = 0, precision = 0;
   int estimator = 0;  // bisp_estimator
+  int diagonal = 0;   // only k1 = k2 outputs
   double L = 0, H = 0, kF = 0, V = 0, P0 = 0, obs[3] = {0, 0, 0};
   size_t max_bytes = 0;
   int64_t Ng = 0, Nk = 0;
@@ -995,6 +996,17 @@ void pair_set(bisp_plan* P, const float2* D00, bool unit, int gsets, const float
   const int nout = gsets * nmult, nblocks = (nb + nbk - 1) / nbk;
   out.assign((size_t)nout * nb * nb, 0.0);
   std::vector<double> res;
+  if (P->diagonal) {  // every block alone: its own pairs hold the diagonal
+    for (int I = 0; I < nblocks; ++I) {
+      const int i0 = I * nbk, ni = std::min(nbk, nb - i0);
+      shell_fields(P, D00, unit, i0, i0 + ni, 0, launches);
+      pairs(ni, res);
+      for (int o = 0; o < nout; ++o)
+        for (int u = 0; u < ni; ++u)
+          out[((size_t)o * nb + i0 + u) * nb + i0 + u] = res[((size_t)o * ni + u) * ni + u];
+    }
+    return;
+  }
   for (int I = 0; I + 1 < nblocks; ++I) {
     const int i0 = I * nbk, ni = std::min(nbk, nb - i0);
     shell_fields(P, D00, unit, i0, i0 + ni, 0, launches);
@@ -1034,7 +1046,8 @@ int fp32_block_bins(bisp_plan* P, size_t other_need) {
   const char* env = std::getenv("BISP_BLOCK_BINS");
   const int force = env ? std::atoi(env) : 0;
   if (P->nb <= 32 && (size_t)P->nb * per_bin <= cap && (force <= 0 || force >= P->nb)) return P->nb;
-  int nbk = (int)std::min<size_t>(16, cap / (2 * per_bin));
+  // diagonal outputs only: one block resident, up to the 32 bins of a pair launch
+  int nbk = P->diagonal ? (int)std::min<size_t>(32, cap / per_bin) : (int)std::min<size_t>(16, cap / (2 * per_bin));
   if (force > 0) nbk = std::min(nbk, force);
   if (nbk < 1) {
     char buf[200];
@@ -1133,6 +1146,7 @@ void f64_pairs(bisp_plan* P, const float2* D00, bool unit, const double* gbase, 
         return slotB + (size_t)(b - j0) * fb + (size_t)c * Ng;
       };
       auto pair = [&](int b1, int b2) {
+        if (P->diagonal && b1 != b2) return;
         for (int gs = 0; gs < gsets; ++gs)
           for (int mu = 0; mu < nmult; ++mu)
             for (const auto& t : P->tri64[mu])
@@ -1240,8 +1254,9 @@ void threept_combine(bisp_plan* P, int npass, const std::vector<double>& cD, con
           const size_t o = ((size_t)mu * nb + a) * nb + b;
           const double s_ab = a == b ? shot : 0.0;
           const double z = pref * raw[(size_t)mu * nb * nb + (size_t)a * nb + b] / (Ngd * V2);
-          if (oB) oB[o] = z - s_ab;
-          if (oS) oS[o] = s_ab;
+          const bool off = P->diagonal && a != b;  // not computed
+          if (oB) oB[o] = off ? NAN : z - s_ab;
+          if (oS) oS[o] = off ? NAN : s_ab;
         }
       }
     }
@@ -1294,7 +1309,7 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
       const size_t inv = std::max(inverse_scratch_bytes(P->N, P->N / 2 - 1, nD),
                                   inverse_scratch_bytes(P->N, pmax, (int)P->comps.size()));
       nbk = fp32_block_bins(P, need + (inv > P->invscr.n ? inv - P->invscr.n : 0));
-      const size_t pool_need = (size_t)(nbk == nb ? nb : 2 * nbk) * P->comps.size() * Ng * 4;
+      const size_t pool_need = (size_t)(nbk == nb || P->diagonal ? nbk : 2 * nbk) * P->comps.size() * Ng * 4;
       // the assignment arena moves into the pool from now on: free it before admission
       if (pool_need > P->pool.n) P->ws.release(&P->bytes);
       add(P->pool, pool_need);
@@ -1496,7 +1511,7 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
     P->f64shell.release(&P->bytes);
   } else {
     // pair reductions
-    P->pool.ensure((size_t)(nbk == nb ? nb : 2 * nbk) * P->comps.size() * Ng * 4, &P->bytes);
+    P->pool.ensure((size_t)(nbk == nb || P->diagonal ? nbk : 2 * nbk) * P->comps.size() * Ng * 4, &P->bytes);
     // i = j != k shot term: unit shells, q fields of every pass (the three-point function
     // reads its q fields at the separations of each r-bin instead, below)
     if (!three) pair_set(P, nullptr, true, npass, P->qf.as<float>(), nbk, cU, &launches);
@@ -1578,8 +1593,9 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
           const double iij = cU[(size_t)(k * nmult + mu) * nb * nb + b1 * nb + b2] / Ngd;
           const double shot = pref * (sh.r + iij);
           const double braw = pref * raw[(size_t)mu * nb * nb + b1 * nb + b2] / Ngd;
-          if (oB) oB[o] = braw - shot;
-          if (oS) oS[o] = shot;
+          const bool off = P->diagonal && b1 != b2;  // not computed
+          if (oB) oB[o] = off ? NAN : braw - shot;
+          if (oS) oS[o] = off ? NAN : shot;
         }
     }
   }
@@ -1663,6 +1679,7 @@ bisp_status bisp_plan_create(bisp_plan** out, const bisp_params* p, void* stream
     P->want_window = p->want_window ? 1 : 0;
     P->precision = p->precision;
     P->estimator = p->estimator;
+    P->diagonal = p->diagonal_only ? 1 : 0;
     const char* dbg = std::getenv("BISP_DEBUG");
     P->debug_mesh = dbg && std::strstr(dbg, "BISP_DEBUG_KEEP_MESH");
     int dev = 0;

@@ -300,6 +300,47 @@ def test_threept_parity(case, r0, monkeypatch):
         assert_close(out["window_shot"], ref["window_shot"], what="Q shot")
 
 
+@pytest.mark.parametrize("case,block,estimator", [("survey_local", 3, "bispectrum"), ("box_cic", 2, "bispectrum"),
+                                                  ("box_tsc_ilv", 0, "threept")])
+def test_diagonal_only(case, block, estimator, monkeypatch):
+    """diagonal_only: the k1 = k2 (r1 = r2) outputs match the oracle, every other output is NaN;
+    with blocks of bins each block is measured alone."""
+    from oracle import threept as T
+
+    if block:
+        monkeypatch.setenv("BISP_BLOCK_BINS", str(block))
+    else:
+        monkeypatch.delenv("BISP_BLOCK_BINS", raising=False)
+    c = CASES[case]
+    N, L = c["N"], c["L"]
+    three = estimator == "threept"
+    edges = (L / N * np.array([0.9, 1.5, 2.05, 2.95, 4.1, 6.0, 8.5]) if three
+             else 2 * np.pi / L * np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5, 11.0, 15.5]))
+    if c["los"] == "global":
+        gal = {"xyz": synthcat.periodic_catalog(N, L, c["np_"], seed=100 + N)}
+        ran = None
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="global", mas=c["mas"], interlace=c["interlace"])
+    else:
+        gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="local", observer=obs, mas=c["mas"],
+                     interlace=c["interlace"], P0=1e4, window=True)
+    ref = T.measure(p, gal, ran) if three else E.measure(p, gal, ran)
+    with _plan(p, estimator=estimator, diagonal_only=True) as plan:
+        _assign(plan, 0, gal)
+        if ran is not None:
+            _assign(plan, 1, ran)
+        out = plan.measure()
+    keys = [("B", "zeta" if three else "B"), ("shot", "shot")]
+    if ran is not None:
+        keys += [("window", "window"), ("window_shot", "window_shot")]
+    nb = len(edges) - 1
+    off = ~np.eye(nb, dtype=bool)
+    for k, rk in keys:
+        d = np.diagonal(out[k], axis1=1, axis2=2)
+        assert_close(d, np.diagonal(ref[rk], axis1=1, axis2=2), what=f"diagonal {k}")
+        assert np.all(np.isnan(out[k][:, off]))
+
+
 def test_default_pair_kernel_is_mma_sync(monkeypatch):
     monkeypatch.delenv("BISP_PAIR_KERNEL", raising=False)
     c = CASES["box_cic"]
