@@ -179,6 +179,42 @@ bisp_status bisp_covariance_factors(int n_mock, int n_bin, int n_par, double* ha
 bisp_status bisp_chi2(const double* cov, int n_bin, int n_mock, const double* x_obs, const double* x_theory,
                       double* chi2);
 
+/* ---- window-convolved model (Sec. 6.2), host FP64, no device work ------------------- */
+
+/* Wigner 9j symbol {j[0] j[1] j[2]; j[3] j[4] j[5]; j[6] j[7] j[8]} of integer arguments
+ * (App. A, Eq. Wigner9j), as a sum over three 6j symbols (Racah's formula).  Errors:
+ * BISP_EINVAL for NULL pointers or j outside [0, 32]. */
+bisp_status bisp_wigner9j(const int* j, double* out);
+
+/* Masked three-point multipoles <zeta_l>_model (Eq. zetaMask) with the integral constraint
+ * zeta_bar (Eq. IC), on an (r1, r2) grid of nr radii r[i] with quadrature weights w[i]
+ * (int dr r^2 f(r) ~ sum_i w_i r_i^2 f(r_i)).  Theory multipoles: n_t triples ells_t (l1, l2, L)
+ * and zeta_t [n_t][nr][nr]; window multipoles: n_q triples ells_q and Q [n_q][nr][nr] (the
+ * measured BISP_THREEPT window output); outputs: n_o triples ells_o and out [n_o][nr][nr],
+ *   out_l = N_l sum_{l' in theory, l'' in window} {l''; l'; l} H_l H_{l1 l1' l1''} H_{l2 l2' l2''}
+ *           H_{L L' L''} / (H_{l'} H_{l''}) Q_{l''} zeta_{l'}  -  Q_l zeta_bar,
+ * H the 3j symbols with zero projections, N_l = (2 l1 + 1)(2 l2 + 1)(2L + 1).  ic = 1 computes
+ * zeta_bar over the multipoles present in both sets (needs Q_000); ic = 0 takes zeta_bar = 0.
+ * zeta_bar may be NULL.  Every l <= 8 and a triangle.  All arrays host, caller-owned.  Errors:
+ * BISP_EINVAL for NULL pointers, empty sets, invalid multipoles, or ic without Q_000. */
+bisp_status bisp_masked_zeta(const int* ells_t, int n_t, const double* zeta_t, const int* ells_q, int n_q,
+                             const double* Q, const int* ells_o, int n_o, const double* r, const double* w, int nr,
+                             int ic, double* out, double* zeta_bar);
+
+/* Hankel transform to the bispectrum (Eq. masked_bispectrum, Eq. HankelTransform):
+ *   B[a][b] = (-i)^{l1+l2} (4 pi)^2 sum_ij w_i r_i^2 w_j r_j^2 j_l1(k1_a r_i) j_l2(k2_b r_j) zeta[i][j]
+ * on host arrays zeta [nr][nr] and B [nk1][nk2]; l1 + l2 even (otherwise the bispectrum is
+ * imaginary: BISP_EUNSUPPORTED), l1, l2 <= 8.  Errors: BISP_EINVAL for NULL pointers or empty grids. */
+bisp_status bisp_zeta_to_bk(int l1, int l2, const double* r, const double* w, int nr, const double* zeta,
+                            const double* k1, int nk1, const double* k2, int nk2, double* B);
+
+/* The inverse transform (Eq. HankelTransform):
+ *   zeta[a][b] = i^{l1+l2} sum_ij wk_i k_i^2 wk_j k_j^2 / (2 pi^2)^2 j_l1(r1_a k_i) j_l2(r2_b k_j) B[i][j]
+ * with B [nk][nk] on one k grid with weights wk (int dk g(k) ~ sum_i wk_i g(k_i)), zeta [nr1][nr2].
+ * Same conditions and errors as bisp_zeta_to_bk. */
+bisp_status bisp_bk_to_zeta(int l1, int l2, const double* k, const double* wk, int nk, const double* B,
+                            const double* r1, int nr1, const double* r2, int nr2, double* zeta);
+
 /* Free every resource of the plan (NULL is accepted). */
 bisp_status bisp_plan_destroy(bisp_plan* plan);
 

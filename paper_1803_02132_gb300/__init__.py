@@ -69,9 +69,15 @@ def _load():
     lib.bisp_covariance.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp]
     lib.bisp_covariance_factors.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
     lib.bisp_chi2.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp]
+    ip = C.POINTER(C.c_int)
+    lib.bisp_wigner9j.argtypes = [ip, dp]
+    lib.bisp_masked_zeta.argtypes = [ip, C.c_int, dp, ip, C.c_int, dp, ip, C.c_int, dp, dp, C.c_int, C.c_int, dp, dp]
+    lib.bisp_zeta_to_bk.argtypes = [C.c_int, C.c_int, dp, dp, C.c_int, dp, dp, C.c_int, dp, C.c_int, dp]
+    lib.bisp_bk_to_zeta.argtypes = [C.c_int, C.c_int, dp, dp, C.c_int, dp, dp, C.c_int, dp, C.c_int, dp]
     for f in ("bisp_plan_create", "bisp_assign", "bisp_measure", "bisp_measure_batch", "bisp_plan_destroy",
               "bisp_plan_query", "bisp_cell_order", "bisp_debug_fetch", "bisp_cell_order_noalloc",
-              "bisp_covariance", "bisp_covariance_factors", "bisp_chi2"):
+              "bisp_covariance", "bisp_covariance_factors", "bisp_chi2", "bisp_wigner9j", "bisp_masked_zeta",
+              "bisp_zeta_to_bk", "bisp_bk_to_zeta"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -284,3 +290,54 @@ def chi2(cov, n_mock, x_obs, x_theory):
     out = C.c_double()
     _check(lib().bisp_chi2(_dp(cov), cov.shape[0], int(n_mock), _dp(xo), _dp(xt), C.byref(out)))
     return out.value
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def wigner9j(j):
+    """Wigner 9j symbol of nine integers (row-major)."""
+    a = np.ascontiguousarray(j, dtype=np.int32).reshape(9)
+    out = C.c_double()
+    _check(lib().bisp_wigner9j(_ip(a), C.byref(out)))
+    return out.value
+
+
+def masked_zeta(theory, window, ells_out, r, w, ic=True):
+    """Masked three-point multipoles (Eq. zetaMask) and the integral constraint (Eq. IC).
+    theory, window: dicts (l1, l2, L) -> [nr, nr] arrays on the radii r with quadrature weights w.
+    Returns ({l: [nr, nr]}, zeta_bar)."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    nr = len(r)
+    lt = list(theory)
+    lq = list(window)
+    et = np.ascontiguousarray(np.array(lt, dtype=np.int32).reshape(-1))
+    eq = np.ascontiguousarray(np.array(lq, dtype=np.int32).reshape(-1))
+    eo = np.ascontiguousarray(np.array(list(ells_out), dtype=np.int32).reshape(-1))
+    zt = np.ascontiguousarray(np.stack([theory[e] for e in lt]), dtype=np.float64)
+    qq = np.ascontiguousarray(np.stack([window[e] for e in lq]), dtype=np.float64)
+    out = np.zeros((len(eo) // 3, nr, nr))
+    zb = C.c_double()
+    _check(lib().bisp_masked_zeta(_ip(et), len(lt), _dp(zt), _ip(eq), len(lq), _dp(qq), _ip(eo), len(eo) // 3,
+                                  _dp(r), _dp(w), nr, 1 if ic else 0, _dp(out), C.byref(zb)))
+    return {tuple(e): out[i] for i, e in enumerate(np.array(list(ells_out)).reshape(-1, 3).tolist())}, zb.value
+
+
+def zeta_to_bk(l1, l2, r, w, zeta, k1, k2):
+    """Hankel transform of zeta [nr, nr] to B [nk1, nk2] (Eq. masked_bispectrum)."""
+    r, w, z, k1, k2 = (np.ascontiguousarray(a, dtype=np.float64) for a in (r, w, zeta, k1, k2))
+    B = np.zeros((len(k1), len(k2)))
+    _check(lib().bisp_zeta_to_bk(int(l1), int(l2), _dp(r), _dp(w), len(r), _dp(z), _dp(k1), len(k1), _dp(k2),
+                                 len(k2), _dp(B)))
+    return B
+
+
+def bk_to_zeta(l1, l2, k, wk, B, r1, r2):
+    """Hankel transform of B [nk, nk] to zeta [nr1, nr2] (Eq. HankelTransform)."""
+    k, wk, B, r1, r2 = (np.ascontiguousarray(a, dtype=np.float64) for a in (k, wk, B, r1, r2))
+    z = np.zeros((len(r1), len(r2)))
+    _check(lib().bisp_bk_to_zeta(int(l1), int(l2), _dp(k), _dp(wk), len(k), _dp(B), _dp(r1), len(r1), _dp(r2),
+                                 len(r2), _dp(z)))
+    return z

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbisp.so")
-SOURCES = ["assign.cu", "fft.cu", "measure.cu", "pair.cu", "plan.cu", "noalloc.cu", "fp64.cu", "stats.cu"]
+SOURCES = ["assign.cu", "fft.cu", "measure.cu", "pair.cu", "plan.cu", "noalloc.cu", "fp64.cu", "stats.cu", "model.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(os.path.dirname(HERE), "include")]
