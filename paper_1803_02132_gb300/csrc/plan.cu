@@ -412,6 +412,9 @@ void build_shells(bisp_plan* P) {
 void build_rshells(bisp_plan* P) {
   const int N = P->N, nb = P->nb, h = N / 2 - 1;
   const int ext = (int)std::min<double>(h, std::floor(P->edges[nb] / P->H) + 1.0);
+  // the separation lists hold at most (2 ext + 1)^3 entries of 4 bytes
+  if ((double)(2 * ext + 1) * (2 * ext + 1) * (2 * ext + 1) > 6.4e7)
+    fail(BISP_EUNSUPPORTED, "r-bins up to this radius reach beyond 199 cells (more than 6.4e7 separations)");
   const long long qmax = 3LL * ext * ext;
   std::vector<int> binq(qmax + 1, -1);
   for (long long q = 0; q <= qmax; ++q) {
