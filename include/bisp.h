@@ -233,7 +233,7 @@ typedef struct {
   double ms_pair;          /* device time of the pair-reduction kernels in the last measure */
   double pair_bytes;       /* algorithmic bytes read by those pair reductions */
   int pair_launches;
-  int pair_kernel;         /* kernel of the last pair reduction: 0 FP32 FMA (more than 32 bins),
+  int pair_kernel;         /* kernel of the last pair reduction: 0 FP32 FMA (jobs outside the tensor-core layout),
                               1 mma.sync TF32 (default), 2 tcgen05 TF32 (BISP_PAIR_KERNEL=tcgen05
                               in the environment, for jobs it covers), 3 FP64 unfused mesh sums
                               (BISP_FP64 plans) */
