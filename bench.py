@@ -65,6 +65,11 @@ WORKLOADS = {
                            n_gal=1_000_000, n_ran=50_000_000, edges=list(np.round(np.linspace(10.0, 210.0, 26), 6)),
                            ells=[(0, 0, 0), (2, 0, 2), (1, 1, 2)], mas="TSC", interlace=True, P0=1e4, window=True,
                            estimator="threept"),
+    # 64 independent periodic realisations on meshes of two sizes (32 at 128^3, 32 at 256^3,
+    # 1e6-4e6 particles each), 15 bins, B000 + B202, measured one after another
+    "batch64": dict(kind="batch", N=256, L=1000.0, n_real=64, sizes=(128, 256), n_p_range=(1_000_000, 4_000_000),
+                    edges=list(np.round(np.linspace(0.01, 0.16, 16), 6)), ells=[(0, 0, 0), (2, 0, 2)], mas="TSC",
+                    interlace=True, P0=0.0, window=False),
     "box64": dict(kind="box", N=64, L=1000.0, n_gen=64, n_p=200_000, edges=list(np.round(np.linspace(0.01, 0.21, 11), 6)),
                   ells=[(0, 0, 0), (2, 0, 2)], mas="CIC", interlace=False, P0=0.0, window=False),
 }
@@ -255,6 +260,83 @@ def run_gpu(args, w, rank, world):
     return out
 
 
+def run_batch(args, w):
+    """A campaign of independent realisations (mixed mesh sizes) through two plans, one per
+    size, each realisation assigned and measured in turn; device-resident inputs."""
+    import torch
+
+    import paper_1803_02132_gb300 as bisp
+    import synthcat
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    rng = np.random.default_rng(2004)
+    cats = []
+    for i in range(w["n_real"]):
+        N = w["sizes"][i % len(w["sizes"])]
+        n_p = int(rng.integers(w["n_p_range"][0], w["n_p_range"][1] + 1))
+        xyz = synthcat.periodic_catalog(N // 2, w["L"], n_p, 3000 + i)
+        cats.append((N, torch.from_numpy(np.ascontiguousarray(xyz, np.float32)).cuda()))
+    stream = torch.cuda.Stream()
+    plans = {N: bisp.Plan(N, w["L"], w["edges"], w["ells"], los="global", mas=w["mas"], interlace=w["interlace"],
+                          stream=stream) for N in w["sizes"]}
+
+    def step():
+        st = {"launches": 0, "pair_ms": 0.0, "pair_bytes": 0.0, "pair_launches": 0}
+        for N, xyz in cats:
+            plans[N].assign(bisp.DATA, xyz)
+            plans[N].measure()
+            inf = plans[N].info()
+            st["launches"] += inf["kernel_launches"]
+            st["pair_ms"] += inf["ms_pair"]
+            st["pair_bytes"] += inf["pair_bytes"]
+            st["pair_launches"] += inf["pair_launches"]
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tot = {"launches": 0, "pair_ms": 0.0, "pair_bytes": 0.0, "pair_launches": 0}
+    for _ in range(args.steps):
+        st = step()
+        for k in tot:
+            tot[k] += st[k]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    for pl in plans.values():
+        pl.close()
+    nbins = n_bins_output(w) * w["n_real"]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    gbs = tot["pair_bytes"] / (tot["pair_ms"] / 1e3) / 1e9 if tot["pair_ms"] > 0 else None
+    return {
+        "metric": f"B_l1l2L(k1,k2) bins/s, {w['n_real']} realisations at 128^3 and 256^3 (global LOS, B000+B202)",
+        "value": nbins / (ms / 1e3), "unit": "bins/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (FP64 accumulation)", "data": "synthetic",
+        "config": {"workload": args.workload, "realisations": w["n_real"], "meshes": list(w["sizes"]),
+                   "particles": list(w["n_p_range"]), "nbins": len(w["edges"]) - 1, "ells": w["ells"],
+                   "bins_per_step": nbins, "schedule": "two plans, realisations measured one after another",
+                   "l2": "inputs of 12-48 MB per realisation, fields of 8-64 MB (no flush between measures)"},
+        "e2e": None, "gpu_launches": tot["launches"] // args.steps,
+        "roofline": {"bound": "hbm", "kernel": "k_pair_tma (mesh sum of F F G, Eq. bi_estimator_FFTs)",
+                     "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm if gbs else None, "traffic": None,
+                     "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
+                     else "of fallback 6800 GB/s"},
+        "clocks": clk,
+    }
+
+
 def fp64_step(bisp, w, g, r, nbins):
     """One step of the plain FP64 form (cuFFT Z2D fields, one FP64 mesh sum per bin pair and
     3j term) on the same device-resident inputs, timed with CUDA events on its stream."""
@@ -387,6 +469,11 @@ def main():
                     help="fp64: the plain FP64 form of the estimator (comparison line)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if args.impl == "reference" and w["kind"] == "batch":
+        # the oracle's sample: one realisation of the larger mesh
+        w = dict(kind="box", N=max(w["sizes"]), L=w["L"], n_gen=max(w["sizes"]) // 2,
+                 n_p=sum(w["n_p_range"]) // 2, edges=w["edges"], ells=w["ells"], mas=w["mas"],
+                 interlace=w["interlace"], P0=0.0, window=False)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
@@ -407,6 +494,10 @@ def main():
                           "data": "synthetic", "config": config_of(args.workload, w, world), "cpu_baseline": cb,
                           "e2e": {"value": v, "unit": "bins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                           "seconds": time.perf_counter() - t0}))
+        return
+    if w["kind"] == "batch":
+        if rank == 0:
+            print(json.dumps(run_batch(args, w)))
         return
     out = run_gpu(args, w, rank, world)
     if rank == 0:
