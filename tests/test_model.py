@@ -59,6 +59,19 @@ def test_masked_coefficients_printed_in_the_paper():
         assert Mo.masked_coefficient(tuple(v[0:3]), tuple(v[3:6]), tuple(v[6:9])) == pytest.approx(v[9] / v[10], rel=1e-13)
 
 
+def test_masked_coefficients_of_eq_maskzeta2():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "masked_zeta_coefficients_eq_maskzeta2.txt"))
+            if l.strip() and l[0] != "#"]
+    assert len(rows) == 14
+    for r in rows:
+        v = [int(x) for x in r]
+        assert Mo.masked_coefficient(tuple(v[0:3]), tuple(v[3:6]), tuple(v[6:9])) == pytest.approx(v[9] / v[10], rel=1e-13)
+    # terms the printed expressions do not contain (and that are not products of two L = 2 modes)
+    assert Mo.masked_coefficient((2, 0, 2), (1, 1, 0), (1, 1, 0)) == pytest.approx(0.0, abs=1e-14)
+    assert Mo.masked_coefficient((1, 1, 2), (1, 1, 0), (1, 1, 0)) == pytest.approx(0.0, abs=1e-14)
+    assert Mo.masked_coefficient((1, 1, 0), (2, 0, 2), (0, 0, 0)) == pytest.approx(0.0, abs=1e-14)
+
+
 def _grid(nr=24, rmax=150.0):
     r = np.linspace(rmax / nr, rmax, nr)
     w = np.full(nr, rmax / nr)
