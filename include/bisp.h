@@ -215,6 +215,19 @@ bisp_status bisp_zeta_to_bk(int l1, int l2, const double* r, const double* w, in
 bisp_status bisp_bk_to_zeta(int l1, int l2, const double* k, const double* wk, int nk, const double* B,
                             const double* r1, int nr1, const double* r2, int nr2, double* zeta);
 
+/* Tree-level bispectrum multipoles B_{l1 l2 L}(k1, k2) (App. F: the second-order kernels
+ * Z1 = b1 + f mu^2 and Z2 = b1 F2 + b2/2 + f mu^2 G2 + (f mu k / 2)(mu1/k1 Z1(k2) + mu2/k2 Z1(k1)),
+ * B = 2 Z2(k1, k2) Z1(k1) Z1(k2) P(k1) P(k2) + cyc.), projected on the TripoSH basis
+ * (Eq. reduced_ones, Eq. TripoSH_J0) by Gauss-Legendre quadrature in mu1 and mu2 (n_mu nodes)
+ * and 2 n_mu azimuths.  P(k) is a host table (n_tab >= 2 ascending k > 0, P > 0), interpolated in
+ * log-log (a power law exactly) and held at its end values outside the table.  out
+ * [n_mult][nk1][nk2] host FP64.  The paper's linear spectrum comes from CLASS, which is not here;
+ * any table (a power law, for instance) serves.  Errors: BISP_EINVAL for NULL pointers, a bad
+ * table, k <= 0, n_mu < 2 or multipoles outside l <= 8 / the triangle rule. */
+bisp_status bisp_tree_multipoles(const double* k_tab, const double* p_tab, int n_tab, double b1, double b2, double f,
+                                 const int* ells, int n_mult, const double* k1, int nk1, const double* k2, int nk2,
+                                 int n_mu, double* out);
+
 /* Free every resource of the plan (NULL is accepted). */
 bisp_status bisp_plan_destroy(bisp_plan* plan);
 

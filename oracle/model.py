@@ -116,3 +116,78 @@ def bk_to_zeta(l1, l2, k, wk, B, r1, r2):
     J1 = spherical_jn(l1, np.outer(r1, k)) * (wk * k * k / (2 * np.pi ** 2))[None, :]
     J2 = spherical_jn(l2, np.outer(r2, k)) * (wk * k * k / (2 * np.pi ** 2))[None, :]
     return ph * J1 @ B @ J2.T
+
+
+# --------------------------------------------------------------------------------------
+# tree-level bispectrum multipoles (App. F)
+# --------------------------------------------------------------------------------------
+
+
+def power_loglog(k_tab, p_tab):
+    """P(k) by log-log interpolation of a table (a power law is reproduced exactly)."""
+    lk, lp = np.log(np.asarray(k_tab, float)), np.log(np.asarray(p_tab, float))
+    return lambda k: np.exp(np.interp(np.log(k), lk, lp))
+
+
+def tree_bispectrum(P, b1, b2, f, k1v, k2v, n=(0.0, 0.0, 1.0)):
+    """B(k1, k2, k3 = -k1 - k2; n) = 2 Z2(k1, k2) Z1(k1) Z1(k2) P1 P2 + cyc. (App. F) for arrays of
+    wave vectors [..., 3]."""
+    n = np.asarray(n, float)
+    k3v = -(k1v + k2v)
+
+    def Z1(kv):
+        k = np.linalg.norm(kv, axis=-1)
+        mu = (kv @ n) / k
+        return b1 + f * mu * mu
+
+    def Z2(av, bv):
+        a = np.linalg.norm(av, axis=-1)
+        b = np.linalg.norm(bv, axis=-1)
+        mab = np.sum(av * bv, axis=-1) / (a * b)
+        F2 = 5.0 / 7.0 + 0.5 * mab * (a / b + b / a) + 2.0 / 7.0 * mab * mab
+        G2 = 3.0 / 7.0 + 0.5 * mab * (a / b + b / a) + 4.0 / 7.0 * mab * mab
+        kv = av + bv
+        k = np.linalg.norm(kv, axis=-1)
+        mu = np.where(k > 0, (kv @ n) / np.where(k > 0, k, 1.0), 0.0)
+        mua, mub = (av @ n) / a, (bv @ n) / b
+        return (b1 * F2 + 0.5 * b2 + f * mu * mu * G2
+                + 0.5 * f * mu * k * (mua / a * Z1(bv) + mub / b * Z1(av)))
+
+    def term(av, bv):
+        return 2.0 * Z2(av, bv) * Z1(av) * Z1(bv) * P(np.linalg.norm(av, axis=-1)) * P(np.linalg.norm(bv, axis=-1))
+
+    return term(k1v, k2v) + term(k2v, k3v) + term(k3v, k1v)
+
+
+def tree_multipole(P, b1, b2, f, ell, k1, k2, n_mu=24, n_phi=48, n=(0.0, 0.0, 1.0)):
+    """B_{l1 l2 L}(k1, k2) = N H sum_m 3j int d^2k1/4pi int d^2k2/4pi y_l1^{m1*} y_l2^{m2*} y_L^{M*}(n)
+    B(k1, k2; n) (Eq. reduced_ones with the expansion of Eq. TripoSH_J0), over both directions on a
+    Gauss-Legendre x uniform grid for one line of sight n (the integrand is rotation invariant, so
+    any n gives the same multipole)."""
+    from .sph import ylm
+    l1, l2, L = ell
+    mu, wmu = np.polynomial.legendre.leggauss(n_mu)
+    ph = 2 * np.pi * (np.arange(n_phi) + 0.5) / n_phi
+    MU1, PH1, MU2, PH2 = np.meshgrid(mu, ph, mu, ph, indexing="ij")
+    W = (wmu[:, None, None, None] * wmu[None, None, :, None]) / (4.0 * n_phi * n_phi)
+    s1, s2 = np.sqrt(1 - MU1 ** 2), np.sqrt(1 - MU2 ** 2)
+    u1 = np.stack([s1 * np.cos(PH1), s1 * np.sin(PH1), MU1], axis=-1)
+    u2 = np.stack([s2 * np.cos(PH2), s2 * np.sin(PH2), MU2], axis=-1)
+    n = np.asarray(n, float) / np.linalg.norm(n)
+    B = tree_bispectrum(P, b1, b2, f, k1 * u1, k2 * u2, n)
+    tot = 0.0 + 0.0j
+    for m1 in range(-l1, l1 + 1):
+        for m2 in range(-l2, l2 + 1):
+            M = -m1 - m2
+            if abs(M) > L:
+                continue
+            c = wigner3j(l1, l2, L, m1, m2, M)
+            if c == 0.0:
+                continue
+            yM = np.conj(ylm(L, M, n[0], n[1], n[2]))
+            if yM == 0:
+                continue
+            y1 = np.conj(ylm(l1, m1, u1[..., 0], u1[..., 1], u1[..., 2]))
+            y2 = np.conj(ylm(l2, m2, u2[..., 0], u2[..., 1], u2[..., 2]))
+            tot += c * yM * np.sum(W * y1 * y2 * B)
+    return n_lll(l1, l2, L) * h_lll(l1, l2, L) * tot.real

@@ -74,10 +74,12 @@ def _load():
     lib.bisp_masked_zeta.argtypes = [ip, C.c_int, dp, ip, C.c_int, dp, ip, C.c_int, dp, dp, C.c_int, C.c_int, dp, dp]
     lib.bisp_zeta_to_bk.argtypes = [C.c_int, C.c_int, dp, dp, C.c_int, dp, dp, C.c_int, dp, C.c_int, dp]
     lib.bisp_bk_to_zeta.argtypes = [C.c_int, C.c_int, dp, dp, C.c_int, dp, dp, C.c_int, dp, C.c_int, dp]
+    lib.bisp_tree_multipoles.argtypes = [dp, dp, C.c_int, C.c_double, C.c_double, C.c_double, ip, C.c_int, dp,
+                                         C.c_int, dp, C.c_int, C.c_int, dp]
     for f in ("bisp_plan_create", "bisp_assign", "bisp_measure", "bisp_measure_batch", "bisp_plan_destroy",
               "bisp_plan_query", "bisp_cell_order", "bisp_debug_fetch", "bisp_cell_order_noalloc",
               "bisp_covariance", "bisp_covariance_factors", "bisp_chi2", "bisp_wigner9j", "bisp_masked_zeta",
-              "bisp_zeta_to_bk", "bisp_bk_to_zeta"):
+              "bisp_zeta_to_bk", "bisp_bk_to_zeta", "bisp_tree_multipoles"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -341,3 +343,13 @@ def bk_to_zeta(l1, l2, k, wk, B, r1, r2):
     _check(lib().bisp_bk_to_zeta(int(l1), int(l2), _dp(k), _dp(wk), len(k), _dp(B), _dp(r1), len(r1), _dp(r2),
                                  len(r2), _dp(z)))
     return z
+
+
+def tree_multipoles(k_tab, p_tab, b1, b2, f, ells, k1, k2, n_mu=24):
+    """Tree-level bispectrum multipoles (App. F) [n_mult, nk1, nk2] for a tabulated P(k)."""
+    kt, pt, k1, k2 = (np.ascontiguousarray(a, dtype=np.float64) for a in (k_tab, p_tab, k1, k2))
+    e = np.ascontiguousarray(np.array(list(ells), dtype=np.int32).reshape(-1))
+    out = np.zeros((len(e) // 3, len(k1), len(k2)))
+    _check(lib().bisp_tree_multipoles(_dp(kt), _dp(pt), len(kt), float(b1), float(b2), float(f), _ip(e), len(e) // 3,
+                                      _dp(k1), len(k1), _dp(k2), len(k2), int(n_mu), _dp(out)))
+    return out

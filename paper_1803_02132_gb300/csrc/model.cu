@@ -96,6 +96,79 @@ double sph_jl(int l, double x) {
   return j;
 }
 
+// 3j symbol (j1 j2 j3; m1 m2 m3) by Racah's formula
+double wigner3j_gen(int j1, int j2, int j3, int m1, int m2, int m3) {
+  if (m1 + m2 + m3 != 0 || std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(m3) > j3 || !triangle(j1, j2, j3))
+    return 0.0;
+  const double pre = log_delta(j1, j2, j3) + 0.5 * (lfac(j1 + m1) + lfac(j1 - m1) + lfac(j2 + m2) + lfac(j2 - m2) +
+                                                   lfac(j3 + m3) + lfac(j3 - m3));
+  const int t0 = std::max(std::max(0, j2 - j3 - m1), j1 - j3 + m2);
+  const int t1 = std::min(std::min(j1 + j2 - j3, j1 - m1), j2 + m2);
+  double s = 0.0;
+  for (int t = t0; t <= t1; ++t) {
+    const double lg = -(lfac(t) + lfac(j3 - j2 + t + m1) + lfac(j3 - j1 + t - m2) + lfac(j1 + j2 - j3 - t) +
+                        lfac(j1 - t - m1) + lfac(j2 - t + m2));
+    s += ((t & 1) ? -1.0 : 1.0) * std::exp(lg + pre);
+  }
+  return (((j1 - j2 - m3) & 1) ? -1.0 : 1.0) * s;
+}
+
+// y_l^m(u) = sqrt(4 pi / (2l+1)) Y_l^m(u) of a unit vector u, any m, Condon-Shortley phase
+void ylm_unit(int l, int m, double x, double y, double z, double* re, double* im) {
+  const int am = std::abs(m);
+  double pmm = 1.0;  // P_m^m without the (1 - z^2)^{m/2} factor: (-1)^m (2m-1)!!
+  for (int k = 1; k <= am; ++k) pmm *= -(2.0 * k - 1.0);
+  double p = pmm;
+  if (l > am) {
+    double p2 = pmm, p1 = (2.0 * am + 1.0) * z * pmm;
+    p = p1;
+    for (int ll = am + 2; ll <= l; ++ll) {
+      p = ((2.0 * ll - 1.0) * z * p1 - (ll + am - 1.0) * p2) / (ll - am);
+      p2 = p1;
+      p1 = p;
+    }
+  }
+  double er = 1.0, ei = 0.0;  // (x + i y)^m
+  for (int k = 0; k < am; ++k) {
+    const double t = er * x - ei * y;
+    ei = er * y + ei * x;
+    er = t;
+  }
+  const double a = std::exp(0.5 * (lfac(l - am) - lfac(l + am))) * p;
+  double r = a * er, i = a * ei;
+  if (m < 0) {  // y_l^{-m} = (-1)^m conj(y_l^m)
+    const double sg = (am & 1) ? -1.0 : 1.0;
+    r *= sg;
+    i *= -sg;
+  }
+  *re = r;
+  *im = i;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n from the Chebyshev guesses)
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double pn = n == 1 ? z : p1, pm = n == 1 ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+      const double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
 bool valid_ell(const int* e) {
   for (int i = 0; i < 3; ++i)
     if (e[i] < 0 || e[i] > LMAX_MODEL) return false;
@@ -235,6 +308,100 @@ bisp_status bisp_bk_to_zeta(int l1, int l2, const double* k, const double* wk, i
       for (int j = 0; j < nk; ++j) s += g[j] * T[(size_t)a * nk + j];
       zeta[(size_t)a * nr2 + b] = ph * s;
     }
+  }
+  return BISP_OK;
+}
+
+bisp_status bisp_tree_multipoles(const double* k_tab, const double* p_tab, int n_tab, double b1, double b2, double f,
+                                 const int* ells, int n_mult, const double* k1, int nk1, const double* k2, int nk2,
+                                 int n_mu, double* out) {
+  if (!k_tab || !p_tab || !ells || !k1 || !k2 || !out || n_tab < 2 || n_mult < 1 || nk1 < 1 || nk2 < 1 || n_mu < 2)
+    return bad(BISP_EINVAL, "bisp_tree_multipoles: NULL argument, fewer than 2 table points or empty grids");
+  for (int i = 0; i < n_tab; ++i)
+    if (!(k_tab[i] > 0.0) || !(p_tab[i] > 0.0) || (i && !(k_tab[i] > k_tab[i - 1])))
+      return bad(BISP_EINVAL, "bisp_tree_multipoles: the P(k) table needs ascending k > 0 and P > 0");
+  for (int i = 0; i < n_mult; ++i)
+    if (!valid_ell(ells + 3 * i)) return bad(BISP_EINVAL, "bisp_tree_multipoles: invalid multipole");
+  for (int i = 0; i < nk1; ++i)
+    if (!(k1[i] > 0.0)) return bad(BISP_EINVAL, "bisp_tree_multipoles: k1 must be positive");
+  for (int i = 0; i < nk2; ++i)
+    if (!(k2[i] > 0.0)) return bad(BISP_EINVAL, "bisp_tree_multipoles: k2 must be positive");
+  // P(k): log-log interpolation, the end values outside the table
+  std::vector<double> lk(n_tab), lp(n_tab);
+  for (int i = 0; i < n_tab; ++i) {
+    lk[i] = std::log(k_tab[i]);
+    lp[i] = std::log(p_tab[i]);
+  }
+  auto P = [&](double k) {
+    const double x = std::log(k);
+    if (x <= lk[0]) return p_tab[0];
+    if (x >= lk[n_tab - 1]) return p_tab[n_tab - 1];
+    const int j = (int)(std::upper_bound(lk.begin(), lk.end(), x) - lk.begin()) - 1;
+    const double t = (x - lk[j]) / (lk[j + 1] - lk[j]);
+    return std::exp(lp[j] + t * (lp[j + 1] - lp[j]));
+  };
+  // second-order kernels (App. F) with the line of sight n = z
+  auto Z1 = [&](const double* v) {
+    const double k = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), mu = v[2] / k;
+    return b1 + f * mu * mu;
+  };
+  auto Z2 = [&](const double* a, const double* b) {
+    const double ka = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double kb = std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    const double mab = (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) / (ka * kb);
+    const double F2 = 5.0 / 7.0 + 0.5 * mab * (ka / kb + kb / ka) + 2.0 / 7.0 * mab * mab;
+    const double G2 = 3.0 / 7.0 + 0.5 * mab * (ka / kb + kb / ka) + 4.0 / 7.0 * mab * mab;
+    const double s[3] = {a[0] + b[0], a[1] + b[1], a[2] + b[2]};
+    const double k = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    const double muk = s[2];  // mu k = (a + b) . n
+    const double mu2 = k > 0.0 ? (s[2] / k) * (s[2] / k) : 0.0;
+    return b1 * F2 + 0.5 * b2 + f * mu2 * G2 + 0.5 * f * muk * (a[2] / (ka * ka) * Z1(b) + b[2] / (kb * kb) * Z1(a));
+  };
+  auto term = [&](const double* a, const double* b) {
+    const double ka = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double kb = std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    return 2.0 * Z2(a, b) * Z1(a) * Z1(b) * P(ka) * P(kb);
+  };
+  std::vector<double> mu, wmu;
+  gauss_legendre(n_mu, mu, wmu);
+  const int n_phi = 2 * n_mu;
+  // Phi_l(k1_hat, k2_hat) = sum_m1 3j(l1 l2 L; m1, -m1, 0) y_l1^{m1*}(k1_hat) y_l2^{-m1*}(k2_hat), y_L^0(z) = 1:
+  // the TripoSH weight with n = z (Eq. reduced_ones with Eq. Slll; rotation invariant)
+  for (int q = 0; q < n_mult * nk1 * nk2; ++q) out[q] = 0.0;
+  for (int i1 = 0; i1 < n_mu; ++i1)
+    for (int i2 = 0; i2 < n_mu; ++i2)
+      for (int jp = 0; jp < n_phi; ++jp) {
+        const double ph = 2.0 * M_PI * (jp + 0.5) / n_phi;
+        const double s1 = std::sqrt(1.0 - mu[i1] * mu[i1]), s2 = std::sqrt(1.0 - mu[i2] * mu[i2]);
+        const double u1[3] = {s1 * std::cos(ph), s1 * std::sin(ph), mu[i1]}, u2[3] = {s2, 0.0, mu[i2]};
+        const double wq = wmu[i1] * wmu[i2] / (4.0 * n_phi);
+        std::vector<double> phi(n_mult, 0.0);
+        for (int e = 0; e < n_mult; ++e) {
+          const int l1 = ells[3 * e], l2 = ells[3 * e + 1], L = ells[3 * e + 2];
+          double acc = 0.0;
+          for (int m1 = -std::min(l1, l2); m1 <= std::min(l1, l2); ++m1) {
+            const double c = wigner3j_gen(l1, l2, L, m1, -m1, 0);
+            if (c == 0.0) continue;
+            double r1, i1, r2, i2;
+            ylm_unit(l1, m1, u1[0], u1[1], u1[2], &r1, &i1);
+            ylm_unit(l2, -m1, u2[0], u2[1], u2[2], &r2, &i2);
+            acc += c * (r1 * r2 - i1 * i2);  // Re(conj(y1) conj(y2)) = Re(y1 y2)
+          }
+          phi[e] = acc;
+        }
+        for (int a = 0; a < nk1; ++a)
+          for (int b = 0; b < nk2; ++b) {
+            const double v1[3] = {k1[a] * u1[0], k1[a] * u1[1], k1[a] * u1[2]};
+            const double v2[3] = {k2[b] * u2[0], k2[b] * u2[1], k2[b] * u2[2]};
+            const double v3[3] = {-v1[0] - v2[0], -v1[1] - v2[1], -v1[2] - v2[2]};
+            const double B = term(v1, v2) + term(v2, v3) + term(v3, v1);
+            for (int e = 0; e < n_mult; ++e) out[((size_t)e * nk1 + a) * nk2 + b] += wq * phi[e] * B;
+          }
+      }
+  for (int e = 0; e < n_mult; ++e) {
+    const int l1 = ells[3 * e], l2 = ells[3 * e + 1], L = ells[3 * e + 2];
+    const double pre = nlll(l1, l2, L) * h3j(l1, l2, L);
+    for (int q = 0; q < nk1 * nk2; ++q) out[(size_t)e * nk1 * nk2 + q] *= pre;
   }
   return BISP_OK;
 }

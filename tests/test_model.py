@@ -165,3 +165,51 @@ def test_library_errors():
     assert e.value.status == bisp.BISP_EUNSUPPORTED
     with pytest.raises(bisp.BispError):
         bisp.wigner9j([1, 1, 1, 1, 1, 1, 1, 1, 99])
+
+
+def _plaw():
+    kt = np.array([1e-4, 10.0])
+    return kt, 2e4 * (kt / 0.05) ** -1.5
+
+
+def test_tree_real_space_is_isotropic_and_follows_the_legendre_route():
+    # f = 0: B depends on the triangle only, so every L > 0 multipole vanishes and
+    # B_{l l 0}(k1, k2) = (2l+1) int dmu/2 L_l(mu) B(k1, k2, mu)   (mu = k1_hat . k2_hat)
+    from oracle.sph import legendre
+    kt, pt = _plaw()
+    P = Mo.power_loglog(kt, pt)
+    k1, k2 = 0.05, 0.08
+    mu, w = np.polynomial.legendre.leggauss(64)
+    v1 = np.stack([np.zeros_like(mu), np.zeros_like(mu), np.full_like(mu, k1)], axis=-1)
+    v2 = k2 * np.stack([np.sqrt(1 - mu * mu), np.zeros_like(mu), mu], axis=-1)
+    B = Mo.tree_bispectrum(P, 1.7, 0.9, 0.0, v1, v2)
+    for l in (0, 1, 2):
+        ref = (2 * l + 1) * np.sum(w / 2 * legendre(l, mu) * B)
+        assert Mo.tree_multipole(P, 1.7, 0.9, 0.0, (l, l, 0), k1, k2) == pytest.approx(ref, rel=1e-8)
+    for ell in [(2, 0, 2), (1, 1, 2), (2, 2, 2)]:
+        assert abs(Mo.tree_multipole(P, 1.7, 0.9, 0.0, ell, k1, k2)) < 1e-8 * abs(ref)
+
+
+def test_tree_multipoles_do_not_depend_on_the_line_of_sight_direction():
+    kt, pt = _plaw()
+    P = Mo.power_loglog(kt, pt)
+    for ell in [(0, 0, 0), (2, 0, 2), (1, 1, 2)]:
+        a = Mo.tree_multipole(P, 2.0, 1.0, 0.7, ell, 0.05, 0.08)
+        b = Mo.tree_multipole(P, 2.0, 1.0, 0.7, ell, 0.05, 0.08, n=(1.0, 0.3, 0.2))
+        assert a == pytest.approx(b, rel=1e-7)
+    # the redshift-space boost makes the quadrupole positive
+    assert Mo.tree_multipole(P, 2.0, 1.0, 0.7, (2, 0, 2), 0.05, 0.08) > 0
+
+
+def test_library_tree_multipoles_match_oracle():
+    kt, pt = _plaw()
+    P = Mo.power_loglog(kt, pt)
+    ells = [(0, 0, 0), (1, 1, 0), (2, 0, 2), (1, 1, 2)]
+    k1, k2 = np.array([0.04, 0.09]), np.array([0.06])
+    lib = bisp.tree_multipoles(kt, pt, 2.0, 1.0, 0.7, ells, k1, k2)
+    for i, e in enumerate(ells):
+        for a, kk1 in enumerate(k1):
+            ref = Mo.tree_multipole(P, 2.0, 1.0, 0.7, e, kk1, k2[0])
+            assert lib[i, a, 0] == pytest.approx(ref, rel=1e-7)
+    with pytest.raises(bisp.BispError):
+        bisp.tree_multipoles(kt[::-1], pt, 1.0, 0.0, 0.0, ells, k1, k2)
