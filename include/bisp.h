@@ -47,7 +47,7 @@ typedef enum {
   BISP_ECUDA = 3,       /* a CUDA runtime call failed */
   BISP_ESTATE = 4,      /* call out of order (e.g. measure before the data catalogue) */
   BISP_ETIMEOUT = 5,    /* a bounded device wait expired */
-  BISP_EUNSUPPORTED = 6 /* valid request outside what this build implements */
+  BISP_EUNSUPPORTED = 6 /* valid request outside what the library implements */
 } bisp_status;
 
 /* Line of sight: global (the z axis of the box, Sec. 4.4) or local (the direction from
