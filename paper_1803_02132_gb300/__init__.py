@@ -148,8 +148,9 @@ class Plan:
         p.fkp_P0 = float(fkp_P0)
         p.max_device_bytes = int(max_device_bytes)
         p.want_window = 1 if want_window else 0
-        p.precision = PRECISION[precision]
-        p.estimator = ESTIMATOR[estimator]
+        # names map to the enums; integers go to the library as given (it validates them)
+        p.precision = PRECISION[precision] if precision in PRECISION else int(precision)
+        p.estimator = ESTIMATOR[estimator] if estimator in ESTIMATOR else int(estimator)
         p.diagonal_only = 1 if diagonal_only else 0
         self.nbins = p.nbins
         self.want_window = bool(want_window)

@@ -49,3 +49,22 @@ def test_oracle_is_not_imported_by_the_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(root, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
+
+
+def test_new_plan_options_are_validated_without_the_gpu():
+    with pytest.raises(bisp.BispError) as e:
+        bisp.Plan(nmesh=64, box_len=1000.0, k_edges=[0.01, 0.02], ells=[(0, 0, 0)], estimator=5)
+    assert e.value.status == bisp.BISP_EINVAL and "estimator" in str(e.value)
+    with pytest.raises(bisp.BispError) as e:  # the FP64 form covers the bispectrum only
+        bisp.Plan(nmesh=64, box_len=1000.0, k_edges=[10.0, 20.0], ells=[(0, 0, 0)], estimator="threept",
+                  precision="fp64")
+    assert e.value.status == bisp.BISP_EUNSUPPORTED
+    with pytest.raises(bisp.BispError) as e:  # r edges may start at 0 but not below
+        bisp.Plan(nmesh=64, box_len=1000.0, k_edges=[-1.0, 20.0], ells=[(0, 0, 0)], estimator="threept")
+    assert e.value.status == bisp.BISP_EINVAL and "r edges" in str(e.value)
+    with pytest.raises(bisp.BispError) as e:  # k edges must be positive
+        bisp.Plan(nmesh=64, box_len=1000.0, k_edges=[0.0, 0.02], ells=[(0, 0, 0)])
+    assert e.value.status == bisp.BISP_EINVAL
+    with pytest.raises(bisp.BispError) as e:
+        bisp.Plan(nmesh=64, box_len=1000.0, k_edges=[0.01, 0.02], ells=[(0, 0, 0)], precision=7)
+    assert e.value.status == bisp.BISP_EINVAL
