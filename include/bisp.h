@@ -14,7 +14,13 @@
  *   - the four shot-noise terms (Eq. shotnoise, Eq. ShotNoise), the normalisation I
  *     (Eq. normalization; periodic box I = Np^3/V^2, Sec. 4.4);
  *   - the window bispectrum: the same estimator on the random catalogue alone (the
- *     bispectrum-space counterpart of Eq. Q).
+ *     bispectrum-space counterpart of Eq. Q);
+ *   - the three-point-function multipoles and the three-point window multipoles Q
+ *     (Sec. 4.3, Eq. reduced_xi_estimator; Sec. 6.1, Eq. Q), and a diagonal-only mode;
+ *   - the plain FP64 form of the bispectrum estimator, as a speed and accuracy baseline.
+ * On the host, for batches of measurements and the window-convolved model: the covariance
+ * statistics of Sec. 5.5 and App. E, and the 9j coupling, integral constraint, Hankel
+ * transforms and tree-level multipoles of Sec. 6.2 and App. F.
  *
  * Conventions shared by every call:
  *   - Every call returns a bisp_status.  Nothing throws across the ABI.  On failure
@@ -99,7 +105,7 @@ typedef struct {
   int precision;           /* bisp_precision (0: BISP_FP32) */
   int estimator;           /* bisp_estimator (0: BISP_BISPECTRUM) */
   int diagonal_only;       /* 1: only the k1 = k2 (r1 = r2) outputs, the diagonal the paper's
-                              signal-to-noise study rests on (Sec. 4.4, Sec. 5.4); every other
+                              signal-to-noise study rests on (Sec. 4.4, Sec. 5.6); every other
                               output is NaN.  When the shell fields of all bins do not fit,
                               each block of bins is then measured alone, with no block pairs. */
 } bisp_params;
@@ -151,10 +157,10 @@ typedef struct {
  * (the kernels' job tables live in module-wide constant memory, so plans never run
  * concurrently); the call returns when all are done.  Errors: BISP_EINVAL for nplans < 0 or NULL
  * arrays; otherwise the first failing plan's status, with its index in the message (later plans
- * are not measured).  No counterpart in the paper beyond its use of many mocks (Sec. 5.4). */
+ * are not measured).  No counterpart in the paper beyond its use of many mocks (Sec. 5.5). */
 bisp_status bisp_measure_batch(bisp_plan* const* plans, const bisp_outputs* outs, int nplans);
 
-/* Covariance of a batch of measurements (Sec. 5.3, Eq. Covariance): X holds n_mock data
+/* Covariance of a batch of measurements (Sec. 5.5, Eq. Covariance): X holds n_mock data
  * vectors of n_bin values, [n_mock][n_bin] host FP64 (for example flattened bisp_measure
  * outputs of independent realisations).  Outputs (host, caller-owned, NULL to skip): mean
  * [n_bin]; cov [n_bin][n_bin] = 1/(n_mock - 1) sum_n (X_n - mean)^T (X_n - mean); corr

@@ -1,4 +1,4 @@
-"""FP64 oracle of the covariance statistics of a batch of measurements (Sec. 5.3,
+"""FP64 oracle of the covariance statistics of a batch of measurements (Sec. 5.5,
 Eq. Covariance; App. E, the Hartlap and Percival factors).
 
 TEST INFRASTRUCTURE ONLY.  Plain loops over the definitions; shares no code with the

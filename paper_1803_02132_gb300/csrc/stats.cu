@@ -1,4 +1,4 @@
-// Covariance statistics of a batch of measurements (Sec. 5.3, Eq. Covariance; App. E):
+// Covariance statistics of a batch of measurements (Sec. 5.5, Eq. Covariance; App. E):
 // host FP64 code on the small output vectors of many realisations (mocks), fixed summation
 // order.  The C ABI is declared in include/bisp.h.
 #include <cmath>

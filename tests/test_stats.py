@@ -1,4 +1,4 @@
-"""Covariance statistics of batches of measurements (Sec. 5.3, Eq. Covariance; App. E): the
+"""Covariance statistics of batches of measurements (Sec. 5.5, Eq. Covariance; App. E): the
 oracle against library routines and statistical facts, and the host functions of the C ABI
 against the oracle.  No GPU: these functions do no device work."""
 import numpy as np
