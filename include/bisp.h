@@ -274,15 +274,19 @@ bisp_status bisp_cell_order(int nmesh, double box_len, int mas, const float* xyz
 
 /* bisp_cell_order without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory during the call -
- * code running under a framework that forbids cudaMalloc/cudaFree inside a step or while a
- * CUDA graph is being recorded, allocators that must not be re-entered, or processes
- * without spare device memory.  Same arguments, outputs and errors as bisp_cell_order.
+ * code running under a framework or memory pool that forbids cudaMalloc/cudaFree inside a
+ * step, allocators that must not be re-entered, or processes without spare device memory.
+ * Same arguments, outputs and errors as bisp_cell_order.
  *   - Scratch lives in one statically sized device array in the library (about
  *     32 bytes per particle of BISP_NOALLOC_MAX_PARTICLES plus 4 MiB, i.e. 36 MiB); every
  *     GPU that loads the library holds it until the process exits.
  *   - n > BISP_NOALLOC_MAX_PARTICLES returns BISP_EINVAL and names the limit.
  *   - The first call on a device resolves the array's device address with that device
- *     current; make that first call before any stream capture.
+ *     current and keeps it for the life of the process; make that first call before any
+ *     stream capture on that device.  After cudaDeviceReset the kept address is stale: do
+ *     not call this entry point again in that process.
+ *   - The call copies a small table from host memory, reads back an error counter and
+ *     synchronises `stream` before it returns.
  *   - All calls share the one array: calls whose GPU work overlaps (on different streams or
  *     host threads) race and corrupt each other's results.  Serialise them.
  *   - The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine). */

@@ -441,18 +441,27 @@ static void deposit_p(const DepositArgs& a, cudaStream_t s) {
 #undef BISP_DEP
 }
 
-void launch_deposit(const DepositArgs& a, cudaStream_t s, int* launches) {
-  if (a.interlace) {
-    if (a.mas == 1) deposit_p<1, 1>(a, s);
-    else if (a.mas == 2) deposit_p<2, 1>(a, s);
-    else deposit_p<3, 1>(a, s);
-  } else {
-    if (a.mas == 1) deposit_p<1, 0>(a, s);
-    else if (a.mas == 2) deposit_p<2, 0>(a, s);
-    else deposit_p<3, 0>(a, s);
+void launch_deposit(const DepositArgs& a0, cudaStream_t s, int* launches) {
+  // at most 16 channels per launch (register accumulators); more channels go in groups
+  const int64_t Ng = (int64_t)a0.N * a0.N * a0.N;
+  for (int c0 = 0; c0 < a0.nchan; c0 += 16) {
+    DepositArgs a = a0;
+    a.nchan = a0.nchan - c0 < 16 ? a0.nchan - c0 : 16;
+    a.vals = a0.vals + (size_t)c0 * a0.n;
+    a.mesh0 = a0.mesh0 + (size_t)c0 * Ng;
+    a.mesh1 = a0.mesh1 ? a0.mesh1 + (size_t)c0 * Ng : nullptr;
+    if (a.interlace) {
+      if (a.mas == 1) deposit_p<1, 1>(a, s);
+      else if (a.mas == 2) deposit_p<2, 1>(a, s);
+      else deposit_p<3, 1>(a, s);
+    } else {
+      if (a.mas == 1) deposit_p<1, 0>(a, s);
+      else if (a.mas == 2) deposit_p<2, 0>(a, s);
+      else deposit_p<3, 0>(a, s);
+    }
+    BISP_CHECK_LAUNCH();
+    if (launches) ++*launches;
   }
-  BISP_CHECK_LAUNCH();
-  if (launches) ++*launches;
 }
 
 // =====================================================================================

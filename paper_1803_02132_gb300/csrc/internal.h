@@ -205,6 +205,8 @@ struct PairJob {
 void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scratch_bytes,
                  cudaStream_t s, int* launches, int* kernel = nullptr);
 size_t pair_scratch_bytes(const PairJob& job);
+// true when one launch of some contraction kernel covers the job (terms, tables, shared memory)
+bool pair_fits(const PairJob& job);
 // true when the pair kernel in use prefers one launch per G set (at most 8 terms a launch)
 bool pair_split_gsets();
 

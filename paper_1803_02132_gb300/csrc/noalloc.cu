@@ -5,6 +5,7 @@
 // size, so the call itself allocates nothing.
 #include <cuda_runtime.h>
 
+#include <exception>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -116,5 +117,11 @@ extern "C" bisp_status bisp_cell_order_noalloc(int nmesh, double box_len, int ma
   } catch (const Error& e) {
     set_last_error(e.msg);
     return (bisp_status)e.status;
+  } catch (const std::exception& e) {  // nothing may leave the C ABI
+    set_last_error(std::string("bisp_cell_order_noalloc: ") + e.what());
+    return BISP_ECUDA;
+  } catch (...) {
+    set_last_error("bisp_cell_order_noalloc: unexpected exception");
+    return BISP_ECUDA;
   }
 }

@@ -1190,6 +1190,21 @@ static int pair_blocks() {
   return nsm;
 }
 
+bool pair_fits(const PairJob& job) {
+  try {
+    const PairJob j = classify(job);
+    TmaLayout L;
+    int ksplit = 1, warps = 1;
+    if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) return true;
+    const PairLaunch c = pair_launch_cfg(j);
+    if (c.smem > 227 * 1024) return false;
+    // instantiated kernels: up to 1024 threads for TM x TN <= 18, 512 above
+    return c.warps * 32 <= (c.TM * c.TN > 18 ? 512 : 1024);
+  } catch (const Error&) {
+    return false;
+  }
+}
+
 size_t pair_scratch_bytes(const PairJob& job) {
   const PairJob j = classify(job);
   if (pair_use_tc(j) && pair_use_umma()) {

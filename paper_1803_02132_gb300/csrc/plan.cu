@@ -825,7 +825,9 @@ struct PassState {
   std::map<std::tuple<int, int, int, int>, std::vector<cplx>> Z;
 };
 
-// pair reduction over the first nbu bins held in the field pool
+// pair reduction over the first nbu bins held in the field pool.  A job whose terms do not fit
+// one contraction launch is split: per G set first, then into halves of the multipole list;
+// the outputs keep the layout [gset][mult][b1][b2] of a single launch.
 void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstride, const float* gbase, int nbu,
               std::vector<double>& out, int* launches) {
   // build a pair job with nout = mults.size() * gsets outputs
@@ -838,12 +840,16 @@ void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstrid
   J.ng = gsets * gstride;
   J.nout = (int)mults.size() * gsets;
   int t = 0, r = 0;
-  for (int gs = 0; gs < gsets; ++gs)
-    for (size_t i = 0; i < mults.size(); ++i) {
+  bool tables_ok = true;
+  for (int gs = 0; gs < gsets && tables_ok; ++gs)
+    for (size_t i = 0; i < mults.size() && tables_ok; ++i) {
       const int o = gs * (int)mults.size() + (int)i;
       J.out_term_off[o] = t;
       for (auto& term : P->terms[mults[i]]) {
-        if (t >= 64 || r + (int)(term.x.size() + term.y.size()) > 512) fail(BISP_EUNSUPPORTED, "too many pair terms");
+        if (t >= 64 || r + (int)(term.x.size() + term.y.size()) > 512) {
+          tables_ok = false;
+          break;
+        }
         J.term[t].xoff = r;
         J.term[t].xcnt = (int)term.x.size();
         for (auto e : term.x) {
@@ -862,6 +868,26 @@ void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstrid
   J.out_term_off[J.nout] = t;
   J.nterm = t;
   J.nrec = r;
+  if (!tables_ok || !pair_fits(J)) {
+    std::vector<double> part;
+    out.clear();
+    if (gsets > 1) {
+      for (int gs = 0; gs < gsets; ++gs) {
+        run_pair(P, mults, 1, gstride, gbase + (size_t)gs * gstride * P->Ng, nbu, part, launches);
+        out.insert(out.end(), part.begin(), part.end());
+      }
+      return;
+    }
+    if (mults.size() > 1) {
+      const size_t h = mults.size() / 2;
+      run_pair(P, std::vector<int>(mults.begin(), mults.begin() + h), 1, gstride, gbase, nbu, part, launches);
+      out.insert(out.end(), part.begin(), part.end());
+      run_pair(P, std::vector<int>(mults.begin() + h, mults.end()), 1, gstride, gbase, nbu, part, launches);
+      out.insert(out.end(), part.begin(), part.end());
+      return;
+    }
+    fail(BISP_EUNSUPPORTED, "the contraction terms of one multipole do not fit one launch");
+  }
   const size_t sb = pair_scratch_bytes(J);
   admit(P, sb > P->pairscr.n ? sb - P->pairscr.n : 0);
   P->pairscr.ensure(sb, &P->bytes);

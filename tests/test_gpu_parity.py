@@ -410,3 +410,68 @@ def test_errors_are_reported():
         with pytest.raises(bisp.BispError) as e:  # local LOS needs randoms
             plan.measure()
         assert e.value.status == bisp.BISP_ESTATE
+
+
+HIGH_ELLS = [(4, 0, 4), (3, 1, 2), (2, 2, 4), (4, 4, 0)]
+
+
+@pytest.mark.parametrize("los", ["global", "local"])
+def test_estimator_parity_high_multipoles(los, monkeypatch):
+    """Multipoles with l = 3 and 4, the largest the header admits (Table 1's selection rules):
+    B404, B312, B224, B440; the local line of sight needs the L = 4 channels (15 delta n and 15 N
+    meshes, deposited in groups) and contraction jobs split over several launches."""
+    monkeypatch.delenv("BISP_BLOCK_BINS", raising=False)
+    monkeypatch.delenv("BISP_PAIR_FP32", raising=False)
+    c = CASES["box_tsc_ilv" if los == "global" else "survey_local"]
+    N, L = c["N"], c["L"]
+    edges = 2 * np.pi / L * np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5, 11.0, 15.5])
+    if los == "global":
+        gal = {"xyz": synthcat.periodic_catalog(N, L, c["np_"], seed=100 + N)}
+        ran = None
+        p = E.Params(N=N, L=L, edges=edges, ells=HIGH_ELLS, los="global", mas=c["mas"], interlace=c["interlace"])
+    else:
+        gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+        p = E.Params(N=N, L=L, edges=edges, ells=HIGH_ELLS, los="local", observer=obs, mas=c["mas"],
+                     interlace=c["interlace"], P0=1e4, window=True)
+    ref = E.measure(p, gal, ran)
+    with _plan(p) as plan:
+        _assign(plan, 0, gal)
+        if ran is not None:
+            _assign(plan, 1, ran)
+        out = plan.measure()
+    assert_close(out["B"], ref["B"], what="B")
+    assert_close(out["shot"], ref["shot"], what="shot")
+    if ran is not None:
+        assert_close(out["window"], ref["window"], what="window")
+        assert_close(out["window_shot"], ref["window_shot"], what="window shot")
+
+
+@pytest.mark.parametrize("case", ["survey_local", "box_tsc_ilv"])
+def test_fp32_fma_contraction_kernel(case, monkeypatch):
+    """The FP32-FMA contraction (k_pair, forced with BISP_PAIR_FP32=1; otherwise used for jobs
+    outside the tensor-core layout) against the oracle."""
+    monkeypatch.setenv("BISP_PAIR_FP32", "1")
+    monkeypatch.delenv("BISP_BLOCK_BINS", raising=False)
+    c = CASES[case]
+    N, L = c["N"], c["L"]
+    edges = 2 * np.pi / L * np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5, 11.0, 15.5])
+    if c["los"] == "global":
+        gal = {"xyz": synthcat.periodic_catalog(N, L, c["np_"], seed=100 + N)}
+        ran = None
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="global", mas=c["mas"], interlace=c["interlace"])
+    else:
+        gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+        p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="local", observer=obs, mas=c["mas"],
+                     interlace=c["interlace"], P0=1e4, window=True)
+    ref = E.measure(p, gal, ran)
+    with _plan(p) as plan:
+        _assign(plan, 0, gal)
+        if ran is not None:
+            _assign(plan, 1, ran)
+        out = plan.measure()
+        assert plan.info()["pair_kernel"] == 0
+    assert_close(out["B"], ref["B"], what="B")
+    assert_close(out["shot"], ref["shot"], what="shot")
+    if ran is not None:
+        assert_close(out["window"], ref["window"], what="window")
+        assert_close(out["window_shot"], ref["window_shot"], what="window shot")
