@@ -29,7 +29,8 @@
  *   - Positions are in box coordinates [0, box_len)^3, float32, interleaved x,y,z.
  *   - A plan owns all its device memory (meshes, spectra, fields) and a CUDA stream;
  *     the caller owns every pointer it passes, and the library only borrows it for the
- *     duration of the call.  Calls on one plan must not overlap (one thread at a time).
+ *     duration of the call.  Calls on one plan must not overlap (one thread at a time);
+ *     different plans may be driven from different host threads at the same time.
  *   - Device pointers passed in are read on the plan's stream; the call returns after
  *     the work has completed (host outputs are written).
  *   - Output arrays are caller-owned host FP64 arrays.
@@ -151,13 +152,16 @@ typedef struct {
   double* nmodes;
 } bisp_outputs;
 
-/* Measure a batch of plans, e.g. many independent realisations on small meshes, in one call:
- * the result for plan i is what bisp_measure(plans[i], outs[i].B, ...) returns.  Each plan must
- * have its catalogues assigned.  The plans are measured one after another on their own streams
- * (the kernels' job tables live in module-wide constant memory, so plans never run
- * concurrently); the call returns when all are done.  Errors: BISP_EINVAL for nplans < 0 or NULL
- * arrays; otherwise the first failing plan's status, with its index in the message (later plans
- * are not measured).  No counterpart in the paper beyond its use of many mocks (Sec. 5.5). */
+/* Measure a batch of plans, e.g. many independent realisations on meshes of different sizes,
+ * in one call: the result for plan i is what bisp_measure(plans[i], outs[i].B, ...) returns, bit
+ * for bit.  Each plan must have its catalogues assigned, and a plan may appear once.  Up to 8 host
+ * worker threads measure the plans concurrently, each plan on its own stream (plans share no
+ * device state: every kernel launch carries its own job table), so the GPU overlaps the work of
+ * several realisations; the call returns when all are done.  Plans created on one shared stream
+ * are serialised by that stream.  Errors: BISP_EINVAL for nplans < 0, NULL arrays or a repeated
+ * plan; otherwise the status of the failing plan with the lowest index, with that index in the
+ * message (the other plans are still measured).  No counterpart in the paper beyond its use of
+ * many mocks (Sec. 5.5). */
 bisp_status bisp_measure_batch(bisp_plan* const* plans, const bisp_outputs* outs, int nplans);
 
 /* Covariance of a batch of measurements (Sec. 5.5, Eq. Covariance): X holds n_mock data

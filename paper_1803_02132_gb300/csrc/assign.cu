@@ -21,10 +21,9 @@ int prep_blocks(int64_t n) {
   return (int)b;
 }
 
-__constant__ PrepArgs c_prep;
-
-__global__ void __launch_bounds__(PREP_THREADS) k_prep() {
-  const PrepArgs& a = c_prep;
+// The job arrives as a __grid_constant__ kernel parameter: every launch carries its own copy,
+// so launches from different plans, streams or host threads never share it.
+__global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ PrepArgs a) {
   constexpr int NSMAX = 34;
   double acc[NSMAX];
 #pragma unroll
@@ -104,8 +103,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep() {
 }
 
 void launch_prep(const PrepArgs& a, cudaStream_t s) {
-  BISP_CUDA(cudaMemcpyToSymbolAsync(c_prep, &a, sizeof(PrepArgs), 0, cudaMemcpyHostToDevice, s));
-  k_prep<<<prep_blocks(a.n), PREP_THREADS, 0, s>>>();
+  k_prep<<<prep_blocks(a.n), PREP_THREADS, 0, s>>>(a);
   BISP_CHECK_LAUNCH();
 }
 
@@ -358,59 +356,152 @@ __device__ __forceinline__ float wker(float t) {
   return 0.f;
 }
 
-// One thread per mesh node c (z fastest).  It visits the home nodes h = c + o,
-// o in [OLO, OHI]^3, as contiguous z runs of the sorted particle array (the run of keys
-// (hx, hy, cz+OLO) .. (hx, hy, cz+OHI)), in a fixed order, so the sums are bit-reproducible.
-// Node positions: mesh 0 at c H, mesh 1 (interlaced) at (c + 1/2) H.  All channels are
-// accumulated in one pass (NC >= nchan registers per mesh).
+// Gather deposit over CTA-owned node tiles.  A CTA owns DT_X x DT_Y x DT_Z mesh nodes (z
+// fastest), one node per thread.  The home cells its nodes draw from, h = c + o with o in
+// [OLO, OHI]^3, form a halo box of RX x RY x RZ cells; their particles, which sit in the sorted
+// arrays as one contiguous range per cell, are listed in (rx, ry, rz) order and staged through
+// shared memory in batches of DT_MAXP, read coalesced.  Every node then visits its (ox, oy, oz)
+// cells in increasing order and each cell's particles in sorted (stable) order: the same order
+// and the same FP32 operations as a node-by-node gather, so the meshes are bit-reproducible.
+// A tile whose halo holds no particle (most of a survey's volume) writes its zeros and returns
+// after one count per halo row.  Node positions: mesh 0 at c H, mesh 1 (interlaced) at
+// (c + 1/2) H.  All channels are accumulated in one pass (NC >= nchan registers per mesh).
+constexpr int DT_X = 4, DT_Y = 4, DT_Z = 16, DT_THREADS = DT_X * DT_Y * DT_Z;
+
+template <int P, int ILV>
+struct DepTile {
+  static constexpr int OLO = (P == 1) ? 0 : -1;
+  static constexpr int OHI = ILV ? (P == 3 ? 2 : 1) : (P == 3 ? 1 : 0);
+  static constexpr int W = OHI - OLO + 1;
+  static constexpr int RX = DT_X + W - 1, RY = DT_Y + W - 1, RZ = DT_Z + W - 1;
+  static constexpr int NCELL = RX * RY * RZ;
+};
+
 template <int P, int ILV, int NC>
-__global__ void __launch_bounds__(256) k_deposit(const uint32_t* __restrict__ cell_start,
-                                                 const uint32_t* __restrict__ keys,
-                                                 const float4* __restrict__ frac, const float* __restrict__ vals,
-                                                 int64_t n, int N, int nchan, float* mesh0, float* mesh1) {
-  constexpr int OLO = (P == 1) ? 0 : -1;
-  constexpr int OHI = ILV ? (P == 3 ? 2 : 1) : (P == 3 ? 1 : 0);
+__global__ void __launch_bounds__(DT_THREADS) k_deposit(const uint32_t* __restrict__ cell_start,
+                                                        const float4* __restrict__ frac,
+                                                        const float* __restrict__ vals, int64_t n, int N,
+                                                        int nchan, float* mesh0, float* mesh1) {
+  using T = DepTile<P, ILV>;
+  constexpr int OLO = T::OLO, OHI = T::OHI, RY = T::RY, RZ = T::RZ, NCELL = T::NCELL;
+  constexpr int MAXP = NC <= 12 ? 512 : 384;  // particles per staged batch (static smem < 48 KB)
+  __shared__ uint32_t s_gs[NCELL];            // first sorted index of each halo cell
+  __shared__ uint32_t s_ts[NCELL + 1];        // position of each halo cell in the tile list
+  __shared__ float4 s_frac[MAXP];
+  __shared__ float s_val[NC][MAXP];
+  __shared__ uint32_t s_wsum[DT_THREADS / 32];
+  __shared__ int s_any;
+  const int ntz = N / DT_Z, nty = N / DT_Y;
+  const int tz = (int)(blockIdx.x % ntz), ty = (int)((blockIdx.x / ntz) % nty), tx = (int)(blockIdx.x / (ntz * nty));
+  const int x0 = tx * DT_X, y0 = ty * DT_Y, z0 = tz * DT_Z;
+  const int lz = threadIdx.x % DT_Z, ly = (threadIdx.x / DT_Z) % DT_Y, lx = threadIdx.x / (DT_Z * DT_Y);
   const int64_t Ng = (int64_t)N * N * N;
-  const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= Ng) return;
-  const int cz = (int)(cell % N), cy = (int)((cell / N) % N), cx = (int)(cell / ((int64_t)N * N));
+  const int64_t cell = ((int64_t)(x0 + lx) * N + (y0 + ly)) * N + (z0 + lz);
+  const uint32_t msk = (uint32_t)(N - 1);
+  const bool zwrap = z0 + OLO < 0 || z0 + DT_Z - 1 + OHI > N - 1;
+  // (1) any particle in the halo?  one range per halo row unless the z run wraps around
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < T::RX * RY; r += blockDim.x) {
+    const uint32_t hx = (uint32_t)(x0 + OLO + r / RY) & msk, hy = (uint32_t)(y0 + OLO + r % RY) & msk;
+    const uint32_t rowkey = (hx * (uint32_t)N + hy) * (uint32_t)N;
+    uint32_t cnt = 0;
+    if (!zwrap) {
+      cnt = cell_start[rowkey + (uint32_t)(z0 + DT_Z - 1 + OHI) + 1] - cell_start[rowkey + (uint32_t)(z0 + OLO)];
+    } else {
+      for (int rz = 0; rz < RZ; ++rz) {
+        const uint32_t k = rowkey + ((uint32_t)(z0 + OLO + rz) & msk);
+        cnt += cell_start[k + 1] - cell_start[k];
+      }
+    }
+    if (cnt) s_any = 1;
+  }
+  __syncthreads();
   float a0[NC], a1[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) a0[k] = a1[k] = 0.f;
-  const bool wrap = cz + OLO < 0 || cz + OHI > N - 1;
-  for (int ox = OLO; ox <= OHI; ++ox) {
-    const int hx = (cx + ox) & (N - 1);
-    for (int oy = OLO; oy <= OHI; ++oy) {
-      const int hy = (cy + oy) & (N - 1);
-      const uint32_t rowkey = ((uint32_t)hx * N + (uint32_t)hy) * (uint32_t)N;
-      // one run without wrap, else one run per home node
-      const int nrun = wrap ? (OHI - OLO + 1) : 1;
-      for (int rr = 0; rr < nrun; ++rr) {
-        uint32_t k0, k1;
-        if (wrap) {
-          k0 = rowkey + (uint32_t)((cz + OLO + rr) & (N - 1));
-          k1 = k0;
-        } else {
-          k0 = rowkey + (uint32_t)(cz + OLO);
-          k1 = rowkey + (uint32_t)(cz + OHI);
-        }
-        const uint32_t p0 = cell_start[k0], p1 = cell_start[k1 + 1];
-        for (uint32_t p = p0; p < p1; ++p) {
-          const float4 d = frac[p];
-          int oz = (int)(keys[p] & (uint32_t)(N - 1)) - cz;
-          if (oz > OHI) oz -= N;
-          if (oz < OLO) oz += N;
-          // distance particle - node along each axis: (h - c) + d
-          const float tx = (float)ox + d.x, ty = (float)oy + d.y, tz = (float)oz + d.z;
-          const float w0 = wker<P>(tx) * wker<P>(ty) * wker<P>(tz);
-          float w1 = 0.f;
-          if (ILV) w1 = wker<P>(tx - 0.5f) * wker<P>(ty - 0.5f) * wker<P>(tz - 0.5f);
+  if (s_any) {
+    // (2) per halo cell: first sorted index and count, then the exclusive scan of the counts
+    constexpr int PER = (NCELL + DT_THREADS - 1) / DT_THREADS;
+    uint32_t cnt[PER];
+    uint32_t tsum = 0;
 #pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            if (k < nchan) {
-              const float v = vals[(size_t)k * n + p];
-              a0[k] = fmaf(w0, v, a0[k]);
-              if (ILV) a1[k] = fmaf(w1, v, a1[k]);
+    for (int j = 0; j < PER; ++j) {
+      const int c = threadIdx.x * PER + j;
+      cnt[j] = 0;
+      if (c < NCELL) {
+        const int rz = c % RZ, ry = (c / RZ) % RY, rx = c / (RZ * RY);
+        const uint32_t hx = (uint32_t)(x0 + OLO + rx) & msk, hy = (uint32_t)(y0 + OLO + ry) & msk;
+        const uint32_t hz = (uint32_t)(z0 + OLO + rz) & msk;
+        const uint32_t k = (hx * (uint32_t)N + hy) * (uint32_t)N + hz;
+        const uint32_t g0 = cell_start[k];
+        s_gs[c] = g0;
+        cnt[j] = cell_start[k + 1] - g0;
+      }
+      tsum += cnt[j];
+    }
+    // block exclusive scan of the per-thread sums (warp shuffles, then the warp totals)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_wsum[wid] = incl;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < wid; ++w) wpre += s_wsum[w];
+    uint32_t pos = wpre + incl - tsum;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int c = threadIdx.x * PER + j;
+      if (c < NCELL) s_ts[c] = pos;
+      pos += cnt[j];
+    }
+    if (threadIdx.x == DT_THREADS - 1) s_ts[NCELL] = pos;
+    __syncthreads();
+    const uint32_t total = s_ts[NCELL];
+    // (3) batches of the tile list
+    for (uint32_t b0 = 0; b0 < total; b0 += MAXP) {
+      const uint32_t b1 = min(total, b0 + (uint32_t)MAXP);
+      __syncthreads();  // the previous batch is consumed
+      for (uint32_t q = b0 + threadIdx.x; q < b1; q += DT_THREADS) {
+        // halo cell of list position q: the last c with s_ts[c] <= q
+        int lo = 0, hi = NCELL - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_ts[mid] <= q) lo = mid;
+          else hi = mid - 1;
+        }
+        const uint32_t g = s_gs[lo] + (q - s_ts[lo]);
+        s_frac[q - b0] = frac[g];
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+          if (k < nchan) s_val[k][q - b0] = vals[(size_t)k * n + g];
+      }
+      __syncthreads();
+      for (int ox = OLO; ox <= OHI; ++ox) {
+        for (int oy = OLO; oy <= OHI; ++oy) {
+          const int rbase = ((lx + ox - OLO) * RY + (ly + oy - OLO)) * RZ + (lz - OLO);
+          for (int oz = OLO; oz <= OHI; ++oz) {
+            const int c = rbase + oz;
+            const uint32_t p0 = max(s_ts[c], b0), p1 = min(s_ts[c + 1], b1);
+            for (uint32_t q = p0; q < p1; ++q) {
+              const float4 d = s_frac[q - b0];
+              // distance particle - node along each axis: (h - c) + d
+              const float tx_ = (float)ox + d.x, ty_ = (float)oy + d.y, tz_ = (float)oz + d.z;
+              const float w0 = wker<P>(tx_) * wker<P>(ty_) * wker<P>(tz_);
+              float w1 = 0.f;
+              if (ILV) w1 = wker<P>(tx_ - 0.5f) * wker<P>(ty_ - 0.5f) * wker<P>(tz_ - 0.5f);
+#pragma unroll
+              for (int k = 0; k < NC; ++k) {
+                if (k < nchan) {
+                  const float v = s_val[k][q - b0];
+                  a0[k] = fmaf(w0, v, a0[k]);
+                  if (ILV) a1[k] = fmaf(w1, v, a1[k]);
+                }
+              }
             }
           }
         }
@@ -429,9 +520,9 @@ __global__ void __launch_bounds__(256) k_deposit(const uint32_t* __restrict__ ce
 template <int P, int ILV>
 static void deposit_p(const DepositArgs& a, cudaStream_t s) {
   const int64_t Ng = (int64_t)a.N * a.N * a.N;
-  const unsigned grid = (unsigned)((Ng + 255) / 256);
+  const unsigned grid = (unsigned)(Ng / DT_THREADS);
 #define BISP_DEP(NC_) \
-  k_deposit<P, ILV, NC_><<<grid, 256, 0, s>>>(a.cell_start, a.keys, a.frac, a.vals, a.n, a.N, a.nchan, a.mesh0, a.mesh1)
+  k_deposit<P, ILV, NC_><<<grid, DT_THREADS, 0, s>>>(a.cell_start, a.frac, a.vals, a.n, a.N, a.nchan, a.mesh0, a.mesh1)
   if (a.nchan <= 1) BISP_DEP(1);
   else if (a.nchan <= 2) BISP_DEP(2);
   else if (a.nchan <= 6) BISP_DEP(6);

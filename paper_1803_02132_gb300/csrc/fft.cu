@@ -193,7 +193,6 @@ void forward_fft(float* mesh0, float* mesh1, int count, int N, int mas, const fl
 // ====================================================================================
 // inverse, pruned
 // ====================================================================================
-__constant__ InvBatch c_inv;
 
 // y_l^m(n) for one (l, m >= 0) by the associated-Legendre recurrence (see common.cuh)
 __device__ __forceinline__ float2 ylm_one(int l, int m, float x, float y, float z, const float* ynorm) {
@@ -269,11 +268,11 @@ __host__ __device__ __forceinline__ InvGeo inv_geo(int N, int P, int LB) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(float2* t1all, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(const __grid_constant__ InvBatch B, float2* t1all,
+                                                      const float2* __restrict__ tw) {
   constexpr int NH = N / 2, LB = Geo<N>::LB, TS = Geo<N>::TS;
   constexpr int EPT = N * LB / TS;  // elements per thread
   extern __shared__ float2 s[];
-  const InvBatch& B = c_inv;
   const InvGeo g = inv_geo(N, B.P, LB);
   const int nz0 = blockIdx.x * LB, iy = blockIdx.y;
   const int sy = iy - g.P;
@@ -359,80 +358,9 @@ __global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(float2* t1all, const float
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::TS) k_inv_y(const float2* t1all, float2* t2all,
-                                                      const float2* __restrict__ tw) {
-  constexpr int LB = Geo<N>::LB;
-  extern __shared__ float2 s[];
-  const InvBatch& B = c_inv;
-  const InvGeo g = inv_geo(N, B.P, LB);
-  const int nz0 = blockIdx.x * LB, x = blockIdx.y, f = blockIdx.z;
-  const float2* t1 = t1all + (size_t)f * g.t1;
-  for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
-    const int l = i % LB, e = i / LB;
-    const int sy = sgn_idx(e, N);
-    float2 v = make_float2(0.f, 0.f);
-    if (sy >= -g.P && sy <= g.P) v = t1[((size_t)x * g.ny + (sy + g.P)) * g.Pz + nz0 + l];
-    s[i] = v;
-  }
-  __syncthreads();
-  fft_smem<N, LB, +1>(s, tw);
-  float2* t2 = t2all + (size_t)f * g.t2;
-  for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
-    const int l = i % LB, e = i / LB;
-    t2[((size_t)x * N + e) * g.Pz + nz0 + l] = s[i];
-  }
-}
-
 // c2r along z: X[k], k <= P (Pz stored, zero above P), Nyquist zero.
 //   Z[k] = (X[k] + X*[NH-k]) + i (X[k] - X*[NH-k]) e^{2 pi i k / N};  z = IDFT_NH(Z)
 //   x[2j] = Re z[j], x[2j+1] = Im z[j]
-template <int N>
-__global__ void __launch_bounds__(Geo<N>::TZ) k_inv_z(const float2* t2all, const float2* __restrict__ tw) {
-  constexpr int NH = N / 2, LBZ = Geo<N>::LBZ, LD = LBZ + 1;
-  __shared__ float2 s[NH * LD];
-  const InvBatch& B = c_inv;
-  const InvGeo g = inv_geo(N, B.P, Geo<N>::LB);
-  const int f = blockIdx.y;
-  const size_t r0 = (size_t)blockIdx.x * LBZ;
-  const float2* t2 = t2all + (size_t)f * g.t2 + r0 * g.Pz;
-  for (int i = threadIdx.x; i < LBZ * NH; i += blockDim.x) {
-    const int l = i / NH, e = i % NH;
-    s[e * LD + l] = e < g.Pz ? t2[(size_t)l * g.Pz + e] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < LBZ * (NH / 2 + 1); i += blockDim.x) {
-    const int l = i % LBZ, k = i / LBZ;
-    if (k == 0) {
-      const float a = s[l].x;
-      s[l] = make_float2(a, a);
-    } else {
-      const int kp = NH - k;
-      const float2 a = s[k * LD + l], b = s[kp * LD + l];
-      const float2 wk = cconj(tw[k * (BISP_TWN / N)]);
-      const float2 wkp = cconj(tw[kp * (BISP_TWN / N)]);
-      const float2 sp = make_float2(a.x + b.x, a.y - b.y);   // a + b*
-      const float2 dm = make_float2(a.x - b.x, a.y + b.y);   // a - b*
-      const float2 t = cmul(dm, wk);
-      const float2 zk = make_float2(sp.x - t.y, sp.y + t.x);  // sp + i t
-      const float2 sp2 = make_float2(b.x + a.x, b.y - a.y);
-      const float2 dm2 = make_float2(b.x - a.x, b.y + a.y);
-      const float2 t2v = cmul(dm2, wkp);
-      const float2 zkp = make_float2(sp2.x - t2v.y, sp2.y + t2v.x);
-      s[k * LD + l] = zk;
-      if (kp != k) s[kp * LD + l] = zkp;
-    }
-  }
-  __syncthreads();
-  fft_smem<NH, LBZ, +1>(s, tw, LD);
-  float* out = B.f[f].out + r0 * N;
-  float2* o2 = reinterpret_cast<float2*>(out);
-  for (int i = threadIdx.x; i < LBZ * NH; i += blockDim.x) {
-    const int l = i / NH, e = i % NH;
-    o2[(size_t)l * NH + e] = s[e * LD + l];
-  }
-}
-
 // c2r along z with the FFT held in registers: NH = A x B, A threads per row, each holding
 // B values.  Step 1: Z[n] for n = a + A b (c2r pre-processing from the T2 row, read from
 // global memory); step 2: B-point DFTs over b; step 3: twiddle e^{2 pi i a kb / NH};
@@ -478,8 +406,8 @@ __device__ __forceinline__ void fft_bulk_load(unsigned dst, const void* src, uns
 }
 
 template <int N>
-__global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const float2* __restrict__ tw,
-                                                   int* err) {
+__global__ void __launch_bounds__(256) k_inv_z_reg(const __grid_constant__ InvBatch Bt, const float2* t2all,
+                                                   const float2* __restrict__ tw, int* err) {
   constexpr int NH = N / 2, A = RegZ<N>::A, B = RegZ<N>::B, ROWS = RegZ<N>::ROWS;
   constexpr int LDT = A + 1;  // padded transpose row
   static_assert(B % A == 0, "B must be a multiple of A");
@@ -487,7 +415,6 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
   float2* wNH = sbuf + ROWS * B * LDT;  // e^{+2 pi i j / NH}
   float2* wN = wNH + NH;                // e^{+2 pi i j / N}, j < NH
   float2* tin = wN + NH;                // two input tiles [ROWS][Pz]
-  const InvBatch& Bt = c_inv;
   const InvGeo g = inv_geo(N, Bt.P, Geo<N>::LB);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(tin + 2 * ROWS * g.Pz);
   const int f = blockIdx.y;
@@ -495,12 +422,14 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
   const unsigned tile_bytes = (unsigned)(ROWS * g.Pz * sizeof(float2));
   const float2* src0 = t2all + (size_t)f * g.t2 + (size_t)blockIdx.x * GROUPS * ROWS * g.Pz;
   const unsigned bar0 = fft_su32(bars);
+  __shared__ int s_abort;
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
     // the first group's rows (contiguous: ROWS consecutive T2 rows)
-    fft_bulk_load(fft_su32(tin), src0, tile_bytes, bar0);
+    if (!Bt.stall) fft_bulk_load(fft_su32(tin), src0, tile_bytes, bar0);
   }
   for (int j = threadIdx.x; j < NH; j += blockDim.x) {
     wNH[j] = cconj(tw[(j * (BISP_TWN / NH)) & (BISP_TWN - 1)]);
@@ -508,18 +437,18 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
   }
   __syncthreads();
   const int l = threadIdx.x / A, a = threadIdx.x % A;
-  bool ok = true;
-  for (int grp = 0; grp < GROUPS; ++grp) {
+  int grp = 0;
+  for (; grp < GROUPS; ++grp) {
     const int cur = grp & 1;
     // prefetch the next group's rows into the other tile (its previous reader, group grp-1,
     // finished before the barrier that ended it)
-    if (threadIdx.x == 0 && grp + 1 < GROUPS) {
+    if (threadIdx.x == 0 && grp + 1 < GROUPS && !Bt.stall) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       fft_bulk_load(fft_su32(tin + (cur ^ 1) * ROWS * g.Pz), src0 + (size_t)(grp + 1) * ROWS * g.Pz, tile_bytes,
                     bar0 + 8u * (cur ^ 1));
     }
     if (!fft_wait(bar0 + 8u * cur, (unsigned)(grp >> 1) & 1u)) {
-      ok = false;
+      s_abort = 1;
       atomicExch(err, 1);
     }
     const size_t row = ((size_t)blockIdx.x * GROUPS + grp) * ROWS + l;
@@ -548,6 +477,7 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
       sbuf[(l * B + kb) * LDT + a] = cmul(v[kb], wNH[(a * kb) & (NH - 1)]);
     }
     __syncthreads();  // also: every thread has read input tile cur
+    if (s_abort) break;  // uniform: set before the barrier; nothing is stored after a timeout
     // stage 2: thread a handles kb = a + A r, r < B / A, an A-point DFT over a' each
     float* out = Bt.f[f].out + row * N;
 #pragma unroll
@@ -560,9 +490,15 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const float2* t2all, const fl
 #pragma unroll
       for (int ka = 0; ka < A; ++ka) {
         const int m = kb + B * ka;
-        if (ok) reinterpret_cast<float2*>(out)[m] = u[ka];
+        reinterpret_cast<float2*>(out)[m] = u[ka];
       }
     }
+  }
+  // after a timeout, the copies of this group and of the prefetched next one may still be in
+  // flight: wait for them (bounded) before the CTA's shared memory is released
+  if (s_abort && threadIdx.x == 0 && !Bt.stall) {
+    fft_wait(bar0 + 8u * (grp & 1), (unsigned)(grp >> 1) & 1u);
+    if (grp + 1 < GROUPS) fft_wait(bar0 + 8u * ((grp + 1) & 1), (unsigned)((grp + 1) >> 1) & 1u);
   }
 }
 
@@ -619,14 +555,14 @@ __device__ __forceinline__ void regl_twiddles(float2* wtab, const float2* __rest
 }
 
 template <int N>
-__global__ void __launch_bounds__(RegL<N>::THREADS) k_inv_y_reg(const float2* t1all, float2* t2all,
+__global__ void __launch_bounds__(RegL<N>::THREADS) k_inv_y_reg(const __grid_constant__ InvBatch Bt,
+                                                                  const float2* t1all, float2* t2all,
                                                                   const float2* __restrict__ tw) {
   constexpr int A = RegL<N>::A, B = RegL<N>::B, LB = RegL<N>::LB;
   extern __shared__ float2 sm[];
   float2* s = sm;
   float2* wtab = sm + (size_t)B * A * LB;
   regl_twiddles<N, +1>(wtab, tw);
-  const InvBatch& Bt = c_inv;
   const InvGeo g = inv_geo(N, Bt.P, LB);
   const int nz0 = blockIdx.x * LB, x = blockIdx.y, f = blockIdx.z;
   const int l = threadIdx.x % LB, a = threadIdx.x / LB;
@@ -651,19 +587,18 @@ static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStr
   const InvGeo g = inv_geo(N, b.P, G::LB);
   float2* t1 = reinterpret_cast<float2*>(scratch);
   float2* t2 = t1 + (size_t)b.nf * g.t1;
-  BISP_CUDA(cudaMemcpyToSymbolAsync(c_inv, &b, sizeof(InvBatch), 0, cudaMemcpyHostToDevice, s));
   using RL = RegL<N>;
   const size_t s1 = (size_t)N * G::LB * sizeof(float2);
   smem_attr(k_inv_x<N>, s1);
   smem_attr(k_inv_y_reg<N>, RL::SMEM);
-  k_inv_x<N><<<dim3(g.Pz / G::LB, g.ny), G::TS, s1, s>>>(t1, tw);
+  k_inv_x<N><<<dim3(g.Pz / G::LB, g.ny), G::TS, s1, s>>>(b, t1, tw);
   BISP_CHECK_LAUNCH();
-  k_inv_y_reg<N><<<dim3(g.Pz / G::LB, N, b.nf), RL::THREADS, RL::SMEM, s>>>(t1, t2, tw);
+  k_inv_y_reg<N><<<dim3(g.Pz / G::LB, N, b.nf), RL::THREADS, RL::SMEM, s>>>(b, t1, t2, tw);
   BISP_CHECK_LAUNCH();
   using RZ = RegZ<N>;
   const size_t zs = RZ::smem(g.Pz);
   smem_attr(k_inv_z_reg<N>, RZ::smem(N / 2));
-  k_inv_z_reg<N><<<dim3(N * N / (RZ::ROWS * RZ::GROUPS), b.nf), 256, zs, s>>>(t2, tw, b.err);
+  k_inv_z_reg<N><<<dim3(N * N / (RZ::ROWS * RZ::GROUPS), b.nf), 256, zs, s>>>(b, t2, tw, b.err);
   BISP_CHECK_LAUNCH();
   if (launches) *launches += 3;
 }

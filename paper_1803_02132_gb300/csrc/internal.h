@@ -20,6 +20,10 @@ struct Error {
       throw ::bisp::Error{3, std::string(#call) + ": " + cudaGetErrorString(e_)};         \
   } while (0)
 #define BISP_CHECK_LAUNCH() BISP_CUDA(cudaGetLastError())
+// Test knob: BISP_INJECT_STALL names kernels ("pair", "zpass") whose first launch in a library call
+// starts none of its staged copies, so that its bounded waits run out and the call reports
+// BISP_ETIMEOUT (no copy is left in flight).
+bool inject_stall(const char* kernel);
 // message returned by bisp_last_error() on the calling thread
 void set_last_error(const std::string& m);
 
@@ -120,6 +124,7 @@ struct InvBatch {
   const float* cw2_1d;    // QSHOT: per-axis tables (E, O, W) packed, see fft.cu
   int interlace;
   int* err;               // set (never cleared) when a bounded wait gives up
+  int stall;              // test knob: the z pass starts no row-group copy (its waits run out)
 };
 size_t inverse_scratch_bytes(int N, int P, int nf);
 

@@ -41,7 +41,6 @@ void launch_axpby(float2* out, const float2* x, double a, const float2* y, doubl
 // ------------------------------------------------------------------------------------
 // shell sums
 // ------------------------------------------------------------------------------------
-__constant__ ZsumArgs c_zs;
 constexpr int ZS_THREADS = 256;
 constexpr int ZS_MAXLM = 9;
 
@@ -57,8 +56,8 @@ __device__ __forceinline__ void zs_add(float& s, float& c, float x) {
   s = t;
 }
 
-__global__ void __launch_bounds__(ZS_THREADS) k_zsum() {
-  const ZsumArgs& A = c_zs;
+// the job is a __grid_constant__ parameter (each launch carries its own copy)
+__global__ void __launch_bounds__(ZS_THREADS) k_zsum(const __grid_constant__ ZsumArgs A) {
   const int b = blockIdx.y;
   const int N = A.N, NH = N / 2;
   const int64_t m0 = A.mode_off[b], m1 = A.mode_off[b + 1];
@@ -157,8 +156,7 @@ __device__ __forceinline__ float2 ystar(int l, int m, float x, float y, float z,
 
 void launch_zsum(const ZsumArgs& a, cudaStream_t s) {
   if (a.nlm > ZS_MAXLM) throw Error{6, "zsum: too many (l, m) per launch"};
-  BISP_CUDA(cudaMemcpyToSymbolAsync(c_zs, &a, sizeof(ZsumArgs), 0, cudaMemcpyHostToDevice, s));
-  k_zsum<<<dim3(a.nblk, a.nbins), ZS_THREADS, 0, s>>>();
+  k_zsum<<<dim3(a.nblk, a.nbins), ZS_THREADS, 0, s>>>(a);
   BISP_CHECK_LAUNCH();
 }
 

@@ -36,7 +36,9 @@ namespace bisp {
 // FP32 partials over at most PR_FLUSH chunks are added to lane-owned FP64 slots in global
 // memory; a second kernel reduces the slots in a fixed order.
 // ------------------------------------------------------------------------------------
-__constant__ PairJob c_pj;
+// Every kernel takes its PairJob as a __grid_constant__ parameter (about 22 KB, inside the 32 KB
+// parameter space): each launch carries its own copy, so launches of different plans, streams or
+// host threads never share a job table.
 constexpr int PR_CH = 64;          // cells per chunk
 constexpr int PR_LD = PR_CH + 4;   // padded row (bank spread for 16-byte loads)
 constexpr int PR_FLUSH = 16;       // chunks per FP32 partial (<= 1024 cells)
@@ -224,8 +226,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // copy one chunk of every component row [b][comp] and G row into shared memory;
 // rowmap[f] = destination row of source row f (f < nb*ncomp: field (b, comp); then G rows)
-__device__ __forceinline__ void pair_stage(float* raw, int64_t x0, const int* rowmap) {
-  const PairJob& J = c_pj;
+__device__ __forceinline__ void pair_stage(const PairJob& J, float* raw, int64_t x0, const int* rowmap) {
   constexpr int Q = PR_CH / 4;  // 16-byte pieces per row (a power of two)
   constexpr int QS = Q == 16 ? 4 : (Q == 8 ? 3 : 2);
   const int nraw = J.nb * J.ncomp;
@@ -240,8 +241,8 @@ __device__ __forceinline__ void pair_stage(float* raw, int64_t x0, const int* ro
 // built sides, block-wide: first the H rows of the chunk, H_h(x) = sum coef G_g(x) (shared by
 // all bins), then one thread per (side, bin, 4-cell quad): X(b, x) = sum_(c,h) P_c(b, x) H_h(x).
 // mnb = ceil(2^32 / nb): j / nb = umulhi(j, mnb) for the small j used here.
-__device__ __forceinline__ void pair_build_sides(const float* raw, float* mat, float* Hs, int bs, unsigned mnb) {
-  const PairJob& J = c_pj;
+__device__ __forceinline__ void pair_build_sides(const PairJob& J, const float* raw, float* mat, float* Hs, int bs,
+                                                 unsigned mnb) {
   constexpr int Q = PR_CH / 4;
   constexpr int QS = Q == 16 ? 4 : (Q == 8 ? 3 : 2);
   const int grow0 = J.nb * bs;
@@ -289,8 +290,8 @@ __device__ __forceinline__ void pair_build_sides(const float* raw, float* mat, f
 }
 
 template <int TM, int TN, int NTHR>
-__global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int ksplit, double* partials) {
-  const PairJob& J = c_pj;
+__global__ void __launch_bounds__(NTHR, 1) k_pair(const __grid_constant__ PairJob J, int nbp, int bs, int rows,
+                                                  int ksplit, double* partials) {
   extern __shared__ __align__(16) float sh[];
   float* mat = sh + (size_t)PR_NSTAGE * rows * PR_LD;  // [nslot][nb][PR_LD]
   float* Hs = mat + (size_t)J.nslot * J.nb * PR_LD;  // [nh][PR_CH]
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
-  if (blockIdx.x < nchunk) pair_stage(sh, (int64_t)blockIdx.x * PR_CH, rowmap);
+  if (blockIdx.x < nchunk) pair_stage(J, sh, (int64_t)blockIdx.x * PR_CH, rowmap);
   cp_async_commit();
   int since_flush = 0, stage = 0;
   for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
@@ -323,12 +324,12 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(int nbp, int bs, int rows, int
     __syncthreads();
     {
       const int64_t nx = ch + gridDim.x;
-      if (nx < nchunk) pair_stage(sh + (size_t)(stage ^ 1) * rows * PR_LD, nx * PR_CH, rowmap);
+      if (nx < nchunk) pair_stage(J, sh + (size_t)(stage ^ 1) * rows * PR_LD, nx * PR_CH, rowmap);
       cp_async_commit();
     }
     const float* raw = sh + (size_t)stage * rows * PR_LD;
     if (J.nslot) {
-      pair_build_sides(raw, mat, Hs, bs, mnb);
+      pair_build_sides(J, raw, mat, Hs, bs, mnb);
       __syncthreads();
     }
     // row pointers of this lane's bins b1 + 4 i and b2 + 8 j (clamped to a valid row)
@@ -422,6 +423,7 @@ struct TmaLayout {
   unsigned bytes;     // dynamic shared memory to request (includes 1024 B alignment slack)
   unsigned tx;        // transaction bytes per stage
   int ncomp, gbox;    // F blocks per half, G rows
+  int stall;          // test knob: start no stage copy, so that every bounded wait runs out
 };
 
 constexpr int TMA_MAXWARP = 20;  // two warps (row halves) per term and cell half
@@ -519,9 +521,8 @@ __device__ __forceinline__ void kahan_add(float2& v, float x) {
 }
 template <int NTHR>
 __global__ void __launch_bounds__(NTHR, 1)
-    k_pair_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const TmaLayout L,
-               int ksplit, double* partials, int* err) {
-  const PairJob& J = c_pj;
+    k_pair_tma(const __grid_constant__ PairJob J, const __grid_constant__ CUtensorMap tmF,
+               const __grid_constant__ CUtensorMap tmG, const TmaLayout L, int ksplit, double* partials, int* err) {
   extern __shared__ unsigned char dsm[];
   __shared__ int s_abort;
   const unsigned raw0 = smem_u32(dsm);
@@ -545,6 +546,7 @@ __global__ void __launch_bounds__(NTHR, 1)
   }
   __syncthreads();
   auto issue = [&](int64_t ch, int st) {  // thread 0 only
+    if (L.stall) return;
     const unsigned bar = bar0 + 8u * st;
     mbar_expect_tx(bar, L.tx);
     for (int h = 0; h < 2; ++h) {
@@ -734,7 +736,6 @@ struct UmmaPlan {
   int slot_side[UM_MAXS];  // side (s_off index) built into B block k
   int warp_slot[UM_WARPS];  // term slot read back by each warp, or -1
 };
-__constant__ UmmaPlan c_um;
 
 struct UmmaLayout {
   unsigned fsz, stage;               // F blocks (ncomp x 4096), raw stage (F + G block)
@@ -783,10 +784,9 @@ __device__ __forceinline__ float4 split_hi4(float4 v) {
 }
 
 __global__ void __launch_bounds__(UM_WARPS * 32, 1)
-    k_pair_umma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const UmmaLayout L,
+    k_pair_umma(const __grid_constant__ PairJob J, const __grid_constant__ UmmaPlan U,
+                const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const UmmaLayout L,
                 float2* slots, int* err) {
-  const PairJob& J = c_pj;
-  const UmmaPlan& U = c_um;
   extern __shared__ unsigned char dsm[];
   __shared__ int s_abort;
   const unsigned raw0 = smem_u32(dsm);
@@ -981,8 +981,8 @@ __global__ void __launch_bounds__(UM_WARPS * 32, 1)
 // out[o][b1][b2] from the compensated slots of k_pair_umma: term t lives in warp
 // 4 grp + quad, lane = bin of its bare side, slot = bin of its built side (T.tr says which of
 // the output's two bins is the lane); fixed-order sums over CTAs.
-__global__ void k_pair_umma_final(const float2* slots, int nblk, int nb, int nout, double* out) {
-  const PairJob& J = c_pj;
+__global__ void k_pair_umma_final(const __grid_constant__ PairJob J, const float2* slots, int nblk, int nb, int nout,
+                                  double* out) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= nout * nb * nb) return;
   const int o = gw / (nb * nb), c1 = (gw / nb) % nb, c2 = gw % nb;
@@ -1021,6 +1021,7 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   L->ncomp = j.ncomp;
   L->gbox = j.ng;
   L->tx = (unsigned)(2 * (fsz + (size_t)j.ng * 128));
+  L->stall = 0;
   *ksplit = 4 * j.nterm <= TMA_MAXWARP ? 2 : 1;
   *warps = 2 * j.nterm * *ksplit;
   return true;
@@ -1225,9 +1226,8 @@ size_t pair_scratch_bytes(const PairJob& job) {
 // final reduction for k_pair_tma (slots are compensated FP32 pairs (s, e), sum s - e): bin
 // (b1, b2) of term t (after the transpose (b1, b2) -> (b2, b1) of terms with T.tr) sits in warp
 // (t*ksplit + ks)*2 + b1/16, lane (b1%8)*4 + (b2%8)/2, slot (b2/8)*4 + ((b1/8)%2)*2 + b2%2
-__global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int ksplit, int nb, int nout,
-                                double* out) {
-  const PairJob& J = c_pj;
+__global__ void k_pair_tc_final(const __grid_constant__ PairJob J, const double* partials, int nblk, int warps,
+                                int ksplit, int nb, int nout, double* out) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= nout * nb * nb) return;
   const int o = gw / (nb * nb), c1 = (gw / nb) % nb, c2 = gw % nb;
@@ -1254,9 +1254,8 @@ __global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int
 
 // out[o][b1][b2] = sum over terms of o, then CTAs and x slices in a fixed order; one warp
 // per output value, lanes stride over CTAs, fixed shuffle tree.
-__global__ void k_pair_final(const double* partials, int nblk, int warps, int ksplit, int TM, int TN, int nb,
-                             int nout, double* out) {
-  const PairJob& J = c_pj;
+__global__ void k_pair_final(const __grid_constant__ PairJob J, const double* partials, int nblk, int warps,
+                             int ksplit, int TM, int TN, int nb, int nout, double* out) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= nout * nb * nb) return;
   const int o = gw / (nb * nb), b1 = (gw / nb) % nb, b2 = gw % nb;
@@ -1281,15 +1280,12 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
   const PairJob j = classify(job);
   if (scratch_bytes < pair_scratch_bytes(job)) throw Error{2, "pair reduction scratch too small"};
   if (j.Ng % PR_CH) throw Error{6, "mesh size not a multiple of the chunk"};
-  BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &j, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
   double* partials = reinterpret_cast<double*>(scratch);
   if (pair_use_tc(j) && pair_use_umma()) {
     PairJob jt = normalised(j);
     UmmaPlan U;
     UmmaLayout UL;
     if (umma_plan(jt, &U, &UL)) {
-      BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &jt, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
-      BISP_CUDA(cudaMemcpyToSymbolAsync(c_um, &U, sizeof(UmmaPlan), 0, cudaMemcpyHostToDevice, s));
       const int nblk = pair_blocks();
       float2* slots = reinterpret_cast<float2*>(scratch);
       int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) +
@@ -1298,10 +1294,10 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
       const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb);
       const CUtensorMap mg = g_map(j.gfields, j.Ng, j.ng);
       BISP_CUDA(cudaFuncSetAttribute(k_pair_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UL.bytes));
-      k_pair_umma<<<nblk, UM_WARPS * 32, UL.bytes, s>>>(mf, mg, UL, slots, err);
+      k_pair_umma<<<nblk, UM_WARPS * 32, UL.bytes, s>>>(jt, U, mf, mg, UL, slots, err);
       BISP_CHECK_LAUNCH();
       const int nout = j.nout * j.nb * j.nb;
-      k_pair_umma_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(slots, nblk, j.nb, j.nout, out_dev);
+      k_pair_umma_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(jt, slots, nblk, j.nb, j.nout, out_dev);
       BISP_CHECK_LAUNCH();
       int herr = 0;
       BISP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1317,19 +1313,20 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
   if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) {
     // the mma.sync kernel builds only A operands (see normalised)
     PairJob jt = normalised(j);
-    BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &jt, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
     const int nblk = pair_blocks();
     const size_t need = (size_t)nblk * warps * 32 * 16 * sizeof(float2);
     int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + need);
     BISP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb);
     const CUtensorMap mg = g_map(j.gfields, j.Ng, j.ng);
+    L.stall = inject_stall("pair") ? 1 : 0;
     BISP_CUDA(cudaFuncSetAttribute(k_pair_tma<32 * TMA_MAXWARP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)L.bytes));
-    k_pair_tma<32 * TMA_MAXWARP><<<nblk, warps * 32, L.bytes, s>>>(mf, mg, L, ksplit, partials, err);
+    k_pair_tma<32 * TMA_MAXWARP><<<nblk, warps * 32, L.bytes, s>>>(jt, mf, mg, L, ksplit, partials, err);
     BISP_CHECK_LAUNCH();
     const int nout = j.nout * j.nb * j.nb;
-    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(partials, nblk, warps, ksplit, j.nb, j.nout, out_dev);
+    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(jt, partials, nblk, warps, ksplit, j.nb, j.nout,
+                                                               out_dev);
     BISP_CHECK_LAUNCH();
     int herr = 0;
     BISP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1344,7 +1341,7 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
 #define BISP_PAIR3(A, B, NT)                                                                              \
   if (c.TM == A && c.TN == B && c.warps * 32 <= NT) {                                                   \
     BISP_CUDA(cudaFuncSetAttribute(k_pair<A, B, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem)); \
-    k_pair<A, B, NT><<<c.nblk, c.warps * 32, c.smem, s>>>(c.nbp, c.bs, c.rows, c.ksplit, partials);           \
+    k_pair<A, B, NT><<<c.nblk, c.warps * 32, c.smem, s>>>(j, c.nbp, c.bs, c.rows, c.ksplit, partials);           \
     launched = true;                                                                                     \
   }
 #define BISP_PAIR(A, B) \
@@ -1360,8 +1357,8 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
   if (!launched) throw Error{6, "pair reduction: no kernel for this shape"};
   BISP_CHECK_LAUNCH();
   const int nout = j.nout * j.nb * j.nb;
-  k_pair_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(partials, c.nblk, c.warps, c.ksplit, c.TM, c.TN, j.nb,
-                                                       j.nout, out_dev);
+  k_pair_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(j, partials, c.nblk, c.warps, c.ksplit, c.TM, c.TN,
+                                                       j.nb, j.nout, out_dev);
   BISP_CHECK_LAUNCH();
   if (launches) *launches += 2;
   if (kernel) *kernel = 0;

@@ -5,12 +5,14 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -23,6 +25,9 @@ using namespace bisp;
 namespace {
 
 thread_local std::string g_err;
+
+// host threads of bisp_measure_batch (plans measured at the same time)
+constexpr int kBatchThreads = 8;
 
 struct Fail {
   int status;
@@ -122,12 +127,27 @@ cplx cm(cplx a, cplx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r};
 // ---------------------------------------------------------------------------------
 // device buffer cache
 // ---------------------------------------------------------------------------------
+// Allocation-failure injection for tests: with BISP_FAIL_ALLOC=k in the environment, the k-th
+// device allocation within one library call fails as if cudaMalloc had (the count restarts at
+// every call of the C ABI).
+thread_local int g_alloc_calls = 0;
+bool inject_alloc_failure() {
+  const char* e = getenv("BISP_FAIL_ALLOC");
+  if (!e || !*e) return false;
+  return ++g_alloc_calls == atoi(e);
+}
+
 struct DBuf {
   void* p = nullptr;
   size_t n = 0;
   void ensure(size_t bytes, size_t* total) {
     if (bytes <= n) return;
     release(total);
+    if (inject_alloc_failure()) {
+      char buf[200];
+      snprintf(buf, sizeof buf, "device allocation of %.3f GB failed (injected by BISP_FAIL_ALLOC)", bytes / 1e9);
+      fail(BISP_ENOMEM, buf);
+    }
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -172,6 +192,17 @@ struct Catalog {
 }  // namespace
 
 void bisp::set_last_error(const std::string& m) { g_err = m; }
+
+// one injected stall per kernel kind and library call (the first launch), reset by guarded()
+thread_local unsigned g_stalls_used = 0;
+bool bisp::inject_stall(const char* kernel) {
+  const char* e = getenv("BISP_INJECT_STALL");
+  if (!e || !strstr(e, kernel)) return false;
+  const unsigned bit = strcmp(kernel, "pair") == 0 ? 1u : 2u;
+  if (g_stalls_used & bit) return false;
+  g_stalls_used |= bit;
+  return true;
+}
 
 struct bisp_plan {
   // parameters
@@ -631,6 +662,7 @@ void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const 
   Catalog& C = P->cat[which];
   cudaStream_t s = P->stream;
   int launches = 0;
+  C.assigned = false;  // set again only when this assignment completes (its buffers may be replaced)
   BISP_CUDA(cudaEventRecord(P->ev0, s));
   const int N = P->N;
   const int64_t Ng = P->Ng;
@@ -825,12 +857,15 @@ struct PassState {
   std::map<std::tuple<int, int, int, int>, std::vector<cplx>> Z;
 };
 
-// pair reduction over the first nbu bins held in the field pool.  A job whose terms do not fit
-// one contraction launch is split: per G set first, then into halves of the multipole list;
-// the outputs keep the layout [gset][mult][b1][b2] of a single launch.
-void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstride, const float* gbase, int nbu,
-              std::vector<double>& out, int* launches) {
-  // build a pair job with nout = mults.size() * gsets outputs
+// pair reduction over the first nbu bins held in the field pool, for the term lists tl (one
+// per multipole).  A job whose terms do not fit one contraction launch is split: per G set
+// first, then into halves of the multipole list, then a single multipole's terms into halves
+// whose results are added in FP64 (a fixed order, so results stay reproducible); the outputs
+// keep the layout [gset][mult][b1][b2] of a single launch.
+using TermList = std::vector<bisp_plan::Term>;
+void run_pair_terms(bisp_plan* P, const std::vector<const TermList*>& tl, int gsets, int gstride, const float* gbase,
+                    int nbu, std::vector<double>& out, int* launches) {
+  // build a pair job with nout = tl.size() * gsets outputs
   PairJob J{};
   J.fields = P->pool.as<float>();
   J.gfields = gbase;
@@ -838,14 +873,14 @@ void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstrid
   J.nb = nbu;
   J.ncomp = (int)P->comps.size();
   J.ng = gsets * gstride;
-  J.nout = (int)mults.size() * gsets;
+  J.nout = (int)tl.size() * gsets;
   int t = 0, r = 0;
   bool tables_ok = true;
   for (int gs = 0; gs < gsets && tables_ok; ++gs)
-    for (size_t i = 0; i < mults.size() && tables_ok; ++i) {
-      const int o = gs * (int)mults.size() + (int)i;
+    for (size_t i = 0; i < tl.size() && tables_ok; ++i) {
+      const int o = gs * (int)tl.size() + (int)i;
       J.out_term_off[o] = t;
-      for (auto& term : P->terms[mults[i]]) {
+      for (auto& term : *tl[i]) {
         if (t >= 64 || r + (int)(term.x.size() + term.y.size()) > 512) {
           tables_ok = false;
           break;
@@ -873,20 +908,28 @@ void run_pair(bisp_plan* P, const std::vector<int>& mults, int gsets, int gstrid
     out.clear();
     if (gsets > 1) {
       for (int gs = 0; gs < gsets; ++gs) {
-        run_pair(P, mults, 1, gstride, gbase + (size_t)gs * gstride * P->Ng, nbu, part, launches);
+        run_pair_terms(P, tl, 1, gstride, gbase + (size_t)gs * gstride * P->Ng, nbu, part, launches);
         out.insert(out.end(), part.begin(), part.end());
       }
       return;
     }
-    if (mults.size() > 1) {
-      const size_t h = mults.size() / 2;
-      run_pair(P, std::vector<int>(mults.begin(), mults.begin() + h), 1, gstride, gbase, nbu, part, launches);
+    if (tl.size() > 1) {
+      const size_t h = tl.size() / 2;
+      run_pair_terms(P, std::vector<const TermList*>(tl.begin(), tl.begin() + h), 1, gstride, gbase, nbu, part,
+                     launches);
       out.insert(out.end(), part.begin(), part.end());
-      run_pair(P, std::vector<int>(mults.begin() + h, mults.end()), 1, gstride, gbase, nbu, part, launches);
+      run_pair_terms(P, std::vector<const TermList*>(tl.begin() + h, tl.end()), 1, gstride, gbase, nbu, part,
+                     launches);
       out.insert(out.end(), part.begin(), part.end());
       return;
     }
-    fail(BISP_EUNSUPPORTED, "the contraction terms of one multipole do not fit one launch");
+    if (tl[0]->size() < 2) fail(BISP_EUNSUPPORTED, "a contraction term does not fit one launch");
+    const size_t h = tl[0]->size() / 2;
+    const TermList lo(tl[0]->begin(), tl[0]->begin() + h), hi(tl[0]->begin() + h, tl[0]->end());
+    run_pair_terms(P, {&lo}, 1, gstride, gbase, nbu, out, launches);
+    run_pair_terms(P, {&hi}, 1, gstride, gbase, nbu, part, launches);
+    for (size_t i = 0; i < out.size(); ++i) out[i] += part[i];
+    return;
   }
   const size_t sb = pair_scratch_bytes(J);
   admit(P, sb > P->pairscr.n ? sb - P->pairscr.n : 0);
@@ -918,6 +961,7 @@ void run_inverse(bisp_plan* P, InvBatch& b, int* launches) {
   b.cw2_1d = P->cw2.as<float>();
   b.interlace = P->interlace;
   b.err = P->flags.as<int>();
+  b.stall = inject_stall("zpass") ? 1 : 0;
   const size_t need = inverse_scratch_bytes(P->N, b.P, b.nf);
   if (need > P->invscr.n) {
     admit(P, need - P->invscr.n);
@@ -1004,17 +1048,19 @@ void pair_set(bisp_plan* P, const float2* D00, bool unit, int gsets, const float
   const int nb = P->nb, nmult = P->nmult, nD = (int)P->dch.size();
   std::vector<int> all(nmult);
   for (int i = 0; i < nmult; ++i) all[i] = i;
+  std::vector<const TermList*> tl;
+  for (int i : all) tl.push_back(&P->terms[i]);
   auto pairs = [&](int nbu, std::vector<double>& res) {
     if (gsets > 1 && pair_split_gsets()) {
       // one launch per G set: outputs [gset][mult][b1][b2] as with a single launch
       res.clear();
       for (int gs = 0; gs < gsets; ++gs) {
         std::vector<double> part;
-        run_pair(P, all, 1, nD, gbase + (size_t)gs * nD * P->Ng, nbu, part, launches);
+        run_pair_terms(P, tl, 1, nD, gbase + (size_t)gs * nD * P->Ng, nbu, part, launches);
         res.insert(res.end(), part.begin(), part.end());
       }
     } else {
-      run_pair(P, all, gsets, nD, gbase, nbu, res, launches);
+      run_pair_terms(P, tl, gsets, nD, gbase, nbu, res, launches);
     }
   };
   if (nbk >= nb) {
@@ -1656,6 +1702,8 @@ void destroy(bisp_plan* P) {
 
 template <class F>
 bisp_status guarded(F&& f) {
+  g_alloc_calls = 0;
+  g_stalls_used = 0;
   try {
     f();
     return BISP_OK;
@@ -1765,13 +1813,46 @@ bisp_status bisp_measure_batch(bisp_plan* const* plans, const bisp_outputs* outs
       g_err = "bisp_measure_batch: plan " + std::to_string(i) + " is NULL";
       return BISP_EINVAL;
     }
-    const bisp_outputs& o = outs[i];
-    const bisp_status st = guarded([&] { do_measure(plans[i], o.B, o.shot, o.window, o.window_shot, o.nmodes); });
-    if (st != BISP_OK) {
-      g_err = "bisp_measure_batch: plan " + std::to_string(i) + ": " + g_err;
-      return st;
-    }
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) {
+        g_err = "bisp_measure_batch: plan " + std::to_string(i) + " repeats plan " + std::to_string(j);
+        return BISP_EINVAL;
+      }
   }
+  if (nplans == 0) return BISP_OK;
+  // Host worker threads measure the plans concurrently, each plan on its own stream, so that the
+  // GPU overlaps the small kernels and host round trips of many realisations.  Every launch
+  // carries its own job table, so plans share no device state.
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    g_err = "bisp_measure_batch: cudaGetDevice failed";
+    return BISP_ECUDA;
+  }
+  std::vector<int> st(nplans, BISP_OK);
+  std::vector<std::string> msg(nplans);
+  std::atomic<int> next{0};
+  auto work = [&] {
+    cudaSetDevice(dev);
+    for (int i = next++; i < nplans; i = next++) {
+      const bisp_outputs& o = outs[i];
+      st[i] = guarded([&] { do_measure(plans[i], o.B, o.shot, o.window, o.window_shot, o.nmodes); });
+      if (st[i] != BISP_OK) msg[i] = g_err;
+    }
+  };
+  const int nthr = std::min(nplans, kBatchThreads);
+  std::vector<std::thread> pool;
+  try {
+    for (int t = 1; t < nthr; ++t) pool.emplace_back(work);
+  } catch (const std::exception&) {
+    // fewer workers (the calling thread still takes part)
+  }
+  work();
+  for (auto& th : pool) th.join();
+  for (int i = 0; i < nplans; ++i)
+    if (st[i] != BISP_OK) {
+      g_err = "bisp_measure_batch: plan " + std::to_string(i) + ": " + msg[i];
+      return (bisp_status)st[i];
+    }
   return BISP_OK;
 }
 

@@ -355,30 +355,112 @@ def test_default_pair_kernel_is_mma_sync(monkeypatch):
 
 
 def test_measure_batch_matches_single_measures():
-    """bisp_measure_batch over independent realisations gives each plan's bisp_measure result
-    exactly, and reports a failing plan by index."""
-    N, L = 32, 1000.0
+    """bisp_measure_batch over independent realisations on meshes of two sizes (measured
+    concurrently by worker threads) gives each plan's bisp_measure result exactly, and reports a
+    failing plan by index."""
+    L = 1000.0
     kf = 2 * np.pi / L
     edges = kf * np.array([1.0, 2.5, 4.0, 5.5, 7.0])
-    p = E.Params(N=N, L=L, edges=edges, ells=[(0, 0, 0), (2, 0, 2)], los="global", mas=3, interlace=True)
     plans = []
     try:
-        for seed in (21, 22, 23):
+        for seed, N in ((21, 32), (22, 64), (23, 32), (24, 64), (25, 32)):
+            p = E.Params(N=N, L=L, edges=edges, ells=[(0, 0, 0), (2, 0, 2)], los="global", mas=3, interlace=True)
             pl = _plan(p)
             _assign(pl, 0, {"xyz": synthcat.periodic_catalog(N, L, 20_000, seed=seed)})
             plans.append(pl)
         single = [pl.measure() for pl in plans]
-        batch = bisp.measure_batch(plans)
-        for a, b in zip(single, batch):
-            for k in ("B", "shot", "nmodes"):
-                assert np.array_equal(a[k], b[k])
+        for _ in range(2):
+            batch = bisp.measure_batch(plans)
+            for a, b in zip(single, batch):
+                for k in ("B", "shot", "nmodes"):
+                    assert np.array_equal(a[k], b[k])
+        p = E.Params(N=32, L=L, edges=edges, ells=[(0, 0, 0), (2, 0, 2)], los="global", mas=3, interlace=True)
         empty = _plan(p)
-        plans.append(empty)
+        plans.insert(3, empty)
         with pytest.raises(bisp.BispError, match="BISP_ESTATE.*plan 3"):
             bisp.measure_batch(plans)
+        with pytest.raises(bisp.BispError, match="BISP_EINVAL.*repeats"):
+            bisp.measure_batch([plans[0], plans[0]])
     finally:
         for pl in plans:
             pl.close()
+
+
+def test_two_plans_from_two_host_threads():
+    """Two plans (a local-line-of-sight survey with window and a periodic box, different meshes)
+    driven at the same time from two host threads on their own streams give exactly the results
+    of measuring each alone: no launch of one plan reads the other's job tables."""
+    import threading
+
+    c = CASES["survey_local"]
+    kf = 2 * np.pi / c["L"]
+    gal, ran, obs = _survey(7, c["N"], c["L"], c["np_"], 4 * c["np_"])
+    ps = E.Params(N=c["N"], L=c["L"], edges=kf * np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5]), ells=c["ells"],
+                  los="local", observer=obs, mas=3, interlace=True, P0=1e4, window=True)
+    Lb = 1000.0
+    pb = E.Params(N=64, L=Lb, edges=2 * np.pi / Lb * np.array([1.0, 3.0, 5.0, 8.0, 12.0]),
+                  ells=[(0, 0, 0), (2, 0, 2), (2, 2, 2)], los="global", mas=2, interlace=False)
+    box = {"xyz": synthcat.periodic_catalog(64, Lb, 100_000, seed=31)}
+    with _plan(ps) as a, _plan(pb) as b:
+        _assign(a, 0, gal)
+        _assign(a, 1, ran)
+        _assign(b, 0, box)
+        ref = [a.measure(), b.measure()]
+        got = [[], []]
+
+        def run(i, pl):
+            for _ in range(4):
+                got[i].append(pl.measure())
+
+        th = [threading.Thread(target=run, args=(0, a)), threading.Thread(target=run, args=(1, b))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+    for i in range(2):
+        assert len(got[i]) == 4
+        for r in got[i]:
+            for k in ref[i]:
+                assert np.array_equal(r[k], ref[i][k]), (i, k)
+
+
+def test_covariance_of_gpu_batch_matches_oracle():
+    """Covariance of bispectrum multipoles over a batch of realisations measured on the GPU
+    (bisp_measure_batch) and formed by bisp_covariance (Sec. 5.5, Eq. Covariance) against the
+    oracle's covariance (oracle/stats.py) of the oracle's outputs on the same seeds; the
+    Hartlap-scaled chi^2 of one realisation (App. E) against both."""
+    from oracle import stats as ST
+
+    N, L = 32, 1000.0
+    kf = 2 * np.pi / L
+    edges = kf * np.array([1.0, 2.5, 4.0, 5.5])
+    p = E.Params(N=N, L=L, edges=edges, ells=[(0, 0, 0), (2, 0, 2)], los="global", mas=3, interlace=True)
+    seeds = list(range(300, 320))
+    cats = [{"xyz": synthcat.periodic_catalog(N, L, 20_000, seed=s)} for s in seeds]
+    plans = []
+    try:
+        for cat in cats:
+            pl = _plan(p)
+            _assign(pl, 0, cat)
+            plans.append(pl)
+        outs = bisp.measure_batch(plans)
+    finally:
+        for pl in plans:
+            pl.close()
+    iu = np.triu_indices(len(edges) - 1)
+    vec = lambda B: np.concatenate([B[0][iu], np.diagonal(B[1])])  # B000 on k1 <= k2, B202 on k1 = k2
+    Xg = np.array([vec(o["B"]) for o in outs])
+    Xo = np.array([vec(E.measure(p, cat, None)["B"]) for cat in cats])
+    cg = bisp.covariance(Xg, n_par=2)
+    mo, co, ro = ST.covariance(Xo)
+    sd = np.sqrt(np.diag(co))
+    assert np.all(np.abs(cg["mean"] - mo) <= 1e-4 * np.abs(Xo).max(axis=0))
+    assert np.all(np.abs(cg["cov"] - co) <= 1e-3 * np.outer(sd, sd))
+    assert np.all(np.abs(cg["corr"] - ro) <= 2e-3)
+    x_th = mo
+    assert bisp.chi2(cg["cov"], len(seeds), Xg[0], cg["mean"]) == pytest.approx(
+        ST.chi2(co, len(seeds), Xo[0], x_th), rel=1e-2)
+    assert cg["hartlap"] == pytest.approx(ST.hartlap(len(seeds), Xg.shape[1]), rel=1e-12)
 
 
 def test_cfg1_box_64_cic_fp():
