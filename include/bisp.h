@@ -109,6 +109,12 @@ typedef struct {
                               signal-to-noise study rests on (Sec. 4.4, Sec. 5.6); every other
                               output is NaN.  When the shell fields of all bins do not fit,
                               each block of bins is then measured alone, with no block pairs. */
+  int los_object;          /* object of the triplet whose line of sight x_hat carries the
+                              y_L^{M*} weight (App. B): 0 or 3 = x3 (the main text's choice),
+                              1 = x1 (the k1 object), 2 = x2 (the k2 object); the shot-noise terms
+                              follow the object that carries the weight.  Local line of sight,
+                              BISP_BISPECTRUM and BISP_FP32 only (otherwise BISP_EUNSUPPORTED); with
+                              the global line of sight every choice gives the same result. */
 } bisp_params;
 
 /* Create a plan.  Validates params (BISP_EINVAL names the offending field), computes the
@@ -260,6 +266,10 @@ typedef struct {
                               1 mma.sync TF32 (default), 2 tcgen05 TF32 (BISP_PAIR_KERNEL=tcgen05
                               in the environment, for jobs it covers), 3 FP64 unfused mesh sums
                               (BISP_FP64 plans) */
+  int zpass_groups;        /* row groups per CTA of the inverse transforms' z pass, chosen by timing
+                              the candidates on the plan's largest shell batch at its first
+                              measurement (every value gives the same fields); 0 before that.
+                              BISP_ZGROUPS=n in the environment fixes it without timing. */
 } bisp_plan_info;
 
 bisp_status bisp_plan_query(const bisp_plan* plan, bisp_plan_info* info);

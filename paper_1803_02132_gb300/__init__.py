@@ -38,7 +38,7 @@ class _Params(C.Structure):
                 ("nbins", C.c_int), ("ells", C.POINTER(C.c_int)), ("n_mult", C.c_int), ("los", C.c_int),
                 ("observer", C.c_double * 3), ("mas", C.c_int), ("interlace", C.c_int), ("fkp_P0", C.c_double),
                 ("max_device_bytes", C.c_size_t), ("want_window", C.c_int), ("precision", C.c_int),
-                ("estimator", C.c_int), ("diagonal_only", C.c_int)]
+                ("estimator", C.c_int), ("diagonal_only", C.c_int), ("los_object", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -47,7 +47,7 @@ class _Info(C.Structure):
                 ("n_data", C.c_int64), ("n_randoms", C.c_int64), ("device_bytes", C.c_size_t),
                 ("kernel_launches", C.c_int), ("ms_assign_data", C.c_double), ("ms_assign_randoms", C.c_double),
                 ("ms_measure", C.c_double), ("ms_pair", C.c_double), ("pair_bytes", C.c_double),
-                ("pair_launches", C.c_int), ("pair_kernel", C.c_int)]
+                ("pair_launches", C.c_int), ("pair_kernel", C.c_int), ("zpass_groups", C.c_int)]
 
 
 def _load():
@@ -128,10 +128,11 @@ class Plan:
 
     def __init__(self, nmesh, box_len, k_edges, ells, los="global", observer=(0.0, 0.0, 0.0), mas="TSC",
                  interlace=False, fkp_P0=0.0, want_window=False, max_device_bytes=0, stream=None,
-                 precision="fp32", estimator="bispectrum", diagonal_only=False):
+                 precision="fp32", estimator="bispectrum", diagonal_only=False, los_object=3):
         """k_edges: k-bin edges [h/Mpc] for the bispectrum, r-bin edges [Mpc/h] for the
         three-point function (estimator="threept"; measure() then returns zeta as "B" and the
-        window multipoles Q as "window")."""
+        window multipoles Q as "window").  los_object: 3 (default), 1 or 2, the object whose line
+        of sight carries the y_L^{M*} weight (App. B)."""
         self._edges = np.ascontiguousarray(k_edges, dtype=np.float64)
         self._ells = np.ascontiguousarray(np.asarray(ells, dtype=np.int32).reshape(-1))
         p = _Params()
@@ -152,6 +153,7 @@ class Plan:
         p.precision = PRECISION[precision] if precision in PRECISION else int(precision)
         p.estimator = ESTIMATOR[estimator] if estimator in ESTIMATOR else int(estimator)
         p.diagonal_only = 1 if diagonal_only else 0
+        p.los_object = int(los_object)
         self.nbins = p.nbins
         self.want_window = bool(want_window)
         self.n_mult = p.n_mult

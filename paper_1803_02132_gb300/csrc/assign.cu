@@ -383,11 +383,14 @@ __global__ void __launch_bounds__(DT_THREADS) k_deposit(const uint32_t* __restri
                                                         const float* __restrict__ vals, int64_t n, int N,
                                                         int nchan, float* mesh0, float* mesh1) {
   using T = DepTile<P, ILV>;
-  constexpr int OLO = T::OLO, OHI = T::OHI, RY = T::RY, RZ = T::RZ, NCELL = T::NCELL;
-  constexpr int MAXP = NC <= 12 ? 512 : 384;  // particles per staged batch (static smem < 48 KB)
-  __shared__ uint32_t s_gs[NCELL];            // first sorted index of each halo cell
-  __shared__ uint32_t s_ts[NCELL + 1];        // position of each halo cell in the tile list
-  __shared__ float4 s_frac[MAXP];
+  constexpr int OLO = T::OLO, OHI = T::OHI, W = T::W, RY = T::RY, RZ = T::RZ, NCELL = T::NCELL;
+  // mesh 0's weight vanishes for every offset in the particle's cell once an offset exceeds O0HI
+  constexpr int O0HI = (P == 3) ? 1 : 0;
+  constexpr int NW = ILV ? 6 : 3;              // per-axis weight tables per staged particle
+  constexpr int MAXP = NC <= 12 ? 256 : 224;   // particles per staged batch (static smem < 48 KB)
+  __shared__ uint32_t s_gs[NCELL];             // first sorted index of each halo cell
+  __shared__ uint32_t s_ts[NCELL + 1];         // position of each halo cell in the tile list
+  __shared__ float s_w[NW][W][MAXP];           // 1D weights W_p(o + d) (mesh 0), W_p(o + d - 1/2) (mesh 1)
   __shared__ float s_val[NC][MAXP];
   __shared__ uint32_t s_wsum[DT_THREADS / 32];
   __shared__ int s_any;
@@ -475,30 +478,46 @@ __global__ void __launch_bounds__(DT_THREADS) k_deposit(const uint32_t* __restri
           else hi = mid - 1;
         }
         const uint32_t g = s_gs[lo] + (q - s_ts[lo]);
-        s_frac[q - b0] = frac[g];
+        const float4 d = frac[g];
+        // 1D weights of this particle for every offset o (distance particle - node = o + d)
+#pragma unroll
+        for (int o = OLO; o <= OHI; ++o) {
+          const float tx_ = (float)o + d.x, ty_ = (float)o + d.y, tz_ = (float)o + d.z;
+          s_w[0][o - OLO][q - b0] = wker<P>(tx_);
+          s_w[1][o - OLO][q - b0] = wker<P>(ty_);
+          s_w[2][o - OLO][q - b0] = wker<P>(tz_);
+          if (ILV) {
+            s_w[NW - 3][o - OLO][q - b0] = wker<P>(tx_ - 0.5f);
+            s_w[NW - 2][o - OLO][q - b0] = wker<P>(ty_ - 0.5f);
+            s_w[NW - 1][o - OLO][q - b0] = wker<P>(tz_ - 0.5f);
+          }
+        }
 #pragma unroll
         for (int k = 0; k < NC; ++k)
           if (k < nchan) s_val[k][q - b0] = vals[(size_t)k * n + g];
       }
       __syncthreads();
+      // every (ox, oy, oz) in increasing order, each cell's particles in sorted order
+#pragma unroll
       for (int ox = OLO; ox <= OHI; ++ox) {
+#pragma unroll
         for (int oy = OLO; oy <= OHI; ++oy) {
           const int rbase = ((lx + ox - OLO) * RY + (ly + oy - OLO)) * RZ + (lz - OLO);
+#pragma unroll
           for (int oz = OLO; oz <= OHI; ++oz) {
+            const bool m0 = ox <= O0HI && oy <= O0HI && oz <= O0HI;  // else mesh 0's weight is 0
             const int c = rbase + oz;
             const uint32_t p0 = max(s_ts[c], b0), p1 = min(s_ts[c + 1], b1);
             for (uint32_t q = p0; q < p1; ++q) {
-              const float4 d = s_frac[q - b0];
-              // distance particle - node along each axis: (h - c) + d
-              const float tx_ = (float)ox + d.x, ty_ = (float)oy + d.y, tz_ = (float)oz + d.z;
-              const float w0 = wker<P>(tx_) * wker<P>(ty_) * wker<P>(tz_);
-              float w1 = 0.f;
-              if (ILV) w1 = wker<P>(tx_ - 0.5f) * wker<P>(ty_ - 0.5f) * wker<P>(tz_ - 0.5f);
+              const uint32_t i = q - b0;
+              float w0 = 0.f, w1 = 0.f;
+              if (m0) w0 = s_w[0][ox - OLO][i] * s_w[1][oy - OLO][i] * s_w[2][oz - OLO][i];
+              if (ILV) w1 = s_w[NW - 3][ox - OLO][i] * s_w[NW - 2][oy - OLO][i] * s_w[NW - 1][oz - OLO][i];
 #pragma unroll
               for (int k = 0; k < NC; ++k) {
                 if (k < nchan) {
-                  const float v = s_val[k][q - b0];
-                  a0[k] = fmaf(w0, v, a0[k]);
+                  const float v = s_val[k][i];
+                  if (m0) a0[k] = fmaf(w0, v, a0[k]);
                   if (ILV) a1[k] = fmaf(w1, v, a1[k]);
                 }
               }

@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(const __grid_constant__ In
   const int jy = sy & (N - 1);
   // shell batches: every field filters the same spectrum over the same shell, so the spectrum
   // values and the shell mask are loaded once, before the field loop
-  const bool shell = B.f[0].kind == SRC_SHELL;
+  const bool shell = B.f[0].kind == SRC_SHELL || B.f[0].kind == SRC_SHELL_SUM;
   float2 av[EPT];
   unsigned inmask = 0;
   if (shell) {
@@ -294,7 +294,8 @@ __global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(const __grid_constant__ In
         const long long q = (long long)sx * sx + (long long)sy * sy + (long long)nz * nz;
         if (q >= B.qlo && q < B.qhi) {
           inmask |= 1u << k;
-          av[k] = B.f[0].unit ? make_float2(1.f, 0.f) : B.f[0].A[((size_t)e * N + jy) * NH + nz];
+          if (B.f[0].kind == SRC_SHELL)
+            av[k] = B.f[0].unit ? make_float2(1.f, 0.f) : B.f[0].A[((size_t)e * N + jy) * NH + nz];
         }
       }
     }
@@ -310,10 +311,25 @@ __global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(const __grid_constant__ In
           const int l = i % LB, e = i / LB;
           const int nz = nz0 + l;
           const int sx = sgn_idx(e, N);
-          const float2 y = ylm_one(F.l, F.m, (float)sx, (float)sy, (float)nz, B.ynorm);
-          // part of y_l^{m*}: Re y or -Im y, times (-i)^l
-          const float c = (F.part ? -y.y : y.x) * B.inv_nmodes;
-          const float2 t = make_float2(av[k].x * c, av[k].y * c);
+          float2 t;
+          if (F.kind == SRC_SHELL_SUM) {
+            // sum over (m, part, channel) entries of part(y_l^{m*}) S(k), then / N_mode
+            const size_t gi = ((size_t)e * N + jy) * NH + nz;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int q = 0; q < F.ne; ++q) {
+              const float2 y = ylm_one(F.l, F.em[q], (float)sx, (float)sy, (float)nz, B.ynorm);
+              const float c = F.ecoef[q] * (F.epart[q] ? -y.y : y.x);
+              const float2 a = B.spec[F.espec[q]][gi];
+              acc.x = fmaf(c, a.x, acc.x);
+              acc.y = fmaf(c, a.y, acc.y);
+            }
+            t = make_float2(acc.x * B.inv_nmodes, acc.y * B.inv_nmodes);
+          } else {
+            const float2 y = ylm_one(F.l, F.m, (float)sx, (float)sy, (float)nz, B.ynorm);
+            // part of y_l^{m*}: Re y or -Im y, times (-i)^l
+            const float c = (F.part ? -y.y : y.x) * B.inv_nmodes;
+            t = make_float2(av[k].x * c, av[k].y * c);
+          }
           switch (F.l & 3) {
             case 0: v = t; break;
             case 1: v = make_float2(t.y, -t.x); break;
@@ -418,7 +434,7 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const __grid_constant__ InvBa
   const InvGeo g = inv_geo(N, Bt.P, Geo<N>::LB);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(tin + 2 * ROWS * g.Pz);
   const int f = blockIdx.y;
-  constexpr int GROUPS = RegZ<N>::GROUPS;
+  const int GROUPS = Bt.zgroups;  // row groups per CTA (a power of two; tuned by the plan)
   const unsigned tile_bytes = (unsigned)(ROWS * g.Pz * sizeof(float2));
   const float2* src0 = t2all + (size_t)f * g.t2 + (size_t)blockIdx.x * GROUPS * ROWS * g.Pz;
   const unsigned bar0 = fft_su32(bars);
@@ -581,6 +597,23 @@ __global__ void __launch_bounds__(RegL<N>::THREADS) k_inv_y_reg(const __grid_con
   regl_finish<N, +1>(s, l, a, [&](int m, float2 u) { t2[(size_t)m * g.Pz] = u; });
 }
 
+int inverse_zgroups(int N, int requested) {
+  int rows = 0, def = 8;
+  switch (N) {
+    case 16: rows = RegZ<16>::ROWS; def = RegZ<16>::GROUPS; break;
+    case 32: rows = RegZ<32>::ROWS; def = RegZ<32>::GROUPS; break;
+    case 64: rows = RegZ<64>::ROWS; def = RegZ<64>::GROUPS; break;
+    case 128: rows = RegZ<128>::ROWS; def = RegZ<128>::GROUPS; break;
+    case 256: rows = RegZ<256>::ROWS; def = RegZ<256>::GROUPS; break;
+    case 512: rows = RegZ<512>::ROWS; def = RegZ<512>::GROUPS; break;
+    default: rows = RegZ<1024>::ROWS; def = RegZ<1024>::GROUPS; break;
+  }
+  int groups = requested > 0 ? requested : def;
+  while (groups > 1 && (groups & (groups - 1))) groups &= groups - 1;
+  if (groups > N * N / rows) groups = N * N / rows;
+  return groups;
+}
+
 template <int N>
 static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStream_t s, int* launches) {
   using G = Geo<N>;
@@ -598,7 +631,12 @@ static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStr
   using RZ = RegZ<N>;
   const size_t zs = RZ::smem(g.Pz);
   smem_attr(k_inv_z_reg<N>, RZ::smem(N / 2));
-  k_inv_z_reg<N><<<dim3(N * N / (RZ::ROWS * RZ::GROUPS), b.nf), 256, zs, s>>>(b, t2, tw, b.err);
+  // row groups per CTA: the plan's tuned value, else the default; a power of two that divides
+  // the N^2 / ROWS row groups
+  const int groups = inverse_zgroups(N, b.zgroups);
+  InvBatch bz = b;
+  bz.zgroups = groups;
+  k_inv_z_reg<N><<<dim3(N * N / (RZ::ROWS * groups), b.nf), 256, zs, s>>>(bz, t2, tw, b.err);
   BISP_CHECK_LAUNCH();
   if (launches) *launches += 3;
 }

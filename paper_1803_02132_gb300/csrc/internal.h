@@ -97,26 +97,34 @@ void forward_fft(float* mesh0, float* mesh1, int count, int N, int mas, const fl
 // 32nd roots of unity for the in-register DFTs (once per process)
 
 // Inverse transforms from half spectra to real fields, pruned to |n_i| <= P.
-enum SrcKind { SRC_PLAIN = 0, SRC_QSHOT = 1, SRC_SHELL = 2, SRC_KERNEL = 3 };
+enum SrcKind { SRC_PLAIN = 0, SRC_QSHOT = 1, SRC_SHELL = 2, SRC_KERNEL = 3, SRC_SHELL_SUM = 4 };
+constexpr int INV_MAXE = 20;  // entries of one SRC_SHELL_SUM field
 struct InvField {
   // SRC_PLAIN:  spec(k) = scale * A(k)
   // SRC_QSHOT:  spec(k) = scale * (A(k) conj(B(k)) - sbar * cw2(k))
   // SRC_SHELL:  spec(k) = mask_b(k)/Nm * (-i)^l * part(y_l^{m*}(k)) * (A(k) or 1)
   // SRC_KERNEL: spec(k) = conj(K(k)) * (A(k) or 1), K the forward FFT of a real separation
   //             kernel (three-point function); every mode but the Nyquist planes
+  // SRC_SHELL_SUM: spec(k) = mask_b(k)/Nm * (-i)^l * sum_e ecoef[e] part_e(y_l^{m_e*}(k)) S_e(k),
+  //             S_e = InvBatch::spec[espec[e]], m_e = em[e] >= 0, part_e = epart[e]: one real field
+  //             of a contraction over (m, channel) done in k space
   int kind;
   const float2* A;
   const float2* B;
   const float2* K;
   float sbar;
   float scale;
-  int l, m, part, unit;   // SRC_SHELL
+  int l, m, part, unit;   // SRC_SHELL (l also SRC_SHELL_SUM)
+  int ne;                 // SRC_SHELL_SUM entries
+  float ecoef[INV_MAXE];
+  signed char em[INV_MAXE], epart[INV_MAXE], espec[INV_MAXE];
   float* out;             // real field [N][N][N]
 };
 struct InvBatch {
   int N, P;               // prune extent: modes with |nx|,|ny|,nz <= P
   int nf;                 // number of fields (<= 32)
   InvField f[32];
+  const float2* spec[16]; // spectra of the SRC_SHELL_SUM entries
   // shell geometry (SRC_SHELL)
   long long qlo, qhi;     // |n|^2 in [qlo, qhi)
   float inv_nmodes;
@@ -125,7 +133,10 @@ struct InvBatch {
   int interlace;
   int* err;               // set (never cleared) when a bounded wait gives up
   int stall;              // test knob: the z pass starts no row-group copy (its waits run out)
+  int zgroups;            // z pass: row groups per CTA (0: the default); any value gives the same fields
 };
+// row groups per CTA that inverse_fft's z pass would use for a requested value at mesh N
+int inverse_zgroups(int N, int requested);
 size_t inverse_scratch_bytes(int N, int P, int nf);
 
 // Separation kernels of one r-bin (three-point function, Sec. 4.3): mesh c of `mesh`
@@ -148,9 +159,12 @@ void inverse_fft(const InvBatch& b, const float2* tw, void* scratch, cudaStream_
 void launch_axpby(float2* out, const float2* x, double a, const float2* y, double b, size_t n,
                   int zero_k0, cudaStream_t s);
 
+// Z = (1/N_mode) sum_shell y_l^{m*}(k) [X(k) conj(N(k)) - Sbar C(k)/W^2(k)], with X = XR + i XI
+// and N = NR + i NI combinations of the spectra of real channel meshes
 struct ZsumArgs {
-  const float2* D00;      // delta n spectrum
-  const float2* NR;       // N_L^M real-part channel spectrum
+  const float2* XR;       // delta n spectrum of the distinct object (real-part channel)
+  const float2* XI;       // imaginary-part channel or nullptr
+  const float2* NR;       // N spectrum of the coincident pair (real-part channel)
   const float2* NI;       // imaginary-part channel or nullptr (M = 0)
   double sbar_re, sbar_im;
   int N, P;
@@ -207,8 +221,11 @@ struct PairJob {
   PairRecipe rec[512];
 };
 // Result: out[o][b1][b2] = sum_x sum_{t in o} X_t(x;b1) Y_t(x;b2)   (FP64)
+// ev0 / ev1 (optional) are recorded right before the contraction kernel and after the final
+// reduction kernel: their interval is the device time of the two kernels alone
 void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scratch_bytes,
-                 cudaStream_t s, int* launches, int* kernel = nullptr);
+                 cudaStream_t s, int* launches, int* kernel = nullptr, cudaEvent_t ev0 = nullptr,
+                 cudaEvent_t ev1 = nullptr);
 size_t pair_scratch_bytes(const PairJob& job);
 // true when one launch of some contraction kernel covers the job (terms, tables, shared memory)
 bool pair_fits(const PairJob& job);

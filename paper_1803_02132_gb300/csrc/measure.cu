@@ -70,21 +70,23 @@ __global__ void __launch_bounds__(ZS_THREADS) k_zsum(const __grid_constant__ Zsu
     const int sx = (int)(code & 1023u) - 512, sy = (int)((code >> 10) & 1023u) - 512, nz = (int)(code >> 20);
     const int jx = sx & (N - 1), jy = sy & (N - 1);
     const size_t gi = ((size_t)jx * N + jy) * NH + nz;
-    const float2 d = A.D00[gi];
+    const float2 xr = A.XR[gi];
+    const float2 xi = A.XI ? A.XI[gi] : make_float2(0.f, 0.f);
     const float2 nr = A.NR[gi];
     const float2 ni = A.NI ? A.NI[gi] : make_float2(0.f, 0.f);
-    // N(k) = NR + i NI ; N(-k) = conj(NR) + i conj(NI)
+    // X(k) = XR + i XI, X(-k) = conj(XR) + i conj(XI); the same for N (spectra of real meshes)
+    const float xkr = xr.x - xi.y, xki = xr.y + xi.x;
+    const float xmr = xr.x + xi.y, xmi = xi.x - xr.y;
     const float nkr = nr.x - ni.y, nki = nr.y + ni.x;
     const float nmr = nr.x + ni.y, nmi = ni.x - nr.y;
     float cw = A.cw2_1d[jx] * A.cw2_1d[jy] * A.cw2_1d[nz];
     if (A.interlace) cw = 0.5f * (cw + A.cw2_1d[N + jx] * A.cw2_1d[N + jy] * A.cw2_1d[N + nz]);
-    // T(k) = D(k) conj(N(k)) - Sbar C/W^2
-    const float dr = d.x, di = d.y;
-    const float tkr = fmaf(dr, nkr, fmaf(di, nki, -sr * cw));
-    const float tki = fmaf(di, nkr, fmaf(-dr, nki, -si * cw));
-    // T(-k) = conj(D(k)) conj(N(-k)) - Sbar C/W^2
-    const float tmr = fmaf(dr, nmr, fmaf(-di, nmi, -sr * cw));
-    const float tmi = fmaf(-di, nmr, fmaf(-dr, nmi, -si * cw));
+    // T(k) = X(k) conj(N(k)) - Sbar C/W^2
+    const float tkr = fmaf(xkr, nkr, fmaf(xki, nki, -sr * cw));
+    const float tki = fmaf(xki, nkr, fmaf(-xkr, nki, -si * cw));
+    // T(-k) = X(-k) conj(N(-k)) - Sbar C/W^2
+    const float tmr = fmaf(xmr, nmr, fmaf(xmi, nmi, -sr * cw));
+    const float tmi = fmaf(xmi, nmr, fmaf(-xmr, nmi, -si * cw));
     const bool pair = nz > 0;
 #pragma unroll
     for (int t = 0; t < ZS_MAXLM; ++t) {

@@ -84,7 +84,22 @@ static PairLaunch pair_launch_cfg(const PairJob& j) {
 
 // merge terms equal up to a scalar, then classify the sides of every term: bare component
 // field (read in place) or built
-static PairJob classify(const PairJob& job) {
+static PairJob classify_impl(const PairJob& job);
+
+// classify() of the last job seen by this thread, kept so that the fit check, the scratch size
+// and the launch of one job classify it once (the tables are a few tens of KB of host work)
+static const PairJob& classify(const PairJob& job) {
+  thread_local PairJob last_in, last_out;
+  thread_local bool valid = false;
+  if (valid && std::memcmp(&last_in, &job, sizeof(PairJob)) == 0) return last_out;
+  valid = false;
+  last_out = classify_impl(job);
+  last_in = job;
+  valid = true;
+  return last_out;
+}
+
+static PairJob classify_impl(const PairJob& job) {
   PairJob j = job;
   {
     // normalised term: a single-entry X side (c, g, coef) with a bare Y side is coef times
@@ -424,6 +439,7 @@ struct TmaLayout {
   unsigned tx;        // transaction bytes per stage
   int ncomp, gbox;    // F blocks per half, G rows
   int stall;          // test knob: start no stage copy, so that every bounded wait runs out
+  unsigned tab;       // offset of the side and H-row tables copied from the job
 };
 
 constexpr int TMA_MAXWARP = 20;  // two warps (row halves) per term and cell half
@@ -544,6 +560,15 @@ __global__ void __launch_bounds__(NTHR, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
+  // the tables the inner loops read (warp-uniform addresses: shared-memory broadcasts): side
+  // entries as (component block offset, H row offset), H-row bounds, H entries (g, coef)
+  const int nse = J.s_off[J.nslot], nhe = J.h_off[J.nh];
+  int2* const s_se = reinterpret_cast<int2*>(gb + L.tab);
+  int* const s_ho = reinterpret_cast<int*>(s_se + nse);
+  int2* const s_he = reinterpret_cast<int2*>(gb + ((L.tab + (unsigned)nse * 8u + (unsigned)(J.nh + 1) * 4u + 7u) & ~7u));
+  for (int i = tid; i < nse; i += blockDim.x) s_se[i] = make_int2(J.s_ent[i][0] * 4096, J.s_ent[i][1] * PR_CH);
+  for (int i = tid; i <= J.nh; i += blockDim.x) s_ho[i] = J.h_off[i];
+  for (int i = tid; i < nhe; i += blockDim.x) s_he[i] = make_int2(J.h_ent[i].g, __float_as_int(J.h_ent[i].coef));
   __syncthreads();
   auto issue = [&](int64_t ch, int st) {  // thread 0 only
     if (L.stall) return;
@@ -560,9 +585,11 @@ __global__ void __launch_bounds__(NTHR, 1)
   float2* slot = reinterpret_cast<float2*>(partials) + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * 16;
 #pragma unroll
   for (int q = 0; q < 16; ++q) slot[q] = make_float2(0.f, 0.f);
-  float run[16];
+  // MMA accumulators: FP32 sums over at most PR_FLUSH chunks (1024 cells), then added with
+  // Kahan compensation to the lane's (sum, compensation) slots
+  float c[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) run[q] = 0.f;
+  for (int q = 0; q < 16; ++q) c[q] = 0.f;
 
   // ldmatrix rows of this lane: matrix j = lane/8, row r = lane%8 of that matrix; every
   // fragment row is congruent to r mod 8, so its swizzled piece is (piece ^ r).
@@ -594,10 +621,6 @@ __global__ void __launch_bounds__(NTHR, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(ch + gridDim.x, st ^ 1);
     }
-    // slot it % 16 is flushed at the end of this chunk; load it now so that the L2 round
-    // trip overlaps the chunk's work
-    const int fg = it & 15;
-    float2 pre = slot[fg];
     if (!mbar_wait_bounded(bar0 + 8u * st, (unsigned)(it >> 1) & 1u)) {
       s_abort = 1;
       atomicExch(err, 1);
@@ -608,19 +631,20 @@ __global__ void __launch_bounds__(NTHR, 1)
       const int h = i >> 4, q = i & 15, hh = q >> 3, p = q & 7;
       const unsigned char* g0 = gb + sbo + hh * L.half + L.fsz;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int e = J.h_off[h]; e < J.h_off[h + 1]; ++e) {
-        const PairRecipe R = J.h_ent[e];
-        if (R.g >= 0) {
-          const float4 gv = *reinterpret_cast<const float4*>(g0 + swz(R.g, p));
-          v.x = fmaf(R.coef, gv.x, v.x);
-          v.y = fmaf(R.coef, gv.y, v.y);
-          v.z = fmaf(R.coef, gv.z, v.z);
-          v.w = fmaf(R.coef, gv.w, v.w);
+      for (int e = s_ho[h]; e < s_ho[h + 1]; ++e) {
+        const int2 R = s_he[e];
+        const float coef = __int_as_float(R.y);
+        if (R.x >= 0) {
+          const float4 gv = *reinterpret_cast<const float4*>(g0 + swz(R.x, p));
+          v.x = fmaf(coef, gv.x, v.x);
+          v.y = fmaf(coef, gv.y, v.y);
+          v.z = fmaf(coef, gv.z, v.z);
+          v.w = fmaf(coef, gv.w, v.w);
         } else {
-          v.x += R.coef;
-          v.y += R.coef;
-          v.z += R.coef;
-          v.w += R.coef;
+          v.x += coef;
+          v.y += coef;
+          v.z += coef;
+          v.w += coef;
         }
       }
       // cells 4p..4p+3 of half hh: step kk = p/2, slot s = p%2 of the pairs of lanes tq = 0..3
@@ -633,9 +657,6 @@ __global__ void __launch_bounds__(NTHR, 1)
     __syncthreads();
     if (s_abort) break;
     // (2) this warp's 16 x 32 block of its term over its cell half (or both halves)
-    float c[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) c[q] = 0.f;
     for (int hh = hfirst; hh < hlast; ++hh) {
       const unsigned fh = base + sbo + hh * L.half;
       const float* hr = Hs + hh * 32 + 2 * tq;
@@ -647,8 +668,9 @@ __global__ void __launch_bounds__(NTHR, 1)
           float s4[4] = {0.f, 0.f, 0.f, 0.f};
           for (int e = e0; e < e1; ++e) {
             uint32_t v[4];
-            ldsm_x4(fh + (unsigned)J.s_ent[e][0] * 4096u + loffA + poffA[kk], v);
-            const float2 hv = *reinterpret_cast<const float2*>(hr + J.s_ent[e][1] * PR_CH + 8 * kk);
+            const int2 se = s_se[e];
+            ldsm_x4(fh + (unsigned)se.x + loffA + poffA[kk], v);
+            const float2 hv = *reinterpret_cast<const float2*>(hr + se.y + 8 * kk);
             s4[0] = fmaf(__uint_as_float(v[0]), hv.x, s4[0]);
             s4[1] = fmaf(__uint_as_float(v[1]), hv.x, s4[1]);
             s4[2] = fmaf(__uint_as_float(v[2]), hv.y, s4[2]);
@@ -677,26 +699,22 @@ __global__ void __launch_bounds__(NTHR, 1)
         for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
       }
     }
+    // every PR_FLUSH chunks the accumulators go to the compensated slots and restart
+    if ((it & (PR_FLUSH - 1)) == PR_FLUSH - 1) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) run[q] += c[q];
-    // round-robin flush: each FP32 running sum covers at most 16 chunks (1024 cells)
-    {
-      float x = 0.f;
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (q == fg) {
-          x = run[q];
-          run[q] = 0.f;
-        }
-      kahan_add(pre, x);
-      slot[fg] = pre;
+      for (int q = 0; q < 16; ++q) {
+        float2 v = slot[q];
+        kahan_add(v, c[q]);
+        slot[q] = v;
+        c[q] = 0.f;
+      }
     }
     __syncthreads();
   }
-  // the running sums not flushed since their last turn
+  // the sums of the chunks since the last flush
   if (!s_abort) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) kahan_add(slot[q], run[q]);
+    for (int q = 0; q < 16; ++q) kahan_add(slot[q], c[q]);
   }
   // after an abort the prefetched stage may still be in flight: wait for it (bounded)
   if (tid == 0 && s_abort) mbar_wait_bounded(bar0 + 8u * ((it + 1) & 1), (unsigned)((it + 1) >> 1) & 1u);
@@ -1009,8 +1027,13 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   const size_t fsz = (size_t)j.ncomp * 4096, gsz = r1024((size_t)j.ng * 128);
   const size_t half = fsz + gsz, stage = 2 * half, hs = 2 * stage;
   const size_t bar = (hs + (size_t)j.nh * PR_CH * 4 + 15) / 16 * 16;
-  const size_t bytes = bar + 16 + 1024;
+  // tables read in the inner loops, copied to shared memory: side entries (int2 each), H-row
+  // offsets, H entries (g, coef)
+  const size_t tab = bar + 16;
+  const size_t tabsz = (size_t)j.s_off[j.nslot] * 8 + (size_t)(j.nh + 1) * 4 + (size_t)j.h_off[j.nh] * 8 + 16;
+  const size_t bytes = tab + tabsz + 1024;
   if (bytes > 227 * 1024 - 256) return false;
+  L->tab = (unsigned)tab;
   L->fsz = (unsigned)fsz;
   L->gsz = (unsigned)gsz;
   L->half = (unsigned)half;
@@ -1193,7 +1216,7 @@ static int pair_blocks() {
 
 bool pair_fits(const PairJob& job) {
   try {
-    const PairJob j = classify(job);
+    const PairJob& j = classify(job);
     TmaLayout L;
     int ksplit = 1, warps = 1;
     if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) return true;
@@ -1207,7 +1230,7 @@ bool pair_fits(const PairJob& job) {
 }
 
 size_t pair_scratch_bytes(const PairJob& job) {
-  const PairJob j = classify(job);
+  const PairJob j = classify(job);  // a copy: the memo may be refilled below
   if (pair_use_tc(j) && pair_use_umma()) {
     PairJob jt = normalised(j);
     UmmaPlan U;
@@ -1276,8 +1299,11 @@ __global__ void k_pair_final(const __grid_constant__ PairJob J, const double* pa
 }
 
 void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scratch_bytes, cudaStream_t s,
-                 int* launches, int* kernel) {
+                 int* launches, int* kernel, cudaEvent_t ev0, cudaEvent_t ev1) {
   const PairJob j = classify(job);
+  auto mark = [&](cudaEvent_t e) {
+    if (e) BISP_CUDA(cudaEventRecord(e, s));
+  };
   if (scratch_bytes < pair_scratch_bytes(job)) throw Error{2, "pair reduction scratch too small"};
   if (j.Ng % PR_CH) throw Error{6, "mesh size not a multiple of the chunk"};
   double* partials = reinterpret_cast<double*>(scratch);
@@ -1294,11 +1320,13 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
       const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb);
       const CUtensorMap mg = g_map(j.gfields, j.Ng, j.ng);
       BISP_CUDA(cudaFuncSetAttribute(k_pair_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UL.bytes));
+      mark(ev0);
       k_pair_umma<<<nblk, UM_WARPS * 32, UL.bytes, s>>>(jt, U, mf, mg, UL, slots, err);
       BISP_CHECK_LAUNCH();
       const int nout = j.nout * j.nb * j.nb;
       k_pair_umma_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(jt, slots, nblk, j.nb, j.nout, out_dev);
       BISP_CHECK_LAUNCH();
+      mark(ev1);
       int herr = 0;
       BISP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
       BISP_CUDA(cudaStreamSynchronize(s));
@@ -1322,12 +1350,14 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
     L.stall = inject_stall("pair") ? 1 : 0;
     BISP_CUDA(cudaFuncSetAttribute(k_pair_tma<32 * TMA_MAXWARP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)L.bytes));
+    mark(ev0);
     k_pair_tma<32 * TMA_MAXWARP><<<nblk, warps * 32, L.bytes, s>>>(jt, mf, mg, L, ksplit, partials, err);
     BISP_CHECK_LAUNCH();
     const int nout = j.nout * j.nb * j.nb;
     k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(jt, partials, nblk, warps, ksplit, j.nb, j.nout,
                                                                out_dev);
     BISP_CHECK_LAUNCH();
+    mark(ev1);
     int herr = 0;
     BISP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     BISP_CUDA(cudaStreamSynchronize(s));
@@ -1349,6 +1379,7 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
 #define BISP_PAIR_S(A, B) \
   if (!launched) BISP_PAIR3(A, B, 512)
   bool launched = false;
+  mark(ev0);
   BISP_PAIR(1, 1) BISP_PAIR(2, 1) BISP_PAIR(3, 2) BISP_PAIR(4, 2) BISP_PAIR(5, 3) BISP_PAIR(6, 3)
   BISP_PAIR_S(7, 4) BISP_PAIR_S(8, 4) BISP_PAIR_S(10, 5)
 #undef BISP_PAIR
@@ -1360,6 +1391,7 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
   k_pair_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(j, partials, c.nblk, c.warps, c.ksplit, c.TM, c.TN,
                                                        j.nb, j.nout, out_dev);
   BISP_CHECK_LAUNCH();
+  mark(ev1);
   if (launches) *launches += 2;
   if (kernel) *kernel = 0;
 }

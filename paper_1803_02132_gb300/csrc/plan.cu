@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <tuple>
@@ -208,6 +209,10 @@ struct bisp_plan {
   // parameters
   int N = 0, NH = 0, nb = 0, nmult = 0, los = 0, mas = 2, interlace = 0, want_window = 0, precision = 0;
   int estimator = 0;  // bisp_estimator
+  int los_obj = 3;    // object of the triplet carrying y_L^{M*}(x_hat): 3 (main text), 1 or 2 (App. B)
+  // autotuned launch shape: z-pass row groups per CTA (0 until measured), and the timings seen
+  int zgroups = 0;
+  std::vector<std::pair<int, float>> tune_log;
   int diagonal = 0;   // only k1 = k2 outputs
   double L = 0, H = 0, kF = 0, V = 0, P0 = 0, obs[3] = {0, 0, 0};
   size_t max_bytes = 0;
@@ -239,6 +244,20 @@ struct bisp_plan {
     std::vector<PairRecipe> x, y;
   };
   std::vector<std::vector<Term>> terms;
+  // line of sight on x1 or x2 (App. B): per multipole and per m of the other object, the
+  // contraction over m and M of the weighted object's fields is done in k space, giving the real
+  // fields K_A, K_B of i^l (K_A + i K_B) = sum_m 3j F_l^m[delta n_L^M] (SRC_SHELL_SUM fields,
+  // entries (coef, |m|, part, D channel)); kterms are the data and window passes' terms over the
+  // components followed by these fields
+  struct KField {
+    int l;
+    std::vector<std::tuple<float, int, int, int>> ent;
+  };
+  std::vector<KField> kfields;
+  std::vector<std::vector<Term>> kterms;
+  int pass_ncomp(bool unit) const {  // field slots per bin in the pool
+    return (int)comps.size() + (unit || los_obj == 3 ? 0 : (int)kfields.size());
+  }
   // the same expansion as plain FP64 terms per multipole: sum_x coef F_c1(b1) F_c2(b2) G_g
   struct Tri {
     int c1, c2, g;
@@ -312,6 +331,10 @@ void validate(const bisp_params* p) {
     if (l1 > BISP_LMAX || L > BISP_LMAX) fail(BISP_EUNSUPPORTED, "l and L above 4 are not built");
   }
   if (p->los != BISP_LOS_GLOBAL_Z && p->los != BISP_LOS_LOCAL) fail(BISP_EINVAL, "los");
+  if (p->los_object < 0 || p->los_object > 3) fail(BISP_EINVAL, "los_object must be 0, 1, 2 or 3");
+  if ((p->los_object == 1 || p->los_object == 2) && p->los == BISP_LOS_LOCAL &&
+      (p->estimator != BISP_BISPECTRUM || p->precision != BISP_FP32))
+    fail(BISP_EUNSUPPORTED, "the line of sight on x1 or x2 is built for the FP32 bispectrum only");
   if (p->mas < 1 || p->mas > 3) fail(BISP_EINVAL, "mas must be 1 (NGP), 2 (CIC) or 3 (TSC)");
   if (p->precision != BISP_FP32 && p->precision != BISP_FP64) fail(BISP_EINVAL, "precision must be BISP_FP32 or BISP_FP64");
   if (!std::isfinite(p->fkp_P0) || p->fkp_P0 < 0) fail(BISP_EINVAL, "fkp_P0");
@@ -484,6 +507,48 @@ void build_rshells(bisp_plan* P) {
 //   F_l^m = i^l (A + i B),  F_l^{-m} = (-1)^m i^l (A - i B)   (three-point function: no i^l),
 //   G_L^M = R + i I,        G_L^{-M} = (-1)^M (R - i I)   (global LOS: G_L^M = delta_M0 G)
 // grouped into pair-kernel terms on the side with fewer components.
+// Contraction terms of one multipole from its trilinear expansion, grouped by the side with
+// fewer distinct components: each term pairs one bare component field with a built side
+// sum_(c, g) coef F_c G_g; a built side spans at most 8 components (a term with more is split
+// into terms over groups of 8 components, whose sum is the same).
+std::vector<bisp_plan::Term> terms_of(const std::map<int, std::vector<std::tuple<int, int, double>>>& by1,
+                                      const std::map<int, std::vector<std::tuple<int, int, double>>>& by2) {
+  std::vector<bisp_plan::Term> ts;
+  const bool bare_y = by2.size() <= by1.size();
+  for (auto& kv : bare_y ? by2 : by1) {
+    // the built side's entries in component order, cut into groups of at most 8 components
+    std::vector<std::tuple<int, int, double>> ent = kv.second;
+    std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) { return std::get<0>(a) < std::get<0>(b); });
+    std::vector<PairRecipe> built;
+    int ncomp = 0, last = -1;
+    auto flush = [&] {
+      if (built.empty()) return;
+      bisp_plan::Term t;
+      if (bare_y) {
+        t.x = built;
+        t.y.push_back({kv.first, -1, 1.0f});
+      } else {
+        t.x.push_back({kv.first, -1, 1.0f});
+        t.y = built;
+      }
+      ts.push_back(t);
+      built.clear();
+      ncomp = 0;
+      last = -1;
+    };
+    for (auto& r : ent) {
+      if (std::get<0>(r) != last) {
+        if (ncomp == 8) flush();
+        ++ncomp;
+        last = std::get<0>(r);
+      }
+      built.push_back({std::get<0>(r), std::get<1>(r), (float)std::get<2>(r)});
+    }
+    flush();
+  }
+  return ts;
+}
+
 void build_recipes(bisp_plan* P) {
   P->terms.clear();
   P->tri64.clear();
@@ -536,24 +601,75 @@ void build_recipes(bisp_plan* P) {
       by1[c1].push_back({c2, g, kv.second});
       by2[c2].push_back({c1, g, kv.second});
     }
-    std::vector<bisp_plan::Term> ts;
-    if (by2.size() <= by1.size()) {
-      for (auto& kv : by2) {
-        bisp_plan::Term t;
-        for (auto& r : kv.second) t.x.push_back({std::get<0>(r), std::get<1>(r), (float)std::get<2>(r)});
-        t.y.push_back({kv.first, -1, 1.0f});
-        ts.push_back(t);
-      }
-    } else {
-      for (auto& kv : by1) {
-        bisp_plan::Term t;
-        t.x.push_back({kv.first, -1, 1.0f});
-        for (auto& r : kv.second) t.y.push_back({std::get<0>(r), std::get<1>(r), (float)std::get<2>(r)});
-        ts.push_back(t);
-      }
-    }
-    P->terms.push_back(ts);
+    P->terms.push_back(terms_of(by1, by2));
     P->tri64.push_back(t64);
+  }
+  P->kfields.clear();
+  P->kterms.clear();
+  if (P->los_obj == 3) return;
+  // line of sight on object a (App. B): K_{m_o}(x; b_a) = sum_{m_a} 3j F_{l_a}^{m_a}[delta n_L^M](x; b_a),
+  // M = -m1 - m2, with delta n_L^M = kX (R + i sX I) in its real channels and, for signed m,
+  // Re y^{m*} = sr part0(|m|), Im y^{m*} = si part1(|m|); then
+  // Re[K_{m_o} F_{l_o}^{m_o}[delta n_0^0] G_0^0] = il k_o (K_A A_o - s_o K_B B_o) G_0^0.
+  const int a = P->los_obj;
+  for (auto& e : P->ells) {
+    const int l1 = e[0], l2 = e[1], L = e[2];
+    const int la = a == 1 ? l1 : l2, lo = a == 1 ? l2 : l1;
+    const double il = (((l1 + l2) / 2) & 1) ? -1.0 : 1.0;
+    std::map<std::tuple<int, int, int>, double> tri;  // (c1, c2, g) -> coef
+    for (int mo = -lo; mo <= lo; ++mo) {
+      std::map<std::tuple<int, int, int>, double> KA, KB;  // (|m|, part, channel) -> coef
+      for (int ma = -la; ma <= la; ++ma) {
+        const int m1 = a == 1 ? ma : mo, m2 = a == 1 ? mo : ma;
+        const int M = -m1 - m2;
+        if (std::abs(M) > L) continue;
+        const double w = wigner3j(l1, l2, L, m1, m2, M);
+        if (w == 0.0) continue;
+        const int aM = std::abs(M), am = std::abs(ma);
+        const int R = P->dchan(L, aM, 0), I = aM ? P->dchan(L, aM, 1) : -1;
+        const double kX = (M < 0 && (aM & 1)) ? -1.0 : 1.0, sX = M < 0 ? -1.0 : 1.0;
+        const double sr = (ma < 0 && (am & 1)) ? -1.0 : 1.0, si = ma < 0 ? -sr : sr;
+        const double c = w * kX;
+        KA[{am, 0, R}] += c * sr;
+        if (I >= 0 && am) KA[{am, 1, I}] += -c * sX * si;
+        if (am) KB[{am, 1, R}] += c * si;
+        if (I >= 0) KB[{am, 0, I}] += c * sX * sr;
+      }
+      auto add_field = [&](const std::map<std::tuple<int, int, int>, double>& ent) {
+        bisp_plan::KField f;
+        f.l = la;
+        double mx = 0.0;
+        for (auto& kv : ent) mx = std::max(mx, std::fabs(kv.second));
+        for (auto& kv : ent)
+          if (std::fabs(kv.second) > 1e-13 * mx)
+            f.ent.push_back({(float)kv.second, std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first)});
+        if (f.ent.empty()) return -1;
+        if ((int)f.ent.size() > INV_MAXE) fail(BISP_EUNSUPPORTED, "line-of-sight field with too many entries");
+        P->kfields.push_back(f);
+        return (int)(P->comps.size() + P->kfields.size() - 1);
+      };
+      const int iA = add_field(KA), iB = add_field(KB);
+      const int amo = std::abs(mo);
+      const double ko = (mo < 0 && (amo & 1)) ? -1.0 : 1.0, so = mo < 0 ? -1.0 : 1.0;
+      const int Ao = P->comp_index.at({lo, amo, 0}), Bo = amo ? P->comp_index.at({lo, amo, 1}) : -1;
+      auto put = [&](int kf, int comp, double coef) {
+        if (kf < 0 || comp < 0) return;
+        if (a == 1) tri[{kf, comp, P->d00}] += coef;
+        else tri[{comp, kf, P->d00}] += coef;
+      };
+      put(iA, Ao, il * ko);
+      put(iB, Bo, -il * ko * so);
+    }
+    double mx = 0.0;
+    for (auto& kv : tri) mx = std::max(mx, std::fabs(kv.second));
+    std::map<int, std::vector<std::tuple<int, int, double>>> by1, by2;
+    for (auto& kv : tri) {
+      if (std::fabs(kv.second) <= 1e-13 * mx) continue;
+      const int c1 = std::get<0>(kv.first), c2 = std::get<1>(kv.first), g = std::get<2>(kv.first);
+      by1[c1].push_back({c2, g, kv.second});
+      by2[c2].push_back({c1, g, kv.second});
+    }
+    P->kterms.push_back(terms_of(by1, by2));
   }
 }
 
@@ -853,8 +969,8 @@ std::pair<const float2*, double> nspec_of(const bisp_plan* P, const Catalog& C, 
 // ---------------------------------------------------------------------------------
 struct PassState {
   std::map<std::pair<int, int>, cplx> sbar;  // (L, M>=0) -> Sbar_L^M
-  // Z[(l, m, L, M)] per bin
-  std::map<std::tuple<int, int, int, int>, std::vector<cplx>> Z;
+  // Z[(l, m, L, M)] per bin; Zp: the primed sums of the line of sight on x1 or x2
+  std::map<std::tuple<int, int, int, int>, std::vector<cplx>> Z, Zp;
 };
 
 // pair reduction over the first nbu bins held in the field pool, for the term lists tl (one
@@ -864,14 +980,14 @@ struct PassState {
 // keep the layout [gset][mult][b1][b2] of a single launch.
 using TermList = std::vector<bisp_plan::Term>;
 void run_pair_terms(bisp_plan* P, const std::vector<const TermList*>& tl, int gsets, int gstride, const float* gbase,
-                    int nbu, std::vector<double>& out, int* launches) {
+                    int nbu, int ncomp, std::vector<double>& out, int* launches) {
   // build a pair job with nout = tl.size() * gsets outputs
   PairJob J{};
   J.fields = P->pool.as<float>();
   J.gfields = gbase;
   J.Ng = P->Ng;
   J.nb = nbu;
-  J.ncomp = (int)P->comps.size();
+  J.ncomp = ncomp;
   J.ng = gsets * gstride;
   J.nout = (int)tl.size() * gsets;
   int t = 0, r = 0;
@@ -908,17 +1024,17 @@ void run_pair_terms(bisp_plan* P, const std::vector<const TermList*>& tl, int gs
     out.clear();
     if (gsets > 1) {
       for (int gs = 0; gs < gsets; ++gs) {
-        run_pair_terms(P, tl, 1, gstride, gbase + (size_t)gs * gstride * P->Ng, nbu, part, launches);
+        run_pair_terms(P, tl, 1, gstride, gbase + (size_t)gs * gstride * P->Ng, nbu, ncomp, part, launches);
         out.insert(out.end(), part.begin(), part.end());
       }
       return;
     }
     if (tl.size() > 1) {
       const size_t h = tl.size() / 2;
-      run_pair_terms(P, std::vector<const TermList*>(tl.begin(), tl.begin() + h), 1, gstride, gbase, nbu, part,
-                     launches);
+      run_pair_terms(P, std::vector<const TermList*>(tl.begin(), tl.begin() + h), 1, gstride, gbase, nbu, ncomp,
+                     part, launches);
       out.insert(out.end(), part.begin(), part.end());
-      run_pair_terms(P, std::vector<const TermList*>(tl.begin() + h, tl.end()), 1, gstride, gbase, nbu, part,
+      run_pair_terms(P, std::vector<const TermList*>(tl.begin() + h, tl.end()), 1, gstride, gbase, nbu, ncomp, part,
                      launches);
       out.insert(out.end(), part.begin(), part.end());
       return;
@@ -926,8 +1042,8 @@ void run_pair_terms(bisp_plan* P, const std::vector<const TermList*>& tl, int gs
     if (tl[0]->size() < 2) fail(BISP_EUNSUPPORTED, "a contraction term does not fit one launch");
     const size_t h = tl[0]->size() / 2;
     const TermList lo(tl[0]->begin(), tl[0]->begin() + h), hi(tl[0]->begin() + h, tl[0]->end());
-    run_pair_terms(P, {&lo}, 1, gstride, gbase, nbu, out, launches);
-    run_pair_terms(P, {&hi}, 1, gstride, gbase, nbu, part, launches);
+    run_pair_terms(P, {&lo}, 1, gstride, gbase, nbu, ncomp, out, launches);
+    run_pair_terms(P, {&hi}, 1, gstride, gbase, nbu, ncomp, part, launches);
     for (size_t i = 0; i < out.size(); ++i) out[i] += part[i];
     return;
   }
@@ -939,9 +1055,7 @@ void run_pair_terms(bisp_plan* P, const std::vector<const TermList*>& tl, int gs
   cudaEvent_t e0, e1;
   BISP_CUDA(cudaEventCreate(&e0));
   BISP_CUDA(cudaEventCreate(&e1));
-  BISP_CUDA(cudaEventRecord(e0, P->stream));
-  pair_reduce(J, P->pairout.as<double>(), P->pairscr.p, P->pairscr.n, P->stream, launches, &P->pair_kernel);
-  BISP_CUDA(cudaEventRecord(e1, P->stream));
+  pair_reduce(J, P->pairout.as<double>(), P->pairscr.p, P->pairscr.n, P->stream, launches, &P->pair_kernel, e0, e1);
   out.resize((size_t)J.nout * J.nb * J.nb);
   BISP_CUDA(cudaMemcpyAsync(out.data(), P->pairout.p, ob, cudaMemcpyDeviceToHost, P->stream));
   BISP_CUDA(cudaStreamSynchronize(P->stream));
@@ -962,6 +1076,7 @@ void run_inverse(bisp_plan* P, InvBatch& b, int* launches) {
   b.interlace = P->interlace;
   b.err = P->flags.as<int>();
   b.stall = inject_stall("zpass") ? 1 : 0;
+  b.zgroups = P->zgroups;
   const size_t need = inverse_scratch_bytes(P->N, b.P, b.nf);
   if (need > P->invscr.n) {
     admit(P, need - P->invscr.n);
@@ -970,9 +1085,70 @@ void run_inverse(bisp_plan* P, InvBatch& b, int* launches) {
   inverse_fft(b, P->tw.as<float2>(), P->invscr.p, P->stream, launches);
 }
 
-// shell fields of bins [b0, b1) into the pool, bin b at pool bin slot b - b0 + slot
-void shell_fields(bisp_plan* P, const float2* D00, bool unit, int b0, int b1, int slot, int* launches) {
+// Autotuner of the inverse transforms' z pass: the number of 16-row groups a CTA takes (more
+// groups share one twiddle-table setup and prefetch pipeline; fewer give more CTAs).  Every value
+// computes the same fields bit for bit, so the choice only moves time.  The plan times its
+// largest shell batch (the costliest prune extent) once with each candidate and keeps the
+// fastest; the choice is cached per (N, prune extent, batch width) for every plan of the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune_cache;
+
+void tune_zgroups(bisp_plan* P, InvBatch& b, int* launches) {
+  const char* e = getenv("BISP_ZGROUPS");  // fixed value (tests, comparisons): no timing
+  if (e && atoi(e) > 0) {
+    P->zgroups = inverse_zgroups(P->N, atoi(e));
+    run_inverse(P, b, launches);
+    return;
+  }
+  const auto key = std::make_tuple(P->N, b.P, b.nf);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      P->zgroups = it->second;
+      run_inverse(P, b, launches);
+      return;
+    }
+  }
+  cudaEvent_t e0, e1;
+  BISP_CUDA(cudaEventCreate(&e0));
+  BISP_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  std::vector<int> tried;
+  P->tune_log.clear();
+  for (int cand : {1, 2, 4, 8, 16, 32}) {
+    const int g = inverse_zgroups(P->N, cand);
+    if (std::find(tried.begin(), tried.end(), g) != tried.end()) continue;
+    tried.push_back(g);
+    P->zgroups = g;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms the caches and the module
+      BISP_CUDA(cudaEventRecord(e0, P->stream));
+      run_inverse(P, b, launches);
+      BISP_CUDA(cudaEventRecord(e1, P->stream));
+      BISP_CUDA(cudaEventSynchronize(e1));
+      BISP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    P->tune_log.push_back({g, ms});
+    if (!best || ms < best_ms) {
+      best = g;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->zgroups = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+}
+
+// shell fields of bins [b0, b1) into the pool, bin b at pool bin slot b - b0 + slot; Dp: the
+// pass's delta n channel spectra (nullptr for unit shells)
+void shell_fields(bisp_plan* P, const float2* Dp, bool unit, int b0, int b1, int slot, int* launches) {
   const int nc = (int)P->comps.size();
+  const int stride = P->pass_ncomp(unit);
+  const float2* D00 = Dp ? Dp + (size_t)P->d00 * P->Nk : nullptr;
   if (P->estimator == BISP_THREEPT) {
     // per r-bin: the separation kernels of its nc components, their forward FFT (no
     // deconvolution), then the full inverse transforms of conj(K) Delta
@@ -1032,9 +1208,39 @@ void shell_fields(bisp_plan* P, const float2* D00, bool unit, int b0, int b1, in
       f.part = P->comps[c].part;
       f.unit = unit ? 1 : 0;
       f.scale = 1.f;
-      f.out = P->pool.as<float>() + ((size_t)(b - b0 + slot) * nc + c) * P->Ng;
+      f.out = P->pool.as<float>() + ((size_t)(b - b0 + slot) * stride + c) * P->Ng;
     }
-    run_inverse(P, B, launches);
+    // the first shell batch of the largest prune extent tunes the z pass (and computes the fields)
+    if (!P->zgroups && P->Pb[b] == *std::max_element(P->Pb.begin(), P->Pb.end()))
+      tune_zgroups(P, B, launches);
+    else
+      run_inverse(P, B, launches);
+    // line of sight on x1 or x2: the k-space contractions over the weighted object's (m, M)
+    const int nk = stride - nc;
+    for (int k0 = 0; k0 < nk; k0 += 32) {
+      InvBatch K{};
+      K.P = P->Pb[b];
+      K.nf = std::min(32, nk - k0);
+      K.qlo = P->qlo[b];
+      K.qhi = P->qhi[b];
+      K.inv_nmodes = B.inv_nmodes;
+      for (size_t ch = 0; ch < P->dch.size() && ch < 16; ++ch) K.spec[ch] = Dp + ch * P->Nk;
+      for (int j = 0; j < K.nf; ++j) {
+        const bisp_plan::KField& kf = P->kfields[k0 + j];
+        InvField& f = K.f[j];
+        f.kind = SRC_SHELL_SUM;
+        f.l = kf.l;
+        f.ne = (int)kf.ent.size();
+        for (int q = 0; q < f.ne; ++q) {
+          f.ecoef[q] = std::get<0>(kf.ent[q]);
+          f.em[q] = (signed char)std::get<1>(kf.ent[q]);
+          f.epart[q] = (signed char)std::get<2>(kf.ent[q]);
+          f.espec[q] = (signed char)std::get<3>(kf.ent[q]);
+        }
+        f.out = P->pool.as<float>() + ((size_t)(b - b0 + slot) * stride + nc + k0 + j) * P->Ng;
+      }
+      run_inverse(P, K, launches);
+    }
   }
 }
 
@@ -1043,24 +1249,27 @@ void shell_fields(bisp_plan* P, const float2* D00, bool unit, int b0, int b1, in
 // taken in blocks of nbk: block I sits in the pool's first slots and block J > I after it, and
 // one pair launch covers their union; a pair (b1, b2) is kept from exactly one union (cross
 // pairs from (I, J), a block's own pairs from (I, I + 1), the last block's from the last union).
-void pair_set(bisp_plan* P, const float2* D00, bool unit, int gsets, const float* gbase, int nbk,
+void pair_set(bisp_plan* P, const float2* Dp, bool unit, int gsets, const float* gbase, int nbk,
               std::vector<double>& out, int* launches) {
+  const float2* D00 = Dp;  // shell_fields takes the pass's channel spectra
   const int nb = P->nb, nmult = P->nmult, nD = (int)P->dch.size();
   std::vector<int> all(nmult);
   for (int i = 0; i < nmult; ++i) all[i] = i;
   std::vector<const TermList*> tl;
-  for (int i : all) tl.push_back(&P->terms[i]);
+  const bool kt = !unit && P->los_obj != 3;
+  for (int i : all) tl.push_back(kt ? &P->kterms[i] : &P->terms[i]);
+  const int ncomp = P->pass_ncomp(unit);
   auto pairs = [&](int nbu, std::vector<double>& res) {
     if (gsets > 1 && pair_split_gsets()) {
       // one launch per G set: outputs [gset][mult][b1][b2] as with a single launch
       res.clear();
       for (int gs = 0; gs < gsets; ++gs) {
         std::vector<double> part;
-        run_pair_terms(P, tl, 1, nD, gbase + (size_t)gs * nD * P->Ng, nbu, part, launches);
+        run_pair_terms(P, tl, 1, nD, gbase + (size_t)gs * nD * P->Ng, nbu, ncomp, part, launches);
         res.insert(res.end(), part.begin(), part.end());
       }
     } else {
-      run_pair_terms(P, tl, gsets, nD, gbase, nbu, res, launches);
+      run_pair_terms(P, tl, gsets, nD, gbase, nbu, ncomp, res, launches);
     }
   };
   if (nbk >= nb) {
@@ -1107,7 +1316,7 @@ void pair_set(bisp_plan* P, const float2* D00, bool unit, int gsets, const float
 // the device memory the measurement still has to allocate besides the pool.
 // BISP_BLOCK_BINS=n in the environment caps the block at n bins (tests of the blocking).
 int fp32_block_bins(bisp_plan* P, size_t other_need) {
-  const size_t per_bin = P->comps.size() * (size_t)P->Ng * 4;
+  const size_t per_bin = (size_t)P->pass_ncomp(false) * (size_t)P->Ng * 4;
   size_t fre = 0, tot = 0;
   BISP_CUDA(cudaMemGetInfo(&fre, &tot));
   const size_t reserve = (size_t)2 << 30;
@@ -1384,7 +1593,7 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
       const size_t inv = std::max(inverse_scratch_bytes(P->N, P->N / 2 - 1, nD),
                                   inverse_scratch_bytes(P->N, pmax, (int)P->comps.size()));
       nbk = fp32_block_bins(P, need + (inv > P->invscr.n ? inv - P->invscr.n : 0));
-      const size_t pool_need = (size_t)(nbk == nb || P->diagonal ? nbk : 2 * nbk) * P->comps.size() * Ng * 4;
+      const size_t pool_need = (size_t)(nbk == nb || P->diagonal ? nbk : 2 * nbk) * P->pass_ncomp(false) * Ng * 4;
       // the assignment arena moves into the pool from now on: free it before admission
       if (pool_need > P->pool.n) P->ws.release(&P->bytes);
       add(P->pool, pool_need);
@@ -1510,6 +1719,14 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
           Q.f[c].B = Np + (size_t)P->n00 * Nk;
           Q.f[c].sbar = (float)(ch.part ? sbv.i : sbv.r);
           Q.f[c].scale = 1.f;
+          if (local && P->los_obj != 3) {
+            // the distinct object is unweighted, the coincident pair carries y_L^M (App. B):
+            // Q = delta n_0^0 conj(N_L^M) - Sbar_L^M C/W^2, N_L^M = N_R + i N_I in real channels
+            Q.f[c].A = Dp + (size_t)P->d00 * Nk;
+            Q.f[c].B = Np + (size_t)P->nchan(ch.L, ch.M, ch.part) * Nk;
+            Q.f[c].scale = ch.part ? -1.f : 1.f;
+            Q.f[c].sbar = (float)(ch.part ? -sbv.i : sbv.r);
+          }
           Q.f[c].out = P->qf.as<float>() + ((size_t)k * nD + c) * Ng;
         }
         run_inverse(P, Q, &launches);
@@ -1521,6 +1738,10 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
       for (int l : P->ls)
         for (int m = -l; m <= l; ++m) lm.push_back({l, m});
       const int nblk = 64;
+      // primed: the distinct object carries y_L^{M*} and the pair is unweighted (line of sight on
+      // x1 or x2, App. B), Z' = avg y_l^{m*} [delta n_L^M conj(N_0^0) - Sbar_L^M C/W^2]
+      const int nkind = (local && P->los_obj != 3) ? 2 : 1;
+      for (int kind = 0; kind < nkind; ++kind)
       for (int L : P->Ls)
         for (int M = 0; M <= L; ++M) {
           if (!local && (L > 0 || M > 0)) continue;
@@ -1528,10 +1749,19 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
           for (size_t g0 = 0; g0 < lm.size(); g0 += 9) {
             const int cnt = (int)std::min<size_t>(9, lm.size() - g0);
             ZsumArgs z{};
-            z.D00 = Dp + (size_t)P->d00 * Nk;
-            const int cr = P->nchan(L, M, 0), ci = M ? P->nchan(L, M, 1) : -1;
-            z.NR = Np + (size_t)cr * Nk;
-            z.NI = ci >= 0 ? Np + (size_t)ci * Nk : nullptr;
+            if (kind == 0) {
+              z.XR = Dp + (size_t)P->d00 * Nk;
+              z.XI = nullptr;
+              const int cr = P->nchan(L, M, 0), ci = M ? P->nchan(L, M, 1) : -1;
+              z.NR = Np + (size_t)cr * Nk;
+              z.NI = ci >= 0 ? Np + (size_t)ci * Nk : nullptr;
+            } else {
+              const int dr = P->dchan(L, M, 0), di = M ? P->dchan(L, M, 1) : -1;
+              z.XR = Dp + (size_t)dr * Nk;
+              z.XI = di >= 0 ? Dp + (size_t)di * Nk : nullptr;
+              z.NR = Np + (size_t)P->n00 * Nk;
+              z.NI = nullptr;
+            }
             z.sbar_re = sbv.r;
             z.sbar_im = sbv.i;
             z.N = P->N;
@@ -1565,7 +1795,7 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
                 }
                 if (P->nmodes[b] > 0) zz[b] = {re / P->nmodes[b], im / P->nmodes[b]};
               }
-              ps[k].Z[{lm[g0 + t].first, lm[g0 + t].second, L, M}] = zz;
+              (kind ? ps[k].Zp : ps[k].Z)[{lm[g0 + t].first, lm[g0 + t].second, L, M}] = zz;
             }
           }
         }
@@ -1586,15 +1816,15 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
     P->f64shell.release(&P->bytes);
   } else {
     // pair reductions
-    P->pool.ensure((size_t)(nbk == nb || P->diagonal ? nbk : 2 * nbk) * P->comps.size() * Ng * 4, &P->bytes);
+    P->pool.ensure((size_t)(nbk == nb || P->diagonal ? nbk : 2 * nbk) * P->pass_ncomp(false) * Ng * 4, &P->bytes);
     // i = j != k shot term: unit shells, q fields of every pass (the three-point function
     // reads its q fields at the separations of each r-bin instead, below)
     if (!three) pair_set(P, nullptr, true, npass, P->qf.as<float>(), nbk, cU, &launches);
     // data
-    pair_set(P, P->pass_spec[0].as<float2>() + (size_t)P->d00 * Nk, false, 1, P->gf[0].as<float>(), nbk, cD,
+    pair_set(P, P->pass_spec[0].as<float2>(), false, 1, P->gf[0].as<float>(), nbk, cD,
              &launches);
     if (npass == 2)
-      pair_set(P, P->pass_spec[1].as<float2>() + (size_t)P->d00 * Nk, false, 1, P->gf[1].as<float>(), nbk, cW,
+      pair_set(P, P->pass_spec[1].as<float2>(), false, 1, P->gf[1].as<float>(), nbk, cW,
                &launches);
   }
   std::vector<float> gq[2];
@@ -1651,14 +1881,17 @@ void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, doubl
                 const double sg = (std::abs(MM) & 1) ? -1.0 : 1.0;
                 return cplx{sg * v.r, -sg * v.i};
               };
-              auto z_at = [&](int l, int m, int MM, int b) {
-                if (MM >= 0) return ps[k].Z.at({l, m, Lz, MM})[b];
-                const cplx v = ps[k].Z.at({l, -m, Lz, -MM})[b];
+              auto z_at = [&](int l, int m, int MM, int b, bool primed) {
+                const auto& Zm = primed ? ps[k].Zp : ps[k].Z;
+                if (MM >= 0) return Zm.at({l, m, Lz, MM})[b];
+                const cplx v = Zm.at({l, -m, Lz, -MM})[b];
                 const double sg = ((m + MM + l) & 1) ? -1.0 : 1.0;
                 return cplx{sg * v.r, -sg * v.i};
               };
               const cplx S = sbar_at(M);
-              const cplx Z1 = z_at(l1, m1, M, b1), Z2 = z_at(l2, m2, M, b2);
+              // the slot that carries the line of sight takes the primed sums (App. B)
+              const bool p1 = local && P->los_obj == 1, p2 = local && P->los_obj == 2;
+              const cplx Z1 = z_at(l1, m1, M, b1, p1), Z2 = z_at(l2, m2, M, b2, p2);
               const cplx iii = cm(S, cm(Y1, Y2));
               const cplx ijj = cm(Z1, Y2);
               const cplx iji = cm(Y1, Z2);
@@ -1757,6 +1990,7 @@ bisp_status bisp_plan_create(bisp_plan** out, const bisp_params* p, void* stream
     P->precision = p->precision;
     P->estimator = p->estimator;
     P->diagonal = p->diagonal_only ? 1 : 0;
+    P->los_obj = (p->los_object == 0 || p->los == BISP_LOS_GLOBAL_Z) ? 3 : p->los_object;
     const char* dbg = std::getenv("BISP_DEBUG");
     P->debug_mesh = dbg && std::strstr(dbg, "BISP_DEBUG_KEEP_MESH");
     int dev = 0;
@@ -1888,6 +2122,7 @@ bisp_status bisp_plan_query(const bisp_plan* P, bisp_plan_info* info) {
   info->pair_bytes = P->pair_bytes;
   info->pair_launches = P->pair_launches;
   info->pair_kernel = P->pair_kernel;
+  info->zpass_groups = P->zgroups;
   return BISP_OK;
 }
 

@@ -32,21 +32,28 @@ def _same(a, b):
 
 
 def test_injected_allocation_failures(monkeypatch):
+    """Plan creation, a first assignment and a first measurement (the calls that allocate), with
+    each of their device allocations failing in turn on a fresh plan: the call returns
+    BISP_ENOMEM naming the bytes, and the plan then assigns and measures exactly as one that saw
+    no failure; a steady-state measurement allocates nothing."""
     monkeypatch.delenv("BISP_FAIL_ALLOC", raising=False)
     xyz = _cat()
     with _plan() as p:
         p.assign(bisp.DATA, xyz)
         ref = p.measure()
-    # plan creation
+        monkeypatch.setenv("BISP_FAIL_ALLOC", "1")  # nothing left to allocate
+        assert _same(p.measure(), ref)
+        monkeypatch.delenv("BISP_FAIL_ALLOC")
     monkeypatch.setenv("BISP_FAIL_ALLOC", "1")
     with pytest.raises(bisp.BispError) as e:
         _plan()
     assert e.value.status == bisp.BISP_ENOMEM and "GB failed" in str(e.value)
     monkeypatch.delenv("BISP_FAIL_ALLOC")
-    with _plan() as p:
-        # every allocation of the first assignment and the first measurement in turn
-        for call in ("assign", "measure"):
-            for k in range(1, 64):
+    for call in ("assign", "measure"):
+        for k in range(1, 64):
+            with _plan() as p:
+                if call == "measure":
+                    p.assign(bisp.DATA, xyz)
                 monkeypatch.setenv("BISP_FAIL_ALLOC", str(k))
                 try:
                     p.assign(bisp.DATA, xyz) if call == "assign" else p.measure()
@@ -56,19 +63,16 @@ def test_injected_allocation_failures(monkeypatch):
                     assert "injected" in str(err)
                     failed = True
                 monkeypatch.delenv("BISP_FAIL_ALLOC")
-                if call == "assign" and failed:
-                    with pytest.raises(bisp.BispError) as e2:  # the catalogue is left unassigned
-                        p.measure()
-                    assert e2.value.status == bisp.BISP_ESTATE
-                    p.assign(bisp.DATA, xyz)
+                if call == "assign":
+                    if failed:
+                        with pytest.raises(bisp.BispError) as e2:  # the catalogue is left unassigned
+                            p.measure()
+                        assert e2.value.status == bisp.BISP_ESTATE
+                        p.assign(bisp.DATA, xyz)
                 assert _same(p.measure(), ref), (call, k)
-                if not failed:
-                    break
-            assert k > 1, f"{call}: no allocation was made"
-        # a steady-state measurement allocates nothing
-        monkeypatch.setenv("BISP_FAIL_ALLOC", "1")
-        assert _same(p.measure(), ref)
-        monkeypatch.delenv("BISP_FAIL_ALLOC")
+            if not failed:
+                break
+        assert k > 1, f"{call}: no allocation was made"
 
 
 @pytest.mark.parametrize("kernel", ["pair", "zpass"])

@@ -557,3 +557,62 @@ def test_fp32_fma_contraction_kernel(case, monkeypatch):
     if ran is not None:
         assert_close(out["window"], ref["window"], what="window")
         assert_close(out["window_shot"], ref["window_shot"], what="window shot")
+
+
+@pytest.mark.parametrize("los_object", [1, 2])
+def test_los_on_x1_x2(los_object, monkeypatch):
+    """The line of sight on x1 or x2 (App. B): the y_L^{M*} weight on the k1 or k2 object, with the
+    contraction over that object's (m, M) done in k space and the shot-noise terms following the
+    weighted object, against oracle/los.py on the local-line-of-sight survey with window; the L = 0
+    multipole does not depend on the choice."""
+    from oracle import los as LS
+
+    monkeypatch.delenv("BISP_BLOCK_BINS", raising=False)
+    c = CASES["survey_local"]
+    N, L = c["N"], c["L"]
+    edges = 2 * np.pi / L * np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5, 11.0, 15.5])
+    ells = [(0, 0, 0), (2, 0, 2), (1, 1, 2), (2, 2, 2), (3, 1, 2)]
+    gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+    p = E.Params(N=N, L=L, edges=edges, ells=ells, los="local", observer=obs, mas=c["mas"],
+                 interlace=c["interlace"], P0=1e4, window=True)
+    ref = LS.measure(p, gal, ran, los_object)
+    with _plan(p, los_object=los_object) as plan:
+        _assign(plan, 0, gal)
+        _assign(plan, 1, ran)
+        out = plan.measure()
+        again = plan.measure()
+    for k, rk in (("B", "B"), ("shot", "shot"), ("window", "window"), ("window_shot", "window_shot")):
+        assert_close(out[k], ref[rk], what=f"x{los_object} {k}")
+    assert np.array_equal(out["B"], again["B"])
+    with _plan(p) as plan3:  # L = 0: the same for every choice
+        _assign(plan3, 0, gal)
+        _assign(plan3, 1, ran)
+        o3 = plan3.measure()
+    assert_close(out["B"][:1], o3["B"][:1], tol=1e-5, what="B000 x1/x2 vs x3")
+
+
+def test_autotuned_zpass_groups_do_not_change_results(monkeypatch):
+    """The autotuner picks the z pass's row groups per CTA by timing candidates on the plan's
+    largest shell batch; every candidate computes the same fields, so measurements with the tuned
+    value and with fixed values (BISP_ZGROUPS) are identical bit for bit."""
+    c = CASES["survey_local"]
+    N, L = c["N"], c["L"]
+    edges = 2 * np.pi / L * np.array([1.0, 2.5, 4.0, 5.5, 7.0, 8.5, 11.0, 15.5])
+    gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+    p = E.Params(N=N, L=L, edges=edges, ells=c["ells"], los="local", observer=obs, mas=3, interlace=True, P0=1e4,
+                 window=True)
+    outs, groups = [], []
+    for fixed in (None, "1", "2", "16"):
+        if fixed:
+            monkeypatch.setenv("BISP_ZGROUPS", fixed)
+        else:
+            monkeypatch.delenv("BISP_ZGROUPS", raising=False)
+        with _plan(p) as plan:
+            _assign(plan, 0, gal)
+            _assign(plan, 1, ran)
+            outs.append(plan.measure())
+            groups.append(plan.info()["zpass_groups"])
+    assert groups[0] > 0
+    for o in outs[1:]:
+        for k in ("B", "shot", "window", "window_shot"):
+            assert np.array_equal(o[k], outs[0][k]), k
