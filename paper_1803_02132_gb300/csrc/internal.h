@@ -3,10 +3,21 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 #include <vector>
 
 namespace bisp {
+
+// NVTX range for the duration of a scope (stages of bisp_assign / bisp_measure show up by name
+// in Nsight timelines; without a tool attached the calls do nothing)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- error handling -------------------------------------------------------------
 struct Error {

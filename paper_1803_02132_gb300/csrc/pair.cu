@@ -230,6 +230,7 @@ static bool pair_use_tc(const PairJob& j) {
 
 struct TmaLayout;
 static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps);
+static int pair_blocks();
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -440,6 +441,10 @@ struct TmaLayout {
   int ncomp, gbox;    // F blocks per half, G rows
   int stall;          // test knob: start no stage copy, so that every bounded wait runs out
   unsigned tab;       // offset of the side and H-row tables copied from the job
+  int nst;            // stages (chunks staged ahead + 1): 3 when shared memory allows, else 2
+  int nblk;           // CTAs of the launch
+  int mh, nt;         // 16-row tiles and 8-column tiles per term (bins covered: 16 mh, 8 nt)
+  unsigned cblk;      // bytes of one component block (bh bins x 128 bytes, bh = max(16 mh, 8 nt))
 };
 
 constexpr int TMA_MAXWARP = 20;  // two warps (row halves) per term and cell half
@@ -493,6 +498,10 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map
       : "memory");
 }
 
+__device__ __forceinline__ void ldsm_x2(unsigned addr, uint32_t* r) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(addr));
+}
+
 __device__ __forceinline__ void ldsm_x4(unsigned addr, uint32_t* r) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
@@ -535,7 +544,10 @@ __device__ __forceinline__ void kahan_add(float2& v, float x) {
   v.y = (t - v.x) - y;
   v.x = t;
 }
-template <int NTHR>
+// MH 16-row tiles (b1) and NT 8-column tiles (b2) per term: (2, 4) covers 32 bins; launches over
+// few bins (blocked unions, small bin sets) take (1, 2) for 16 bins or (1, 1) for 8, so that
+// their MMAs and staged bytes shrink with the bins.
+template <int NTHR, int MH, int NT, int NST>
 __global__ void __launch_bounds__(NTHR, 1)
     k_pair_tma(const __grid_constant__ PairJob J, const __grid_constant__ CUtensorMap tmF,
                const __grid_constant__ CUtensorMap tmG, const TmaLayout L, int ksplit, double* partials, int* err) {
@@ -546,17 +558,17 @@ __global__ void __launch_bounds__(NTHR, 1)
   unsigned char* const gb = dsm + (base - raw0);  // generic pointer to the aligned base
   float* const Hs = reinterpret_cast<float*>(gb + L.hs);
   const unsigned bar0 = base + L.bar;
-  const int64_t nchunk = J.Ng / PR_CH;
+  constexpr int chc = PR_CH;  // cells per chunk: two 32-cell halves
+  const int64_t nchunk = J.Ng / chc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // warp = ((term * ksplit) + cell half) * 2 + row half: rows 16 mi .. 16 mi + 15 of the term tile
-  const int mi = warp & 1, grp = warp >> 1;
+  // warp = ((term * ksplit) + cell half) * MH + row half: rows 16 mi .. 16 mi + 15 of the term tile
+  const int mi = warp % MH, grp = warp / MH;
   const int t = grp / ksplit, ks = grp % ksplit;
   const PairTermDesc T = J.term[t];
   unsigned long long pol = 0;
   if (tid == 0) {
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    mbar_init(bar0, 1);
-    mbar_init(bar0 + 8, 1);
+    for (int k = 0; k < NST; ++k) mbar_init(bar0 + 8u * k, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
@@ -566,7 +578,7 @@ __global__ void __launch_bounds__(NTHR, 1)
   int2* const s_se = reinterpret_cast<int2*>(gb + L.tab);
   int* const s_ho = reinterpret_cast<int*>(s_se + nse);
   int2* const s_he = reinterpret_cast<int2*>(gb + ((L.tab + (unsigned)nse * 8u + (unsigned)(J.nh + 1) * 4u + 7u) & ~7u));
-  for (int i = tid; i < nse; i += blockDim.x) s_se[i] = make_int2(J.s_ent[i][0] * 4096, J.s_ent[i][1] * PR_CH);
+  for (int i = tid; i < nse; i += blockDim.x) s_se[i] = make_int2(J.s_ent[i][0] * (int)L.cblk, J.s_ent[i][1] * chc);
   for (int i = tid; i <= J.nh; i += blockDim.x) s_ho[i] = J.h_off[i];
   for (int i = tid; i < nhe; i += blockDim.x) s_he[i] = make_int2(J.h_ent[i].g, __float_as_int(J.h_ent[i].coef));
   __syncthreads();
@@ -576,8 +588,8 @@ __global__ void __launch_bounds__(NTHR, 1)
     mbar_expect_tx(bar, L.tx);
     for (int h = 0; h < 2; ++h) {
       const unsigned hb = base + st * L.stage + h * L.half;
-      const int x = (int)(ch * PR_CH + 32 * h);
-      for (int c = 0; c < L.ncomp; ++c) tma_load_3d(hb + (unsigned)c * 4096u, &tmF, x, c, 0, bar, pol);
+      const int x = (int)(ch * chc + 32 * h);
+      for (int c = 0; c < L.ncomp; ++c) tma_load_3d(hb + (unsigned)c * L.cblk, &tmF, x, c, 0, bar, pol);
       tma_load_2d(hb + L.fsz, &tmG, x, 0, bar, pol);
     }
   };
@@ -585,11 +597,13 @@ __global__ void __launch_bounds__(NTHR, 1)
   float2* slot = reinterpret_cast<float2*>(partials) + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * 16;
 #pragma unroll
   for (int q = 0; q < 16; ++q) slot[q] = make_float2(0.f, 0.f);
-  // MMA accumulators: FP32 sums over at most PR_FLUSH chunks (1024 cells), then added with
-  // Kahan compensation to the lane's (sum, compensation) slots
-  float c[16];
+  // per chunk the MMA accumulators start from zero (the tensor core's accumulation stays at the
+  // size of one chunk's products); chunk sums go to FP32 running sums over at most PR_FLUSH
+  // chunks (1024 cells), which are added round robin with Kahan compensation to the lane's
+  // (sum, compensation) slots
+  float run[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) c[q] = 0.f;
+  for (int q = 0; q < 16; ++q) run[q] = 0.f;
 
   // ldmatrix rows of this lane: matrix j = lane/8, row r = lane%8 of that matrix; every
   // fragment row is congruent to r mod 8, so its swizzled piece is (piece ^ r).
@@ -610,18 +624,32 @@ __global__ void __launch_bounds__(NTHR, 1)
   // terms are normalised so that only the X (A operand) side can be built
   const bool xb = T.xslot >= 0;
   const int e0 = xb ? J.s_off[T.xslot] : 0, e1 = xb ? J.s_off[T.xslot + 1] : 0;
-  const unsigned xoff = xb ? 0u : (unsigned)T.xdir * 4096u, yoff = (unsigned)T.ydir * 4096u;
+  const unsigned xoff = xb ? 0u : (unsigned)T.xdir * L.cblk, yoff = (unsigned)T.ydir * L.cblk;
   const int hfirst = ksplit == 2 ? ks : 0, hlast = ksplit == 2 ? ks + 1 : 2;
 
-  if (tid == 0 && blockIdx.x < nchunk) issue(blockIdx.x, 0);
+  // NST - 1 chunks staged ahead; chunk index it uses stage it % NST, phase (it / NST) & 1
+  int issued = 0;  // thread 0: chunks whose copies were started
+  if (tid == 0)
+    for (int k = 0; k < NST - 1; ++k)
+      if (blockIdx.x + (int64_t)k * gridDim.x < nchunk) {
+        issue(blockIdx.x + (int64_t)k * gridDim.x, k);
+        ++issued;
+      }
   int it = 0;
   for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x, ++it) {
-    const int st = it & 1;
-    if (tid == 0 && ch + gridDim.x < nchunk) {
+    const int st = it % NST;
+    // the stage of chunk it + NST - 1 was last read by chunk it - 1, before the barrier ending it
+    const int64_t nx = ch + (int64_t)(NST - 1) * gridDim.x;
+    if (tid == 0 && nx < nchunk) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(ch + gridDim.x, st ^ 1);
+      issue(nx, (it + NST - 1) % NST);
+      ++issued;
     }
-    if (!mbar_wait_bounded(bar0 + 8u * st, (unsigned)(it >> 1) & 1u)) {
+    // slot it % 16 is flushed at the end of this chunk; load it now so that the L2 round
+    // trip overlaps the chunk's work
+    const int fg = it & 15;
+    float2 pre = slot[fg];
+    if (!mbar_wait_bounded(bar0 + 8u * st, (unsigned)(it / NST) & 1u)) {
       s_abort = 1;
       atomicExch(err, 1);
     }
@@ -648,7 +676,7 @@ __global__ void __launch_bounds__(NTHR, 1)
         }
       }
       // cells 4p..4p+3 of half hh: step kk = p/2, slot s = p%2 of the pairs of lanes tq = 0..3
-      float* d = Hs + h * PR_CH + hh * 32 + (p >> 1) * 8 + (p & 1);
+      float* d = Hs + h * chc + hh * 32 + (p >> 1) * 8 + (p & 1);
       d[0] = v.x;
       d[2] = v.y;
       d[4] = v.z;
@@ -657,6 +685,9 @@ __global__ void __launch_bounds__(NTHR, 1)
     __syncthreads();
     if (s_abort) break;
     // (2) this warp's 16 x 32 block of its term over its cell half (or both halves)
+    float c[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) c[q] = 0.f;
     for (int hh = hfirst; hh < hlast; ++hh) {
       const unsigned fh = base + sbo + hh * L.half;
       const float* hr = Hs + hh * 32 + 2 * tq;
@@ -681,43 +712,58 @@ __global__ void __launch_bounds__(NTHR, 1)
         } else {
           ldsm_x4(fh + xoff + loffA + poffA[kk], av);
         }
+        if (NT >= 2) {
 #pragma unroll
-        for (int i = 0; i < 2; ++i) ldsm_x4(fh + yoff + loffB[i] + poffB[kk], bv[i]);
+          for (int i = 0; i < NT / 2; ++i) ldsm_x4(fh + yoff + loffB[i] + poffB[kk], bv[i]);
+        } else {  // one n tile: matrices (k 0-3, k 4-7) of rows 0-7, addresses from lanes 0-15
+          ldsm_x2(fh + yoff + loffB[0] + poffB[kk], bv[0]);
+        }
         uint32_t ah[4], al[4], bh[4][2], bl[4][2];
 #pragma unroll
         for (int e = 0; e < 4; ++e) split_tf32(av[e], ah[e], al[e]);
+        if (NT >= 2) {
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
+          for (int i = 0; i < NT / 2; ++i)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
+            for (int e = 0; e < 4; ++e) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
+        } else {
+          split_tf32(bv[0][0], bh[0][0], bl[0][0]);
+          split_tf32(bv[0][1], bh[0][1], bl[0][1]);
+        }
         // small products first, pass-major so that consecutive MMAs are independent
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
+        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
+        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
 #pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
+        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
       }
     }
-    // every PR_FLUSH chunks the accumulators go to the compensated slots and restart
-    if ((it & (PR_FLUSH - 1)) == PR_FLUSH - 1) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        float2 v = slot[q];
-        kahan_add(v, c[q]);
-        slot[q] = v;
-        c[q] = 0.f;
-      }
+    for (int q = 0; q < 16; ++q) run[q] += c[q];
+    // round-robin flush: each FP32 running sum covers at most 16 chunks (1024 cells)
+    {
+      float x = 0.f;
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (q == fg) {
+          x = run[q];
+          run[q] = 0.f;
+        }
+      kahan_add(pre, x);
+      slot[fg] = pre;
     }
     __syncthreads();
   }
-  // the sums of the chunks since the last flush
+  // the running sums not flushed since their last turn
   if (!s_abort) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) kahan_add(slot[q], c[q]);
+    for (int q = 0; q < 16; ++q) kahan_add(slot[q], run[q]);
   }
-  // after an abort the prefetched stage may still be in flight: wait for it (bounded)
-  if (tid == 0 && s_abort) mbar_wait_bounded(bar0 + 8u * ((it + 1) & 1), (unsigned)((it + 1) >> 1) & 1u);
+  // after an abort the copies of the failed chunk and of the chunks staged ahead may still be in
+  // flight: wait for them (bounded) before the CTA's shared memory is released
+  if (tid == 0 && s_abort)
+    for (int k = it; k < issued; ++k) mbar_wait_bounded(bar0 + 8u * (k % NST), (unsigned)(k / NST) & 1u);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1022,17 +1068,29 @@ __global__ void k_pair_umma_final(const __grid_constant__ PairJob J, const float
 }
 
 static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) {
-  if (j.nb > 32 || 2 * j.nterm > TMA_MAXWARP || j.ng < 1 || j.ng > 256 || j.ncomp < 1) return false;
+  if (j.nb > 32 || (j.nb <= 16 ? 1 : 2) * j.nterm > TMA_MAXWARP || j.ng < 1 || j.ng > 256 || j.ncomp < 1)
+    return false;
   auto r1024 = [](size_t b) { return (b + 1023) / 1024 * 1024; };
-  const size_t fsz = (size_t)j.ncomp * 4096, gsz = r1024((size_t)j.ng * 128);
-  const size_t half = fsz + gsz, stage = 2 * half, hs = 2 * stage;
-  const size_t bar = (hs + (size_t)j.nh * PR_CH * 4 + 15) / 16 * 16;
+  const int mh = j.nb <= 16 ? 1 : 2, nt = j.nb <= 8 ? 1 : (j.nb <= 16 ? 2 : 4);
+  const int bh = std::max(16 * mh, 8 * nt);  // bins staged per component block
+  const size_t fsz = (size_t)j.ncomp * bh * 128, gsz = r1024((size_t)j.ng * 128);
+  const size_t half = fsz + gsz, stage = 2 * half;
   // tables read in the inner loops, copied to shared memory: side entries (int2 each), H-row
   // offsets, H entries (g, coef)
-  const size_t tab = bar + 16;
   const size_t tabsz = (size_t)j.s_off[j.nslot] * 8 + (size_t)(j.nh + 1) * 4 + (size_t)j.h_off[j.nh] * 8 + 16;
-  const size_t bytes = tab + tabsz + 1024;
-  if (bytes > 227 * 1024 - 256) return false;
+  const char* env = getenv("BISP_PAIR_STAGES");
+  int nst = env && atoi(env) == 2 ? 2 : 3;
+  size_t hs = 0, bar = 0, tab = 0, bytes = 0;
+  for (; nst >= 2; --nst) {
+    hs = (size_t)nst * stage;
+    bar = (hs + (size_t)j.nh * PR_CH * 4 + 15) / 16 * 16;
+    tab = bar + ((size_t)8 * nst + 15) / 16 * 16;
+    bytes = tab + tabsz + 1024;
+    if (bytes <= 227 * 1024 - 256) break;
+  }
+  if (nst < 2) return false;
+  L->nst = nst;
+  L->nblk = pair_blocks();
   L->tab = (unsigned)tab;
   L->fsz = (unsigned)fsz;
   L->gsz = (unsigned)gsz;
@@ -1045,8 +1103,11 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   L->gbox = j.ng;
   L->tx = (unsigned)(2 * (fsz + (size_t)j.ng * 128));
   L->stall = 0;
-  *ksplit = 4 * j.nterm <= TMA_MAXWARP ? 2 : 1;
-  *warps = 2 * j.nterm * *ksplit;
+  L->mh = mh;
+  L->nt = nt;
+  L->cblk = (unsigned)(bh * 128);
+  *ksplit = 2 * mh * j.nterm <= TMA_MAXWARP ? 2 : 1;
+  *warps = mh * j.nterm * *ksplit;
   return true;
 }
 
@@ -1194,11 +1255,11 @@ static CUtensorMap g_map(const float* base, int64_t Ng, int rows) {
 
 // component fields [nb][ncomp][Ng]: boxes of 32 cells x 1 component x 32 bins (bins >= nb
 // are filled with zeros), 128-byte swizzle
-static CUtensorMap f_map(const float* base, int64_t Ng, int ncomp, int nb) {
+static CUtensorMap f_map(const float* base, int64_t Ng, int ncomp, int nb, int bh = 32) {
   CUtensorMap m;
   const cuuint64_t dim[3] = {(cuuint64_t)Ng, (cuuint64_t)ncomp, (cuuint64_t)nb};
   const cuuint64_t stride[2] = {(cuuint64_t)Ng * sizeof(float), (cuuint64_t)Ng * ncomp * sizeof(float)};
-  const cuuint32_t box[3] = {32, 1, 32};
+  const cuuint32_t box[3] = {32, 1, (cuuint32_t)bh};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dim, stride, box,
                                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1240,7 +1301,7 @@ size_t pair_scratch_bytes(const PairJob& job) {
   TmaLayout L;
   int ksplit = 1, warps = 1;
   if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps))
-    return (size_t)pair_blocks() * warps * 32 * 16 * sizeof(float2) + 256;
+    return (size_t)L.nblk * warps * 32 * 16 * sizeof(float2) + 256;
   const PairLaunch c = pair_launch_cfg(j);
   return (size_t)c.nblk * c.warps * 32 * c.TM * c.TN * sizeof(double);
 }
@@ -1248,9 +1309,9 @@ size_t pair_scratch_bytes(const PairJob& job) {
 
 // final reduction for k_pair_tma (slots are compensated FP32 pairs (s, e), sum s - e): bin
 // (b1, b2) of term t (after the transpose (b1, b2) -> (b2, b1) of terms with T.tr) sits in warp
-// (t*ksplit + ks)*2 + b1/16, lane (b1%8)*4 + (b2%8)/2, slot (b2/8)*4 + ((b1/8)%2)*2 + b2%2
+// (t*ksplit + ks)*mh + b1/16, lane (b1%8)*4 + (b2%8)/2, slot (b2/8)*4 + ((b1/8)%2)*2 + b2%2
 __global__ void k_pair_tc_final(const __grid_constant__ PairJob J, const double* partials, int nblk, int warps,
-                                int ksplit, int nb, int nout, double* out) {
+                                int ksplit, int mh, int nb, int nout, double* out) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= nout * nb * nb) return;
   const int o = gw / (nb * nb), c1 = (gw / nb) % nb, c2 = gw % nb;
@@ -1262,7 +1323,7 @@ __global__ void k_pair_tc_final(const __grid_constant__ PairJob J, const double*
     const int q = (b2 / 8) * 4 + ((b1 / 8) % 2) * 2 + (b2 % 2);
     double s = 0.0;
     for (int ks = 0; ks < ksplit; ++ks) {
-      const int w = (t * ksplit + ks) * 2 + b1 / 16;
+      const int w = (t * ksplit + ks) * mh + b1 / 16;
       for (int c = lane; c < nblk; c += 32) {
         const float2 v = reinterpret_cast<const float2*>(partials)[(((size_t)c * warps + w) * 32 + ln) * 16 + q];
         s += (double)v.x - (double)v.y;
@@ -1341,20 +1402,30 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
   if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) {
     // the mma.sync kernel builds only A operands (see normalised)
     PairJob jt = normalised(j);
-    const int nblk = pair_blocks();
+    const int nblk = L.nblk;
     const size_t need = (size_t)nblk * warps * 32 * 16 * sizeof(float2);
     int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + need);
     BISP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb);
+    const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb, (int)(L.cblk / 128));
     const CUtensorMap mg = g_map(j.gfields, j.Ng, j.ng);
     L.stall = inject_stall("pair") ? 1 : 0;
-    BISP_CUDA(cudaFuncSetAttribute(k_pair_tma<32 * TMA_MAXWARP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)L.bytes));
-    mark(ev0);
-    k_pair_tma<32 * TMA_MAXWARP><<<nblk, warps * 32, L.bytes, s>>>(jt, mf, mg, L, ksplit, partials, err);
+    auto launch = [&](auto kern) {
+      BISP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));
+      mark(ev0);
+      kern<<<nblk, warps * 32, L.bytes, s>>>(jt, mf, mg, L, ksplit, partials, err);
+    };
+    if (L.nst == 3) {
+      if (L.mh == 2) launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 3>);
+      else if (L.nt == 2) launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 3>);
+      else launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 3>);
+    } else {
+      if (L.mh == 2) launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 2>);
+      else if (L.nt == 2) launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 2>);
+      else launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 2>);
+    }
     BISP_CHECK_LAUNCH();
     const int nout = j.nout * j.nb * j.nb;
-    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(jt, partials, nblk, warps, ksplit, j.nb, j.nout,
+    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(jt, partials, nblk, warps, ksplit, L.mh, j.nb, j.nout,
                                                                out_dev);
     BISP_CHECK_LAUNCH();
     mark(ev1);

@@ -775,6 +775,7 @@ void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const 
   if (n < 0) fail(BISP_EINVAL, "n < 0");
   if (n > 0 && !xyz) fail(BISP_EINVAL, "xyz is NULL");
   if (n >= (int64_t)0xffffffffLL) fail(BISP_EUNSUPPORTED, "more than 2^32-1 particles");
+  NvtxRange nv(which == BISP_DATA ? "bisp_assign data" : "bisp_assign randoms");
   Catalog& C = P->cat[which];
   cudaStream_t s = P->stream;
   int launches = 0;
@@ -1052,6 +1053,7 @@ void run_pair_terms(bisp_plan* P, const std::vector<const TermList*>& tl, int gs
   P->pairscr.ensure(sb, &P->bytes);
   const size_t ob = (size_t)J.nout * J.nb * J.nb * 8;
   P->pairout.ensure(ob, &P->bytes);
+  NvtxRange nv("contraction (mesh sum of F F G)");
   cudaEvent_t e0, e1;
   BISP_CUDA(cudaEventCreate(&e0));
   BISP_CUDA(cudaEventCreate(&e1));
@@ -1146,6 +1148,7 @@ void tune_zgroups(bisp_plan* P, InvBatch& b, int* launches) {
 // shell fields of bins [b0, b1) into the pool, bin b at pool bin slot b - b0 + slot; Dp: the
 // pass's delta n channel spectra (nullptr for unit shells)
 void shell_fields(bisp_plan* P, const float2* Dp, bool unit, int b0, int b1, int slot, int* launches) {
+  NvtxRange nv(unit ? "unit-shell fields" : "shell-filtered fields");
   const int nc = (int)P->comps.size();
   const int stride = P->pass_ncomp(unit);
   const float2* D00 = Dp ? Dp + (size_t)P->d00 * P->Nk : nullptr;
@@ -1231,7 +1234,7 @@ void shell_fields(bisp_plan* P, const float2* Dp, bool unit, int b0, int b1, int
         f.kind = SRC_SHELL_SUM;
         f.l = kf.l;
         f.ne = (int)kf.ent.size();
-        for (int q = 0; q < f.ne; ++q) {
+        for (int q = 0; q < f.ne && q < INV_MAXE; ++q) {
           f.ecoef[q] = std::get<0>(kf.ent[q]);
           f.em[q] = (signed char)std::get<1>(kf.ent[q]);
           f.epart[q] = (signed char)std::get<2>(kf.ent[q]);
@@ -1550,6 +1553,7 @@ void threept_combine(bisp_plan* P, int npass, const std::vector<double>& cD, con
 }
 
 void do_measure(bisp_plan* P, double* outB, double* outShot, double* outW, double* outWS, double* outNm) {
+  NvtxRange nv("bisp_measure");
   Catalog& G = P->cat[BISP_DATA];
   Catalog& R = P->cat[BISP_RANDOMS];
   if (!G.assigned) fail(BISP_ESTATE, "measure before the data catalogue was assigned");

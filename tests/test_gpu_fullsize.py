@@ -120,3 +120,47 @@ def test_survey512_full_size_spectra_and_properties():
         m = np.abs(bg[im]) > 0.01 * np.abs(bg[im]).max()
         assert np.max(np.abs(bl[im] - bg[im])[m] / np.abs(bg[im])[m]) <= 1e-4
     assert info["norm_I"] > 0
+
+
+def test_survey512_sampled_pairs_against_oracle():
+    """The headline workload at its full size, in bench.py's launch configuration: the 512^3
+    survey (local line of sight, FKP weights, TSC with interlacing, 1e6 galaxies and 5e7 randoms,
+    window pass) against FP64 oracle values at sampled bin pairs of B000, B202 (both orders of
+    l1 != l2) and B112, next to and at the top bin: B, its shot noise, the window bispectrum and its
+    shot noise.  The oracle values are stored in tests/golden/survey512_sampled_pairs.json, written
+    by tests/golden/make_survey512_sampled_pairs.py (the oracle only) from the same seeded
+    catalogues, whose checksums the test checks first."""
+    import hashlib
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "survey512_sampled_pairs.json")
+    gold = json.load(open(path))
+    w = bench.WORKLOADS["survey512"]
+    gw = gold["workload"]
+    assert gw["N"] == w["N"] and gw["L"] == w["L"] and gw["n_gen"] == w["n_gen"]
+    assert gw["n_gal"] == w["n_gal"] and gw["n_ran"] == w["n_ran"] and gw["P0"] == w["P0"]
+    assert np.allclose(gw["edges"], w["edges"]) and [tuple(e) for e in gw["ells"]] == w["ells"]
+    gal, ran = bench.make_inputs(w, seed=gw["seed"])
+    for nm, cat in (("gal", gal), ("ran", ran)):
+        for k in ("xyz", "nbar"):
+            dig = hashlib.sha256(np.ascontiguousarray(cat[k]).tobytes()).hexdigest()
+            assert dig == gold["catalogue_sha256"][f"{nm}_{k}"], f"{nm} {k}: the generator gives another catalogue"
+    with _plan_for(w) as plan:
+        plan.assign(bisp.DATA, _dev(gal["xyz"]), None, _dev(gal["nbar"]))
+        plan.assign(bisp.RANDOMS, _dev(ran["xyz"]), None, _dev(ran["nbar"]))
+        out = plan.measure()
+        info = plan.info()
+    assert info["norm_I"] == pytest.approx(gold["norm_I"], rel=1e-6)
+    assert info["alpha"] == pytest.approx(gold["alpha"], rel=1e-9)
+    for rec in gold["values"]:
+        im = w["ells"].index(tuple(rec["ells"]))
+        b1, b2 = rec["b1"], rec["b2"]
+        for key in ("B", "shot", "window", "window_shot"):
+            ref = rec[key]
+            got = out[key][im, b1, b2]
+            # bins with |value| below 1% of the multipole's largest |value| are outside the
+            # tolerance's scope (cancellation); the sampled pairs are chosen above it
+            scale = np.abs(out[key][im]).max()
+            if abs(ref) > 0.01 * scale:
+                assert abs(got - ref) <= TOL * abs(ref), (rec["ells"], b1, b2, key, got, ref)
