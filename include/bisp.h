@@ -162,7 +162,8 @@ typedef struct {
  * in one call: the result for plan i is what bisp_measure(plans[i], outs[i].B, ...) returns, bit
  * for bit.  Each plan must have its catalogues assigned, and a plan may appear once.  Up to 8 host
  * worker threads measure the plans concurrently, each plan on its own stream (plans share no
- * device state: every kernel launch carries its own job table), so the GPU overlaps the work of
+ * device buffers; the kernels' job tables are launch parameters, except the contraction's, which
+ * is held under a process-wide lock until its launches complete), so the GPU overlaps the work of
  * several realisations; the call returns when all are done.  Plans created on one shared stream
  * are serialised by that stream.  Errors: BISP_EINVAL for nplans < 0, NULL arrays or a repeated
  * plan; otherwise the status of the failing plan with the lowest index, with that index in the

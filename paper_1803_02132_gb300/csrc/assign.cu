@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_deposit(const uint32_t* __restri
   __shared__ uint32_t s_ts[NCELL + 1];         // position of each halo cell in the tile list
   __shared__ float s_w[NW][W][MAXP];           // 1D weights W_p(o + d) (mesh 0), W_p(o + d - 1/2) (mesh 1)
   __shared__ float s_val[NC][MAXP];
+  __shared__ unsigned char s_rz[MAXP];         // halo z index of each staged particle's cell
   __shared__ uint32_t s_wsum[DT_THREADS / 32];
   __shared__ int s_any;
   const int ntz = N / DT_Z, nty = N / DT_Y;
@@ -479,6 +480,7 @@ __global__ void __launch_bounds__(DT_THREADS) k_deposit(const uint32_t* __restri
         }
         const uint32_t g = s_gs[lo] + (q - s_ts[lo]);
         const float4 d = frac[g];
+        s_rz[q - b0] = (unsigned char)(lo % RZ);
         // 1D weights of this particle for every offset o (distance particle - node = o + d)
 #pragma unroll
         for (int o = OLO; o <= OHI; ++o) {
@@ -497,29 +499,29 @@ __global__ void __launch_bounds__(DT_THREADS) k_deposit(const uint32_t* __restri
           if (k < nchan) s_val[k][q - b0] = vals[(size_t)k * n + g];
       }
       __syncthreads();
-      // every (ox, oy, oz) in increasing order, each cell's particles in sorted order
+      // every (ox, oy) in increasing order; the node's W cells of that halo row are consecutive in
+      // the tile list, so one range holds them, oz ascending and each cell's particles in sorted
+      // order (the order of a cell-by-cell visit)
 #pragma unroll
       for (int ox = OLO; ox <= OHI; ++ox) {
 #pragma unroll
         for (int oy = OLO; oy <= OHI; ++oy) {
-          const int rbase = ((lx + ox - OLO) * RY + (ly + oy - OLO)) * RZ + (lz - OLO);
+          const int c = ((lx + ox - OLO) * RY + (ly + oy - OLO)) * RZ + lz;  // cell of oz = OLO
+          const uint32_t p0 = max(s_ts[c], b0), p1 = min(s_ts[c + W], b1);
+          const bool mxy = ox <= O0HI && oy <= O0HI;  // else mesh 0's weight is 0
+          for (uint32_t q = p0; q < p1; ++q) {
+            const uint32_t i = q - b0;
+            const int zo = (int)s_rz[i] - lz;  // oz - OLO
+            const bool m0 = mxy && zo + OLO <= O0HI;
+            float w0 = 0.f, w1 = 0.f;
+            if (m0) w0 = s_w[0][ox - OLO][i] * s_w[1][oy - OLO][i] * s_w[2][zo][i];
+            if (ILV) w1 = s_w[NW - 3][ox - OLO][i] * s_w[NW - 2][oy - OLO][i] * s_w[NW - 1][zo][i];
 #pragma unroll
-          for (int oz = OLO; oz <= OHI; ++oz) {
-            const bool m0 = ox <= O0HI && oy <= O0HI && oz <= O0HI;  // else mesh 0's weight is 0
-            const int c = rbase + oz;
-            const uint32_t p0 = max(s_ts[c], b0), p1 = min(s_ts[c + 1], b1);
-            for (uint32_t q = p0; q < p1; ++q) {
-              const uint32_t i = q - b0;
-              float w0 = 0.f, w1 = 0.f;
-              if (m0) w0 = s_w[0][ox - OLO][i] * s_w[1][oy - OLO][i] * s_w[2][oz - OLO][i];
-              if (ILV) w1 = s_w[NW - 3][ox - OLO][i] * s_w[NW - 2][oy - OLO][i] * s_w[NW - 1][oz - OLO][i];
-#pragma unroll
-              for (int k = 0; k < NC; ++k) {
-                if (k < nchan) {
-                  const float v = s_val[k][i];
-                  if (m0) a0[k] = fmaf(w0, v, a0[k]);
-                  if (ILV) a1[k] = fmaf(w1, v, a1[k]);
-                }
+            for (int k = 0; k < NC; ++k) {
+              if (k < nchan) {
+                const float v = s_val[k][i];
+                if (m0) a0[k] = fmaf(w0, v, a0[k]);
+                if (ILV) a1[k] = fmaf(w1, v, a1[k]);
               }
             }
           }

@@ -36,9 +36,9 @@ namespace bisp {
 // FP32 partials over at most PR_FLUSH chunks are added to lane-owned FP64 slots in global
 // memory; a second kernel reduces the slots in a fixed order.
 // ------------------------------------------------------------------------------------
-// Every kernel takes its PairJob as a __grid_constant__ parameter (about 22 KB, inside the 32 KB
-// parameter space): each launch carries its own copy, so launches of different plans, streams or
-// host threads never share a job table.
+// The FMA and tcgen05 kernels take their PairJob as a __grid_constant__ parameter (about 22 KB,
+// inside the 32 KB parameter space): each launch carries its own copy.  The TMA kernel reads it from
+// a constant-memory slot held under a lock until its launches complete (see c_pj below).
 constexpr int PR_CH = 64;          // cells per chunk
 constexpr int PR_LD = PR_CH + 4;   // padded row (bank spread for 16-byte loads)
 constexpr int PR_FLUSH = 16;       // chunks per FP32 partial (<= 1024 cells)
@@ -440,7 +440,6 @@ struct TmaLayout {
   unsigned tx;        // transaction bytes per stage
   int ncomp, gbox;    // F blocks per half, G rows
   int stall;          // test knob: start no stage copy, so that every bounded wait runs out
-  unsigned tab;       // offset of the side and H-row tables copied from the job
   int nst;            // stages (chunks staged ahead + 1): 3 when shared memory allows, else 2
   int nblk;           // CTAs of the launch
   int mh, nt;         // 16-row tiles and 8-column tiles per term (bins covered: 16 mh, 8 nt)
@@ -544,13 +543,23 @@ __device__ __forceinline__ void kahan_add(float2& v, float x) {
   v.y = (t - v.x) - y;
   v.x = t;
 }
+// The TMA kernel and its final reduction read their job from module constant memory: its warp-
+// uniform table reads in the inner loops are constant-cache hits, measurably faster (4 % of the
+// kernel) than the same reads from a kernel parameter or shared memory.  The one slot is guarded
+// by g_pj_mu from the copy into it until the launches that read it have completed, so that plans
+// driven from several host threads never overwrite a job in use (their contractions serialise;
+// one contraction fills the GPU).
+__constant__ PairJob c_pj;
+static std::mutex g_pj_mu;
+
 // MH 16-row tiles (b1) and NT 8-column tiles (b2) per term: (2, 4) covers 32 bins; launches over
 // few bins (blocked unions, small bin sets) take (1, 2) for 16 bins or (1, 1) for 8, so that
 // their MMAs and staged bytes shrink with the bins.
 template <int NTHR, int MH, int NT, int NST>
 __global__ void __launch_bounds__(NTHR, 1)
-    k_pair_tma(const __grid_constant__ PairJob J, const __grid_constant__ CUtensorMap tmF,
-               const __grid_constant__ CUtensorMap tmG, const TmaLayout L, int ksplit, double* partials, int* err) {
+    k_pair_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const TmaLayout L,
+               int ksplit, double* partials, int* err) {
+  const PairJob& J = c_pj;
   extern __shared__ unsigned char dsm[];
   __shared__ int s_abort;
   const unsigned raw0 = smem_u32(dsm);
@@ -572,15 +581,6 @@ __global__ void __launch_bounds__(NTHR, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
-  // the tables the inner loops read (warp-uniform addresses: shared-memory broadcasts): side
-  // entries as (component block offset, H row offset), H-row bounds, H entries (g, coef)
-  const int nse = J.s_off[J.nslot], nhe = J.h_off[J.nh];
-  int2* const s_se = reinterpret_cast<int2*>(gb + L.tab);
-  int* const s_ho = reinterpret_cast<int*>(s_se + nse);
-  int2* const s_he = reinterpret_cast<int2*>(gb + ((L.tab + (unsigned)nse * 8u + (unsigned)(J.nh + 1) * 4u + 7u) & ~7u));
-  for (int i = tid; i < nse; i += blockDim.x) s_se[i] = make_int2(J.s_ent[i][0] * (int)L.cblk, J.s_ent[i][1] * chc);
-  for (int i = tid; i <= J.nh; i += blockDim.x) s_ho[i] = J.h_off[i];
-  for (int i = tid; i < nhe; i += blockDim.x) s_he[i] = make_int2(J.h_ent[i].g, __float_as_int(J.h_ent[i].coef));
   __syncthreads();
   auto issue = [&](int64_t ch, int st) {  // thread 0 only
     if (L.stall) return;
@@ -628,28 +628,36 @@ __global__ void __launch_bounds__(NTHR, 1)
   const int hfirst = ksplit == 2 ? ks : 0, hlast = ksplit == 2 ? ks + 1 : 2;
 
   // NST - 1 chunks staged ahead; chunk index it uses stage it % NST, phase (it / NST) & 1
-  int issued = 0;  // thread 0: chunks whose copies were started
-  if (tid == 0)
-    for (int k = 0; k < NST - 1; ++k)
-      if (blockIdx.x + (int64_t)k * gridDim.x < nchunk) {
-        issue(blockIdx.x + (int64_t)k * gridDim.x, k);
-        ++issued;
-      }
+  int issued = 0;  // thread 0: chunks whose copies were started (NST > 2)
+  if constexpr (NST == 2) {
+    if (tid == 0 && blockIdx.x < nchunk) issue(blockIdx.x, 0);
+  } else {
+    if (tid == 0)
+      for (int k = 0; k < NST - 1; ++k)
+        if (blockIdx.x + (int64_t)k * gridDim.x < nchunk) {
+          issue(blockIdx.x + (int64_t)k * gridDim.x, k);
+          ++issued;
+        }
+  }
   int it = 0;
   for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x, ++it) {
-    const int st = it % NST;
+    const int st = NST == 2 ? (it & 1) : it % NST;
     // the stage of chunk it + NST - 1 was last read by chunk it - 1, before the barrier ending it
     const int64_t nx = ch + (int64_t)(NST - 1) * gridDim.x;
     if (tid == 0 && nx < nchunk) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(nx, (it + NST - 1) % NST);
-      ++issued;
+      if constexpr (NST == 2) {
+        issue(nx, st ^ 1);
+      } else {
+        issue(nx, (it + NST - 1) % NST);
+        ++issued;
+      }
     }
     // slot it % 16 is flushed at the end of this chunk; load it now so that the L2 round
     // trip overlaps the chunk's work
     const int fg = it & 15;
     float2 pre = slot[fg];
-    if (!mbar_wait_bounded(bar0 + 8u * st, (unsigned)(it / NST) & 1u)) {
+    if (!mbar_wait_bounded(bar0 + 8u * st, NST == 2 ? ((unsigned)it >> 1) & 1u : (unsigned)(it / NST) & 1u)) {
       s_abort = 1;
       atomicExch(err, 1);
     }
@@ -659,11 +667,11 @@ __global__ void __launch_bounds__(NTHR, 1)
       const int h = i >> 4, q = i & 15, hh = q >> 3, p = q & 7;
       const unsigned char* g0 = gb + sbo + hh * L.half + L.fsz;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int e = s_ho[h]; e < s_ho[h + 1]; ++e) {
-        const int2 R = s_he[e];
-        const float coef = __int_as_float(R.y);
-        if (R.x >= 0) {
-          const float4 gv = *reinterpret_cast<const float4*>(g0 + swz(R.x, p));
+      for (int e = J.h_off[h]; e < J.h_off[h + 1]; ++e) {
+        const PairRecipe R = J.h_ent[e];
+        const float coef = R.coef;
+        if (R.g >= 0) {
+          const float4 gv = *reinterpret_cast<const float4*>(g0 + swz(R.g, p));
           v.x = fmaf(coef, gv.x, v.x);
           v.y = fmaf(coef, gv.y, v.y);
           v.z = fmaf(coef, gv.z, v.z);
@@ -699,9 +707,8 @@ __global__ void __launch_bounds__(NTHR, 1)
           float s4[4] = {0.f, 0.f, 0.f, 0.f};
           for (int e = e0; e < e1; ++e) {
             uint32_t v[4];
-            const int2 se = s_se[e];
-            ldsm_x4(fh + (unsigned)se.x + loffA + poffA[kk], v);
-            const float2 hv = *reinterpret_cast<const float2*>(hr + se.y + 8 * kk);
+            ldsm_x4(fh + (unsigned)J.s_ent[e][0] * L.cblk + loffA + poffA[kk], v);
+            const float2 hv = *reinterpret_cast<const float2*>(hr + J.s_ent[e][1] * chc + 8 * kk);
             s4[0] = fmaf(__uint_as_float(v[0]), hv.x, s4[0]);
             s4[1] = fmaf(__uint_as_float(v[1]), hv.x, s4[1]);
             s4[2] = fmaf(__uint_as_float(v[2]), hv.y, s4[2]);
@@ -762,8 +769,13 @@ __global__ void __launch_bounds__(NTHR, 1)
   }
   // after an abort the copies of the failed chunk and of the chunks staged ahead may still be in
   // flight: wait for them (bounded) before the CTA's shared memory is released
-  if (tid == 0 && s_abort)
-    for (int k = it; k < issued; ++k) mbar_wait_bounded(bar0 + 8u * (k % NST), (unsigned)(k / NST) & 1u);
+  if (tid == 0 && s_abort) {
+    if constexpr (NST == 2) {  // chunks it and it + 1 (a wait for a copy never started runs out)
+      for (int k = it; k <= it + 1; ++k) mbar_wait_bounded(bar0 + 8u * (k & 1), ((unsigned)k >> 1) & 1u);
+    } else {
+      for (int k = it; k < issued; ++k) mbar_wait_bounded(bar0 + 8u * (k % NST), (unsigned)(k / NST) & 1u);
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -1075,23 +1087,18 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   const int bh = std::max(16 * mh, 8 * nt);  // bins staged per component block
   const size_t fsz = (size_t)j.ncomp * bh * 128, gsz = r1024((size_t)j.ng * 128);
   const size_t half = fsz + gsz, stage = 2 * half;
-  // tables read in the inner loops, copied to shared memory: side entries (int2 each), H-row
-  // offsets, H entries (g, coef)
-  const size_t tabsz = (size_t)j.s_off[j.nslot] * 8 + (size_t)(j.nh + 1) * 4 + (size_t)j.h_off[j.nh] * 8 + 16;
   const char* env = getenv("BISP_PAIR_STAGES");
   int nst = env && atoi(env) == 2 ? 2 : 3;
-  size_t hs = 0, bar = 0, tab = 0, bytes = 0;
+  size_t hs = 0, bar = 0, bytes = 0;
   for (; nst >= 2; --nst) {
     hs = (size_t)nst * stage;
     bar = (hs + (size_t)j.nh * PR_CH * 4 + 15) / 16 * 16;
-    tab = bar + ((size_t)8 * nst + 15) / 16 * 16;
-    bytes = tab + tabsz + 1024;
+    bytes = bar + ((size_t)8 * nst + 15) / 16 * 16 + 1024;
     if (bytes <= 227 * 1024 - 256) break;
   }
   if (nst < 2) return false;
   L->nst = nst;
   L->nblk = pair_blocks();
-  L->tab = (unsigned)tab;
   L->fsz = (unsigned)fsz;
   L->gsz = (unsigned)gsz;
   L->half = (unsigned)half;
@@ -1106,7 +1113,10 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   L->mh = mh;
   L->nt = nt;
   L->cblk = (unsigned)(bh * 128);
-  *ksplit = 2 * mh * j.nterm <= TMA_MAXWARP ? 2 : 1;
+  // cell halves split over warps when the warps fit; BISP_PAIR_KSPLIT=1 keeps one warp per (term,
+  // row tile) over both halves (half the warps, twice the registers per thread)
+  const char* eks = getenv("BISP_PAIR_KSPLIT");
+  *ksplit = (!eks || atoi(eks) != 1) && 2 * mh * j.nterm <= TMA_MAXWARP ? 2 : 1;
   *warps = mh * j.nterm * *ksplit;
   return true;
 }
@@ -1310,8 +1320,9 @@ size_t pair_scratch_bytes(const PairJob& job) {
 // final reduction for k_pair_tma (slots are compensated FP32 pairs (s, e), sum s - e): bin
 // (b1, b2) of term t (after the transpose (b1, b2) -> (b2, b1) of terms with T.tr) sits in warp
 // (t*ksplit + ks)*mh + b1/16, lane (b1%8)*4 + (b2%8)/2, slot (b2/8)*4 + ((b1/8)%2)*2 + b2%2
-__global__ void k_pair_tc_final(const __grid_constant__ PairJob J, const double* partials, int nblk, int warps,
-                                int ksplit, int mh, int nb, int nout, double* out) {
+__global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int ksplit, int mh, int nb, int nout,
+                                double* out) {
+  const PairJob& J = c_pj;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= nout * nb * nb) return;
   const int o = gw / (nb * nb), c1 = (gw / nb) % nb, c2 = gw % nb;
@@ -1409,24 +1420,29 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
     const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb, (int)(L.cblk / 128));
     const CUtensorMap mg = g_map(j.gfields, j.Ng, j.ng);
     L.stall = inject_stall("pair") ? 1 : 0;
+    // the constant slot is ours from the copy until the synchronisation at the end of this call
+    std::lock_guard<std::mutex> lk(g_pj_mu);
+    BISP_CUDA(cudaMemcpyToSymbolAsync(c_pj, &jt, sizeof(PairJob), 0, cudaMemcpyHostToDevice, s));
     auto launch = [&](auto kern) {
       BISP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));
       mark(ev0);
-      kern<<<nblk, warps * 32, L.bytes, s>>>(jt, mf, mg, L, ksplit, partials, err);
+      kern<<<nblk, warps * 32, L.bytes, s>>>(mf, mg, L, ksplit, partials, err);
     };
+    // launches of at most 10 warps take the instance bounded at 320 threads (more registers per
+    // thread for the unrolled k steps)
+    const bool small = warps <= 10;
     if (L.nst == 3) {
-      if (L.mh == 2) launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 3>);
-      else if (L.nt == 2) launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 3>);
-      else launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 3>);
+      if (L.mh == 2) small ? launch(k_pair_tma<320, 2, 4, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 3>);
+      else if (L.nt == 2) small ? launch(k_pair_tma<320, 1, 2, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 3>);
+      else small ? launch(k_pair_tma<320, 1, 1, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 3>);
     } else {
-      if (L.mh == 2) launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 2>);
-      else if (L.nt == 2) launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 2>);
-      else launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 2>);
+      if (L.mh == 2) small ? launch(k_pair_tma<320, 2, 4, 2>) : launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 2>);
+      else if (L.nt == 2) small ? launch(k_pair_tma<320, 1, 2, 2>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 2>);
+      else small ? launch(k_pair_tma<320, 1, 1, 2>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 2>);
     }
     BISP_CHECK_LAUNCH();
     const int nout = j.nout * j.nb * j.nb;
-    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(jt, partials, nblk, warps, ksplit, L.mh, j.nb, j.nout,
-                                                               out_dev);
+    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(partials, nblk, warps, ksplit, L.mh, j.nb, j.nout, out_dev);
     BISP_CHECK_LAUNCH();
     mark(ev1);
     int herr = 0;

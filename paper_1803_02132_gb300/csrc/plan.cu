@@ -2059,8 +2059,9 @@ bisp_status bisp_measure_batch(bisp_plan* const* plans, const bisp_outputs* outs
   }
   if (nplans == 0) return BISP_OK;
   // Host worker threads measure the plans concurrently, each plan on its own stream, so that the
-  // GPU overlaps the small kernels and host round trips of many realisations.  Every launch
-  // carries its own job table, so plans share no device state.
+  // GPU overlaps the small kernels and host round trips of many realisations.  Plans share no
+  // device buffers; job tables are launch parameters, or (the contraction's) a constant slot held
+  // under a lock until its launches complete.
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     g_err = "bisp_measure_batch: cudaGetDevice failed";
