@@ -434,7 +434,7 @@ struct TmaLayout {
   unsigned fsz, gsz;  // bytes of the F blocks (ncomp x 4096) and of the G block of one half
   unsigned half;      // fsz + gsz
   unsigned stage;     // 2 * half
-  unsigned hs;        // offset of the H rows [nh][64 floats], fragment order
+  unsigned hs;        // offset of the H rows, two buffers [2][nh][64 floats], fragment order
   unsigned bar;       // offset of the two mbarriers
   unsigned bytes;     // dynamic shared memory to request (includes 1024 B alignment slack)
   unsigned tx;        // transaction bytes per stage
@@ -552,6 +552,94 @@ __device__ __forceinline__ void kahan_add(float2& v, float x) {
 __constant__ PairJob c_pj;
 static std::mutex g_pj_mu;
 
+// A warp's fragment addressing: ldmatrix row offsets and swizzled pieces, its term's sides
+struct PairFrag {
+  unsigned loffA, loffB[2], poffA[4], poffB[4];
+  unsigned xoff, yoff;  // bare X (when not built) and Y component blocks
+  int e0, e1;           // entries of the built X side
+  int tq;
+  bool xb;
+};
+
+// The products of NH consecutive 32-cell halves (from h0) of one staged chunk, accumulated into
+// c.  The built sides of all NH halves and four k steps are formed in one pass over the side's
+// entries (one table read and address per entry; the shared-memory loads are independent), then
+// every k step loads and splits the bare side and issues its 3 NT MMAs.
+template <int NT, int NH>
+__device__ __forceinline__ void pair_halves(float (&c)[16], const PairJob& J, const TmaLayout& L, unsigned sb,
+                                            int h0, const float* Hs, const PairFrag& F) {
+  uint32_t av[NH][4][4];
+  if (F.xb) {
+    // built side sum_(c,h) F_c(b, x) H_h(x) for this lane's fragment cells
+    float s4[NH][4][4];
+#pragma unroll
+    for (int hh = 0; hh < NH; ++hh)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s4[hh][u][0] = s4[hh][u][1] = s4[hh][u][2] = s4[hh][u][3] = 0.f;
+    for (int e = F.e0; e < F.e1; ++e) {
+      const unsigned ao = sb + (unsigned)J.s_ent[e][0] * L.cblk + F.loffA;
+      const float* hp = Hs + J.s_ent[e][1] * PR_CH + 2 * F.tq;
+#pragma unroll
+      for (int hh = 0; hh < NH; ++hh) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          uint32_t v[4];
+          ldsm_x4(ao + (unsigned)(h0 + hh) * L.half + F.poffA[u], v);
+          const float2 hv = *reinterpret_cast<const float2*>(hp + (h0 + hh) * 32 + 8 * u);
+          s4[hh][u][0] = fmaf(__uint_as_float(v[0]), hv.x, s4[hh][u][0]);
+          s4[hh][u][1] = fmaf(__uint_as_float(v[1]), hv.x, s4[hh][u][1]);
+          s4[hh][u][2] = fmaf(__uint_as_float(v[2]), hv.y, s4[hh][u][2]);
+          s4[hh][u][3] = fmaf(__uint_as_float(v[3]), hv.y, s4[hh][u][3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int hh = 0; hh < NH; ++hh)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) av[hh][u][e] = __float_as_uint(s4[hh][u][e]);
+  } else {
+#pragma unroll
+    for (int hh = 0; hh < NH; ++hh)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ldsm_x4(sb + (unsigned)(h0 + hh) * L.half + F.xoff + F.loffA + F.poffA[u], av[hh][u]);
+  }
+#pragma unroll
+  for (int hh = 0; hh < NH; ++hh) {
+    const unsigned fh = sb + (unsigned)(h0 + hh) * L.half + F.yoff;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      uint32_t bv[2][4];
+      if (NT >= 2) {
+#pragma unroll
+        for (int i = 0; i < NT / 2; ++i) ldsm_x4(fh + F.loffB[i] + F.poffB[kk], bv[i]);
+      } else {  // one n tile: matrices (k 0-3, k 4-7) of rows 0-7, addresses from lanes 0-15
+        ldsm_x2(fh + F.loffB[0] + F.poffB[kk], bv[0]);
+      }
+      uint32_t ah[4], al[4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split_tf32(av[hh][kk][e], ah[e], al[e]);
+      if (NT >= 2) {
+#pragma unroll
+        for (int i = 0; i < NT / 2; ++i)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
+      } else {
+        split_tf32(bv[0][0], bh[0][0], bl[0][0]);
+        split_tf32(bv[0][1], bh[0][1], bl[0][1]);
+      }
+      // small products first, pass-major so that consecutive MMAs are independent
+#pragma unroll
+      for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
+#pragma unroll
+      for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
+#pragma unroll
+      for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
+    }
+  }
+}
+
 // MH 16-row tiles (b1) and NT 8-column tiles (b2) per term: (2, 4) covers 32 bins; launches over
 // few bins (blocked unions, small bin sets) take (1, 2) for 16 bins or (1, 1) for 8, so that
 // their MMAs and staged bytes shrink with the bins.
@@ -561,11 +649,11 @@ __global__ void __launch_bounds__(NTHR, 1)
                int ksplit, double* partials, int* err) {
   const PairJob& J = c_pj;
   extern __shared__ unsigned char dsm[];
-  __shared__ int s_abort;
+  __shared__ int s_abort[2];  // per chunk parity (see the barrier below)
   const unsigned raw0 = smem_u32(dsm);
   const unsigned base = (raw0 + 1023u) & ~1023u;
   unsigned char* const gb = dsm + (base - raw0);  // generic pointer to the aligned base
-  float* const Hs = reinterpret_cast<float*>(gb + L.hs);
+  float* const Hs0 = reinterpret_cast<float*>(gb + L.hs);
   const unsigned bar0 = base + L.bar;
   constexpr int chc = PR_CH;  // cells per chunk: two 32-cell halves
   const int64_t nchunk = J.Ng / chc;
@@ -579,11 +667,13 @@ __global__ void __launch_bounds__(NTHR, 1)
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     for (int k = 0; k < NST; ++k) mbar_init(bar0 + 8u * k, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = 0;
+    s_abort[0] = s_abort[1] = 0;
   }
   __syncthreads();
+  int issued = 0;                         // thread 0: chunks whose copies were started
   auto issue = [&](int64_t ch, int st) {  // thread 0 only
     if (L.stall) return;
+    ++issued;
     const unsigned bar = bar0 + 8u * st;
     mbar_expect_tx(bar, L.tx);
     for (int h = 0; h < 2; ++h) {
@@ -625,45 +715,33 @@ __global__ void __launch_bounds__(NTHR, 1)
   const bool xb = T.xslot >= 0;
   const int e0 = xb ? J.s_off[T.xslot] : 0, e1 = xb ? J.s_off[T.xslot + 1] : 0;
   const unsigned xoff = xb ? 0u : (unsigned)T.xdir * L.cblk, yoff = (unsigned)T.ydir * L.cblk;
-  const int hfirst = ksplit == 2 ? ks : 0, hlast = ksplit == 2 ? ks + 1 : 2;
 
-  // NST - 1 chunks staged ahead; chunk index it uses stage it % NST, phase (it / NST) & 1
-  int issued = 0;  // thread 0: chunks whose copies were started (NST > 2)
-  if constexpr (NST == 2) {
-    if (tid == 0 && blockIdx.x < nchunk) issue(blockIdx.x, 0);
-  } else {
-    if (tid == 0)
-      for (int k = 0; k < NST - 1; ++k)
-        if (blockIdx.x + (int64_t)k * gridDim.x < nchunk) {
-          issue(blockIdx.x + (int64_t)k * gridDim.x, k);
-          ++issued;
-        }
-  }
+  // NST - 1 chunks staged ahead; chunk index it uses stage it % NST, phase (it / NST) & 1.
+  // One barrier per chunk: once every thread has passed the barrier of chunk it, every warp
+  // has finished chunk it - 1, so its stage takes chunk it + NST - 1 and its H buffer (it + 1) & 1
+  // is free.  The abort flag of chunk it is s_abort[it & 1]: a thread that sets the flag of
+  // chunk it + 1 has passed the barrier of chunk it, so every thread has read the same slot for
+  // chunk it - 1 before.
+  if (tid == 0)
+    for (int k = 0; k < NST - 1; ++k)
+      if (blockIdx.x + (int64_t)k * gridDim.x < nchunk) issue(blockIdx.x + (int64_t)k * gridDim.x, k);
+  const int nhi = J.nh << 4;
   int it = 0;
   for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x, ++it) {
     const int st = NST == 2 ? (it & 1) : it % NST;
-    // the stage of chunk it + NST - 1 was last read by chunk it - 1, before the barrier ending it
-    const int64_t nx = ch + (int64_t)(NST - 1) * gridDim.x;
-    if (tid == 0 && nx < nchunk) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if constexpr (NST == 2) {
-        issue(nx, st ^ 1);
-      } else {
-        issue(nx, (it + NST - 1) % NST);
-        ++issued;
-      }
-    }
     // slot it % 16 is flushed at the end of this chunk; load it now so that the L2 round
     // trip overlaps the chunk's work
     const int fg = it & 15;
     float2 pre = slot[fg];
     if (!mbar_wait_bounded(bar0 + 8u * st, NST == 2 ? ((unsigned)it >> 1) & 1u : (unsigned)(it / NST) & 1u)) {
-      s_abort = 1;
+      s_abort[it & 1] = 1;
       atomicExch(err, 1);
     }
     const unsigned sbo = st * L.stage;  // offset of this stage
-    // (1) H rows, stored per half as [kk][tq][cell tq | cell tq+4]
-    for (int i = tid; i < (J.nh << 4); i += blockDim.x) {
+    float* const Hs = Hs0 + (it & 1) * (J.nh * chc);
+    // (1) H rows, stored per half as [kk][tq][cell tq | cell tq+4]; the items go to the last
+    // threads first (the host orders terms heaviest first, so these are the lightest warps)
+    for (int i = (int)blockDim.x - 1 - tid; i < nhi; i += blockDim.x) {
       const int h = i >> 4, q = i & 15, hh = q >> 3, p = q & 7;
       const unsigned char* g0 = gb + sbo + hh * L.half + L.fsz;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -691,91 +769,52 @@ __global__ void __launch_bounds__(NTHR, 1)
       d[6] = v.w;
     }
     __syncthreads();
-    if (s_abort) break;
+    if (s_abort[it & 1]) break;
+    const int64_t nx = ch + (int64_t)(NST - 1) * gridDim.x;
+    if (tid == 0 && nx < nchunk) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(nx, NST == 2 ? (st ^ 1) : (it + NST - 1) % NST);
+    }
     // (2) this warp's 16 x 32 block of its term over its cell half (or both halves)
     float c[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) c[q] = 0.f;
-    for (int hh = hfirst; hh < hlast; ++hh) {
-      const unsigned fh = base + sbo + hh * L.half;
-      const float* hr = Hs + hh * 32 + 2 * tq;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        uint32_t av[4], bv[2][4];
-        if (xb) {
-          // built side sum_(c,h) F_c(b, x) H_h(x) for this lane's fragment cells
-          float s4[4] = {0.f, 0.f, 0.f, 0.f};
-          for (int e = e0; e < e1; ++e) {
-            uint32_t v[4];
-            ldsm_x4(fh + (unsigned)J.s_ent[e][0] * L.cblk + loffA + poffA[kk], v);
-            const float2 hv = *reinterpret_cast<const float2*>(hr + J.s_ent[e][1] * chc + 8 * kk);
-            s4[0] = fmaf(__uint_as_float(v[0]), hv.x, s4[0]);
-            s4[1] = fmaf(__uint_as_float(v[1]), hv.x, s4[1]);
-            s4[2] = fmaf(__uint_as_float(v[2]), hv.y, s4[2]);
-            s4[3] = fmaf(__uint_as_float(v[3]), hv.y, s4[3]);
-          }
-#pragma unroll
-          for (int e = 0; e < 4; ++e) av[e] = __float_as_uint(s4[e]);
-        } else {
-          ldsm_x4(fh + xoff + loffA + poffA[kk], av);
-        }
-        if (NT >= 2) {
-#pragma unroll
-          for (int i = 0; i < NT / 2; ++i) ldsm_x4(fh + yoff + loffB[i] + poffB[kk], bv[i]);
-        } else {  // one n tile: matrices (k 0-3, k 4-7) of rows 0-7, addresses from lanes 0-15
-          ldsm_x2(fh + yoff + loffB[0] + poffB[kk], bv[0]);
-        }
-        uint32_t ah[4], al[4], bh[4][2], bl[4][2];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) split_tf32(av[e], ah[e], al[e]);
-        if (NT >= 2) {
-#pragma unroll
-          for (int i = 0; i < NT / 2; ++i)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
-        } else {
-          split_tf32(bv[0][0], bh[0][0], bl[0][0]);
-          split_tf32(bv[0][1], bh[0][1], bl[0][1]);
-        }
-        // small products first, pass-major so that consecutive MMAs are independent
-#pragma unroll
-        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
-#pragma unroll
-        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
-#pragma unroll
-        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
-      }
-    }
+    const PairFrag F{loffA, {loffB[0], loffB[1]}, {poffA[0], poffA[1], poffA[2], poffA[3]},
+                     {poffB[0], poffB[1], poffB[2], poffB[3]}, xoff, yoff, e0, e1, tq, xb};
+    if (ksplit == 1)
+      pair_halves<NT, 2>(c, J, L, base + sbo, 0, Hs, F);
+    else
+      pair_halves<NT, 1>(c, J, L, base + sbo, ks, Hs, F);
 #pragma unroll
     for (int q = 0; q < 16; ++q) run[q] += c[q];
-    // round-robin flush: each FP32 running sum covers at most 16 chunks (1024 cells)
+    // round-robin flush: each FP32 running sum covers at most 16 chunks (1024 cells); fg is
+    // warp-uniform, so the switch is one indexed branch
     {
       float x = 0.f;
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (q == fg) {
-          x = run[q];
-          run[q] = 0.f;
-        }
+      switch (fg) {
+#define BISP_TAKE(q) \
+  case q:            \
+    x = run[q];      \
+    run[q] = 0.f;    \
+    break;
+        BISP_TAKE(0) BISP_TAKE(1) BISP_TAKE(2) BISP_TAKE(3) BISP_TAKE(4) BISP_TAKE(5) BISP_TAKE(6) BISP_TAKE(7)
+        BISP_TAKE(8) BISP_TAKE(9) BISP_TAKE(10) BISP_TAKE(11) BISP_TAKE(12) BISP_TAKE(13) BISP_TAKE(14) BISP_TAKE(15)
+#undef BISP_TAKE
+      }
       kahan_add(pre, x);
       slot[fg] = pre;
     }
-    __syncthreads();
   }
+  const bool aborted = it < (nchunk - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x;  // left at a break
   // the running sums not flushed since their last turn
-  if (!s_abort) {
+  if (!aborted) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) kahan_add(slot[q], run[q]);
   }
   // after an abort the copies of the failed chunk and of the chunks staged ahead may still be in
   // flight: wait for them (bounded) before the CTA's shared memory is released
-  if (tid == 0 && s_abort) {
-    if constexpr (NST == 2) {  // chunks it and it + 1 (a wait for a copy never started runs out)
-      for (int k = it; k <= it + 1; ++k) mbar_wait_bounded(bar0 + 8u * (k & 1), ((unsigned)k >> 1) & 1u);
-    } else {
-      for (int k = it; k < issued; ++k) mbar_wait_bounded(bar0 + 8u * (k % NST), (unsigned)(k / NST) & 1u);
-    }
-  }
+  if (tid == 0 && aborted)
+    for (int k = it; k < issued; ++k) mbar_wait_bounded(bar0 + 8u * (k % NST), (unsigned)(k / NST) & 1u);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1092,7 +1131,7 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   size_t hs = 0, bar = 0, bytes = 0;
   for (; nst >= 2; --nst) {
     hs = (size_t)nst * stage;
-    bar = (hs + (size_t)j.nh * PR_CH * 4 + 15) / 16 * 16;
+    bar = (hs + 2 * (size_t)j.nh * PR_CH * 4 + 15) / 16 * 16;
     bytes = bar + ((size_t)8 * nst + 15) / 16 * 16 + 1024;
     if (bytes <= 227 * 1024 - 256) break;
   }
@@ -1113,10 +1152,14 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   L->mh = mh;
   L->nt = nt;
   L->cblk = (unsigned)(bh * 128);
-  // cell halves split over warps when the warps fit; BISP_PAIR_KSPLIT=1 keeps one warp per (term,
-  // row tile) over both halves (half the warps, twice the registers per thread)
+  // cell halves split over warps only when the warps still fit the 320-thread instance: one warp
+  // per (term, row tile) over both halves runs with more registers per thread, which measured
+  // faster than twice the warps (survey 512^3: 146.5 against 150.3 ms per step);
+  // BISP_PAIR_KSPLIT=1 or 2 forces the choice (2 while the warps fit the launch)
   const char* eks = getenv("BISP_PAIR_KSPLIT");
-  *ksplit = (!eks || atoi(eks) != 1) && 2 * mh * j.nterm <= TMA_MAXWARP ? 2 : 1;
+  const int force = eks ? atoi(eks) : 0;
+  const bool two = force == 2 ? 2 * mh * j.nterm <= TMA_MAXWARP : (force != 1 && 2 * mh * j.nterm <= 10);
+  *ksplit = two ? 2 : 1;
   *warps = mh * j.nterm * *ksplit;
   return true;
 }
@@ -1215,6 +1258,26 @@ bool pair_split_gsets() { return pair_use_umma(); }
 
 // a job with its terms normalised for the tensor-core kernels: the built side is X (a term
 // with a built Y is computed as Y X^T and read back transposed)
+// Terms reordered by the entries of their built side, heaviest first (stable), with the output
+// table remapped: the TMA kernel hands the per-chunk H rows to the last warps, i.e. the lightest
+// terms, which keeps the warps' work per chunk level.
+static void heavy_first(PairJob& j) {
+  int perm[64], inv[64];
+  auto weight = [&](int t) {
+    const int x = j.term[t].xslot;
+    return x >= 0 ? j.s_off[x + 1] - j.s_off[x] : 0;
+  };
+  for (int t = 0; t < j.nterm; ++t) perm[t] = t;
+  std::stable_sort(perm, perm + j.nterm, [&](int a, int b) { return weight(a) > weight(b); });
+  const PairJob src = j;
+  for (int n = 0; n < j.nterm; ++n) {
+    j.term[n] = src.term[perm[n]];
+    j.term_out[n] = src.term_out[perm[n]];
+    inv[perm[n]] = n;
+  }
+  for (int e = 0; e < j.out_ent_off[j.nout]; ++e) j.out_ent_term[e] = inv[src.out_ent_term[e]];
+}
+
 static PairJob normalised(const PairJob& j) {
   PairJob jt = j;
   for (int t = 0; t < jt.nterm; ++t) {
@@ -1413,6 +1476,7 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
   if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) {
     // the mma.sync kernel builds only A operands (see normalised)
     PairJob jt = normalised(j);
+    heavy_first(jt);
     const int nblk = L.nblk;
     const size_t need = (size_t)nblk * warps * 32 * 16 * sizeof(float2);
     int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + need);

@@ -528,6 +528,37 @@ def test_estimator_parity_high_multipoles(los, monkeypatch):
         assert_close(out["window_shot"], ref["window_shot"], what="window shot")
 
 
+_SHAPE_REF = {}
+
+
+@pytest.mark.parametrize("ksplit,ells", [("1", None), ("2", None), ("1", [(0, 0, 0)]), ("2", [(0, 0, 0)])])
+def test_tma_contraction_launch_shapes(ksplit, ells, monkeypatch):
+    """The TMA contraction at 25 bins, the headline workload's tile shape (two 16-row by four
+    8-column tiles per term), on a small survey with window: the cell halves of a chunk on one
+    warp or on two (BISP_PAIR_KSPLIT), for the survey's five terms (two staged chunks) and for
+    B000 alone (one term, three staged chunks), against the oracle."""
+    monkeypatch.setenv("BISP_PAIR_KSPLIT", ksplit)
+    monkeypatch.delenv("BISP_BLOCK_BINS", raising=False)
+    c = CASES["survey_local"]
+    N, L = c["N"], c["L"]
+    ells = ells or c["ells"]
+    edges = 2 * np.pi / L * np.linspace(1.0, 15.5, 26)
+    key = tuple(ells)
+    if key not in _SHAPE_REF:
+        gal, ran, obs = _survey(7, N, L, c["np_"], 4 * c["np_"])
+        p = E.Params(N=N, L=L, edges=edges, ells=ells, los="local", observer=obs, mas=c["mas"],
+                     interlace=c["interlace"], P0=1e4, window=True)
+        _SHAPE_REF[key] = (p, gal, ran, E.measure(p, gal, ran))
+    p, gal, ran, ref = _SHAPE_REF[key]
+    with _plan(p) as plan:
+        _assign(plan, 0, gal)
+        _assign(plan, 1, ran)
+        out = plan.measure()
+        assert plan.info()["pair_kernel"] == 1
+    for k in ("B", "shot", "window", "window_shot"):
+        assert_close(out[k], ref[k], what=k)
+
+
 @pytest.mark.parametrize("case", ["survey_local", "box_tsc_ilv"])
 def test_fp32_fma_contraction_kernel(case, monkeypatch):
     """The FP32-FMA contraction (k_pair, forced with BISP_PAIR_FP32=1; otherwise used for jobs
