@@ -229,7 +229,7 @@ static bool pair_use_tc(const PairJob& j) {
 }
 
 struct TmaLayout;
-static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps);
+static bool tma_layout(const PairJob& j, TmaLayout* L, int* warps);
 static int pair_blocks();
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_pair(const __grid_constant__ PairJo
 // compensation to a lane-owned FP32 (sum, compensation) slot in global memory, whose load is
 // issued at the start of the chunk.
 // ------------------------------------------------------------------------------------
+constexpr int TMA_MAXWARP = 20;  // warps of a CTA
 struct TmaLayout {
   unsigned fsz, gsz;  // bytes of the F blocks (ncomp x 4096) and of the G block of one half
   unsigned half;      // fsz + gsz
@@ -444,9 +445,14 @@ struct TmaLayout {
   int nblk;           // CTAs of the launch
   int mh, nt;         // 16-row tiles and 8-column tiles per term (bins covered: 16 mh, 8 nt)
   unsigned cblk;      // bytes of one component block (bh bins x 128 bytes, bh = max(16 mh, 8 nt))
+  // warps: one per (term, 16-row tile) over both cell halves of a chunk, or, for a term whose
+  // built side makes it the heaviest, one per (term, cell half, row tile)
+  unsigned char wterm[TMA_MAXWARP];  // warp -> term
+  unsigned char whalf[TMA_MAXWARP];  // warp -> cell half 0 or 1, or 2 for both
+  unsigned char wrow[TMA_MAXWARP];   // warp -> 16-row tile
+  unsigned char tfirst[64];          // term -> its first warp (then half-major, row tile minor)
+  unsigned char tsplit[64];          // term -> 1 (warps over both halves) or 2 (one per half)
 };
-
-constexpr int TMA_MAXWARP = 20;  // two warps (row halves) per term and cell half
 constexpr unsigned long long TMA_WAIT_NS = 2000000000ull;  // 2 s per wait
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -646,7 +652,7 @@ __device__ __forceinline__ void pair_halves(float (&c)[16], const PairJob& J, co
 template <int NTHR, int MH, int NT, int NST>
 __global__ void __launch_bounds__(NTHR, 1)
     k_pair_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const TmaLayout L,
-               int ksplit, double* partials, int* err) {
+               double* partials, int* err) {
   const PairJob& J = c_pj;
   extern __shared__ unsigned char dsm[];
   __shared__ int s_abort[2];  // per chunk parity (see the barrier below)
@@ -658,9 +664,8 @@ __global__ void __launch_bounds__(NTHR, 1)
   constexpr int chc = PR_CH;  // cells per chunk: two 32-cell halves
   const int64_t nchunk = J.Ng / chc;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // warp = ((term * ksplit) + cell half) * MH + row half: rows 16 mi .. 16 mi + 15 of the term tile
-  const int mi = warp % MH, grp = warp / MH;
-  const int t = grp / ksplit, ks = grp % ksplit;
+  // the warp's term, cell half (2: both) and 16-row tile: rows 16 mi .. 16 mi + 15 of the term tile
+  const int t = L.wterm[warp], hc = L.whalf[warp], mi = L.wrow[warp];
   const PairTermDesc T = J.term[t];
   unsigned long long pol = 0;
   if (tid == 0) {
@@ -781,10 +786,10 @@ __global__ void __launch_bounds__(NTHR, 1)
     for (int q = 0; q < 16; ++q) c[q] = 0.f;
     const PairFrag F{loffA, {loffB[0], loffB[1]}, {poffA[0], poffA[1], poffA[2], poffA[3]},
                      {poffB[0], poffB[1], poffB[2], poffB[3]}, xoff, yoff, e0, e1, tq, xb};
-    if (ksplit == 1)
+    if (hc == 2)
       pair_halves<NT, 2>(c, J, L, base + sbo, 0, Hs, F);
     else
-      pair_halves<NT, 1>(c, J, L, base + sbo, ks, Hs, F);
+      pair_halves<NT, 1>(c, J, L, base + sbo, hc, Hs, F);
 #pragma unroll
     for (int q = 0; q < 16; ++q) run[q] += c[q];
     // round-robin flush: each FP32 running sum covers at most 16 chunks (1024 cells); fg is
@@ -1118,7 +1123,7 @@ __global__ void k_pair_umma_final(const __grid_constant__ PairJob J, const float
   if (lane == 0) out[gw] = tot;
 }
 
-static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) {
+static bool tma_layout(const PairJob& j, TmaLayout* L, int* warps) {
   if (j.nb > 32 || (j.nb <= 16 ? 1 : 2) * j.nterm > TMA_MAXWARP || j.ng < 1 || j.ng > 256 || j.ncomp < 1)
     return false;
   auto r1024 = [](size_t b) { return (b + 1023) / 1024 * 1024; };
@@ -1152,15 +1157,56 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* ksplit, int* warps) 
   L->mh = mh;
   L->nt = nt;
   L->cblk = (unsigned)(bh * 128);
-  // cell halves split over warps only when the warps still fit the 320-thread instance: one warp
-  // per (term, row tile) over both halves runs with more registers per thread, which measured
-  // faster than twice the warps (survey 512^3: 146.5 against 150.3 ms per step);
-  // BISP_PAIR_KSPLIT=1 or 2 forces the choice (2 while the warps fit the launch)
+  // Warps.  Work per warp and chunk ~ (entries of the built side + 6.5) per cell half (6.5:
+  // the bare side's loads and splits and the MMAs, in units of one entry).  Every term starts
+  // with one warp per row tile over both halves; while warps are few (at most 8 after doubling)
+  // every term splits its halves over two warps; otherwise the term with the most work per warp
+  // splits while that work is more than 15 % above the mean and the warps stay within 12 (the
+  // 384-thread instance).  BISP_PAIR_KSPLIT=1 or 2 forces one warp over both halves or one per
+  // half for every term (2 while the warps fit the launch).
   const char* eks = getenv("BISP_PAIR_KSPLIT");
   const int force = eks ? atoi(eks) : 0;
-  const bool two = force == 2 ? 2 * mh * j.nterm <= TMA_MAXWARP : (force != 1 && 2 * mh * j.nterm <= 10);
-  *ksplit = two ? 2 : 1;
-  *warps = mh * j.nterm * *ksplit;
+  int split[64];
+  double cost[64], tot = 0.0;
+  for (int t = 0; t < j.nterm; ++t) {
+    const PairTermDesc& T = j.term[t];
+    const int sl = T.xslot >= 0 ? T.xslot : T.yslot;
+    cost[t] = (sl >= 0 ? j.s_off[sl + 1] - j.s_off[sl] : 0) + 6.5;
+    tot += cost[t];
+    split[t] = 1;
+  }
+  int w = mh * j.nterm;
+  if (force == 2 ? 2 * w <= TMA_MAXWARP : (force != 1 && 2 * w <= 8)) {
+    for (int t = 0; t < j.nterm; ++t) split[t] = 2;
+    w *= 2;
+  } else if (force != 1) {
+    for (;;) {
+      int tm = 0, nsp = 0;
+      for (int t = 0; t < j.nterm; ++t) {
+        nsp += split[t];
+        if (cost[t] / split[t] > cost[tm] / split[tm]) tm = t;
+      }
+      if (split[tm] == 1 && cost[tm] > 1.15 * tot / nsp && w + mh <= 12) {
+        split[tm] = 2;
+        w += mh;
+      } else {
+        break;
+      }
+    }
+  }
+  if (w > TMA_MAXWARP) return false;
+  int k = 0;
+  for (int t = 0; t < j.nterm; ++t) {
+    L->tfirst[t] = (unsigned char)k;
+    L->tsplit[t] = (unsigned char)split[t];
+    for (int h = 0; h < split[t]; ++h)
+      for (int mi = 0; mi < mh; ++mi, ++k) {
+        L->wterm[k] = (unsigned char)t;
+        L->whalf[k] = (unsigned char)(split[t] == 2 ? h : 2);
+        L->wrow[k] = (unsigned char)mi;
+      }
+  }
+  *warps = w;
   return true;
 }
 
@@ -1352,8 +1398,8 @@ bool pair_fits(const PairJob& job) {
   try {
     const PairJob& j = classify(job);
     TmaLayout L;
-    int ksplit = 1, warps = 1;
-    if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) return true;
+    int warps = 1;
+    if (pair_use_tc(j) && tma_layout(j, &L, &warps)) return true;
     const PairLaunch c = pair_launch_cfg(j);
     if (c.smem > 227 * 1024) return false;
     // instantiated kernels: up to 1024 threads for TM x TN <= 18, 512 above
@@ -1372,18 +1418,18 @@ size_t pair_scratch_bytes(const PairJob& job) {
     if (umma_plan(jt, &U, &UL)) return (size_t)pair_blocks() * UM_WARPS * 32 * 32 * sizeof(float2) + 256;
   }
   TmaLayout L;
-  int ksplit = 1, warps = 1;
-  if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps))
-    return (size_t)L.nblk * warps * 32 * 16 * sizeof(float2) + 256;
+  int warps = 1;
+  if (pair_use_tc(j) && tma_layout(j, &L, &warps)) return (size_t)L.nblk * warps * 32 * 16 * sizeof(float2) + 256;
   const PairLaunch c = pair_launch_cfg(j);
   return (size_t)c.nblk * c.warps * 32 * c.TM * c.TN * sizeof(double);
 }
 
 
 // final reduction for k_pair_tma (slots are compensated FP32 pairs (s, e), sum s - e): bin
-// (b1, b2) of term t (after the transpose (b1, b2) -> (b2, b1) of terms with T.tr) sits in warp
-// (t*ksplit + ks)*mh + b1/16, lane (b1%8)*4 + (b2%8)/2, slot (b2/8)*4 + ((b1/8)%2)*2 + b2%2
-__global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int ksplit, int mh, int nb, int nout,
+// (b1, b2) of term t (after the transpose (b1, b2) -> (b2, b1) of terms with T.tr) sits in warps
+// tfirst[t] + ks*mh + b1/16 for ks < tsplit[t], lane (b1%8)*4 + (b2%8)/2, slot
+// (b2/8)*4 + ((b1/8)%2)*2 + b2%2
+__global__ void k_pair_tc_final(const double* partials, int nblk, int warps, const TmaLayout L, int nb, int nout,
                                 double* out) {
   const PairJob& J = c_pj;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -1396,8 +1442,8 @@ __global__ void k_pair_tc_final(const double* partials, int nblk, int warps, int
     const int ln = (b1 % 8) * 4 + (b2 % 8) / 2;
     const int q = (b2 / 8) * 4 + ((b1 / 8) % 2) * 2 + (b2 % 2);
     double s = 0.0;
-    for (int ks = 0; ks < ksplit; ++ks) {
-      const int w = (t * ksplit + ks) * mh + b1 / 16;
+    for (int ks = 0; ks < L.tsplit[t]; ++ks) {
+      const int w = L.tfirst[t] + ks * L.mh + b1 / 16;
       for (int c = lane; c < nblk; c += 32) {
         const float2 v = reinterpret_cast<const float2*>(partials)[(((size_t)c * warps + w) * 32 + ln) * 16 + q];
         s += (double)v.x - (double)v.y;
@@ -1472,11 +1518,15 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
     }
   }
   TmaLayout L;
-  int ksplit = 1, warps = 1;
-  if (pair_use_tc(j) && tma_layout(j, &L, &ksplit, &warps)) {
-    // the mma.sync kernel builds only A operands (see normalised)
-    PairJob jt = normalised(j);
+  int warps = 1;
+  PairJob jt;
+  if (pair_use_tc(j)) {
+    // the mma.sync kernel builds only A operands (see normalised); its warp tables follow the
+    // order of heavy_first
+    jt = normalised(j);
     heavy_first(jt);
+  }
+  if (pair_use_tc(j) && tma_layout(jt, &L, &warps)) {
     const int nblk = L.nblk;
     const size_t need = (size_t)nblk * warps * 32 * 16 * sizeof(float2);
     int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + need);
@@ -1490,23 +1540,23 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
     auto launch = [&](auto kern) {
       BISP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));
       mark(ev0);
-      kern<<<nblk, warps * 32, L.bytes, s>>>(mf, mg, L, ksplit, partials, err);
+      kern<<<nblk, warps * 32, L.bytes, s>>>(mf, mg, L, partials, err);
     };
-    // launches of at most 10 warps take the instance bounded at 320 threads (more registers per
+    // launches of at most 12 warps take the instance bounded at 384 threads (more registers per
     // thread for the unrolled k steps)
-    const bool small = warps <= 10;
+    const bool small = warps <= 12;
     if (L.nst == 3) {
-      if (L.mh == 2) small ? launch(k_pair_tma<320, 2, 4, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 3>);
-      else if (L.nt == 2) small ? launch(k_pair_tma<320, 1, 2, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 3>);
-      else small ? launch(k_pair_tma<320, 1, 1, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 3>);
+      if (L.mh == 2) small ? launch(k_pair_tma<384, 2, 4, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 3>);
+      else if (L.nt == 2) small ? launch(k_pair_tma<384, 1, 2, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 3>);
+      else small ? launch(k_pair_tma<384, 1, 1, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 3>);
     } else {
-      if (L.mh == 2) small ? launch(k_pair_tma<320, 2, 4, 2>) : launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 2>);
-      else if (L.nt == 2) small ? launch(k_pair_tma<320, 1, 2, 2>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 2>);
-      else small ? launch(k_pair_tma<320, 1, 1, 2>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 2>);
+      if (L.mh == 2) small ? launch(k_pair_tma<384, 2, 4, 2>) : launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 2>);
+      else if (L.nt == 2) small ? launch(k_pair_tma<384, 1, 2, 2>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 2>);
+      else small ? launch(k_pair_tma<384, 1, 1, 2>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 2>);
     }
     BISP_CHECK_LAUNCH();
     const int nout = j.nout * j.nb * j.nb;
-    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(partials, nblk, warps, ksplit, L.mh, j.nb, j.nout, out_dev);
+    k_pair_tc_final<<<(nout * 32 + 255) / 256, 256, 0, s>>>(partials, nblk, warps, L, j.nb, j.nout, out_dev);
     BISP_CHECK_LAUNCH();
     mark(ev1);
     int herr = 0;
