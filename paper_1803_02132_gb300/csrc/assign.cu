@@ -356,38 +356,44 @@ __device__ __forceinline__ float wker(float t) {
   return 0.f;
 }
 
-// Gather deposit over CTA-owned node tiles.  A CTA owns DT_X x DT_Y x DT_Z mesh nodes (z
-// fastest), one node per thread.  The home cells its nodes draw from, h = c + o with o in
+// Gather deposit over CTA-owned node tiles.  A CTA owns DT_X x DT_Y x DZ mesh nodes (z
+// fastest), one node per thread; DZ = 32 (16 for a 16^3 mesh), so that a warp is one line of
+// nodes along z: its lanes need the same halo rows, and a staged batch keeps a warp's lanes
+// either all busy or all idle.  The home cells its nodes draw from, h = c + o with o in
 // [OLO, OHI]^3, form a halo box of RX x RY x RZ cells; their particles, which sit in the sorted
 // arrays as one contiguous range per cell, are listed in (rx, ry, rz) order and staged through
-// shared memory in batches of DT_MAXP, read coalesced.  Every node then visits its (ox, oy, oz)
+// shared memory in batches of MAXP, read coalesced.  Every node then visits its (ox, oy, oz)
 // cells in increasing order and each cell's particles in sorted (stable) order: the same order
 // and the same FP32 operations as a node-by-node gather, so the meshes are bit-reproducible.
 // A tile whose halo holds no particle (most of a survey's volume) writes its zeros and returns
 // after one count per halo row.  Node positions: mesh 0 at c H, mesh 1 (interlaced) at
 // (c + 1/2) H.  All channels are accumulated in one pass (NC >= nchan registers per mesh).
-constexpr int DT_X = 4, DT_Y = 4, DT_Z = 16, DT_THREADS = DT_X * DT_Y * DT_Z;
+constexpr int DT_X = 4, DT_Y = 4;
 
-template <int P, int ILV>
+template <int P, int ILV, int DZ>
 struct DepTile {
+  static constexpr int THREADS = DT_X * DT_Y * DZ;
   static constexpr int OLO = (P == 1) ? 0 : -1;
   static constexpr int OHI = ILV ? (P == 3 ? 2 : 1) : (P == 3 ? 1 : 0);
   static constexpr int W = OHI - OLO + 1;
-  static constexpr int RX = DT_X + W - 1, RY = DT_Y + W - 1, RZ = DT_Z + W - 1;
+  static constexpr int RX = DT_X + W - 1, RY = DT_Y + W - 1, RZ = DZ + W - 1;
   static constexpr int NCELL = RX * RY * RZ;
 };
 
-template <int P, int ILV, int NC>
-__global__ void __launch_bounds__(DT_THREADS) k_deposit(const uint32_t* __restrict__ cell_start,
+template <int P, int ILV, int NC, int DZ>
+__global__ void __launch_bounds__(DT_X * DT_Y * DZ) k_deposit(const uint32_t* __restrict__ cell_start,
                                                         const float4* __restrict__ frac,
                                                         const float* __restrict__ vals, int64_t n, int N,
                                                         int nchan, float* mesh0, float* mesh1) {
-  using T = DepTile<P, ILV>;
+  using T = DepTile<P, ILV, DZ>;
+  constexpr int DT_THREADS = T::THREADS, DT_Z = DZ;
   constexpr int OLO = T::OLO, OHI = T::OHI, W = T::W, RY = T::RY, RZ = T::RZ, NCELL = T::NCELL;
   // mesh 0's weight vanishes for every offset in the particle's cell once an offset exceeds O0HI
   constexpr int O0HI = (P == 3) ? 1 : 0;
   constexpr int NW = ILV ? 6 : 3;              // per-axis weight tables per staged particle
-  constexpr int MAXP = NC <= 12 ? 256 : 224;   // particles per staged batch (static smem < 48 KB)
+  // particles per staged batch: what the static shared memory (48 KB) leaves after the halo tables
+  constexpr int MAXP_FIT = (48 * 1024 - 8 * NCELL - 512) / (4 * (NW * W + NC) + 1);
+  constexpr int MAXP = MAXP_FIT >= 256 ? 256 : (MAXP_FIT / 32) * 32;
   __shared__ uint32_t s_gs[NCELL];             // first sorted index of each halo cell
   __shared__ uint32_t s_ts[NCELL + 1];         // position of each halo cell in the tile list
   __shared__ float s_w[NW][W][MAXP];           // 1D weights W_p(o + d) (mesh 0), W_p(o + d - 1/2) (mesh 1)
@@ -538,12 +544,13 @@ __global__ void __launch_bounds__(DT_THREADS) k_deposit(const uint32_t* __restri
   }
 }
 
-template <int P, int ILV>
-static void deposit_p(const DepositArgs& a, cudaStream_t s) {
+template <int P, int ILV, int DZ>
+static void deposit_pz(const DepositArgs& a, cudaStream_t s) {
   const int64_t Ng = (int64_t)a.N * a.N * a.N;
-  const unsigned grid = (unsigned)(Ng / DT_THREADS);
+  constexpr int TH = DepTile<P, ILV, DZ>::THREADS;
+  const unsigned grid = (unsigned)(Ng / TH);
 #define BISP_DEP(NC_) \
-  k_deposit<P, ILV, NC_><<<grid, DT_THREADS, 0, s>>>(a.cell_start, a.frac, a.vals, a.n, a.N, a.nchan, a.mesh0, a.mesh1)
+  k_deposit<P, ILV, NC_, DZ><<<grid, TH, 0, s>>>(a.cell_start, a.frac, a.vals, a.n, a.N, a.nchan, a.mesh0, a.mesh1)
   if (a.nchan <= 1) BISP_DEP(1);
   else if (a.nchan <= 2) BISP_DEP(2);
   else if (a.nchan <= 6) BISP_DEP(6);
@@ -551,6 +558,12 @@ static void deposit_p(const DepositArgs& a, cudaStream_t s) {
   else if (a.nchan <= 16) BISP_DEP(16);
   else throw Error{6, "deposit: more than 16 channels"};
 #undef BISP_DEP
+}
+
+template <int P, int ILV>
+static void deposit_p(const DepositArgs& a, cudaStream_t s) {
+  if (a.N >= 32) deposit_pz<P, ILV, 32>(a, s);
+  else deposit_pz<P, ILV, 16>(a, s);
 }
 
 void launch_deposit(const DepositArgs& a0, cudaStream_t s, int* launches) {
