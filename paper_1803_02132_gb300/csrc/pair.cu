@@ -230,6 +230,7 @@ static bool pair_use_tc(const PairJob& j) {
 
 struct TmaLayout;
 static bool tma_layout(const PairJob& j, TmaLayout* L, int* warps);
+static bool pairable(const PairJob& j, int a, int b);
 static int pair_blocks();
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -452,6 +453,8 @@ struct TmaLayout {
   unsigned char wrow[TMA_MAXWARP];   // warp -> 16-row tile
   unsigned char tfirst[64];          // term -> its first warp (then half-major, row tile minor)
   unsigned char tsplit[64];          // term -> 1 (warps over both halves) or 2 (one per half)
+  unsigned char tsub[64];            // term -> its slot group in the warp (two-term warps: 0 or 1)
+  int ntm;                           // terms per warp: 2 when every term has a partner (see dual_order)
 };
 constexpr unsigned long long TMA_WAIT_NS = 2000000000ull;  // 2 s per wait
 
@@ -646,10 +649,81 @@ __device__ __forceinline__ void pair_halves(float (&c)[16], const PairJob& J, co
   }
 }
 
+// Two terms in one warp: terms t and t + 1 with the same bare Y side and the same components
+// on their built X sides, which differ only in the H rows (the two G sets of a launch).  Per
+// cell half the two built sides share every ldmatrix load; per k step the bare side's fragments
+// are loaded and split once for both terms' 24 MMAs.
+template <int NT>
+__device__ __forceinline__ void pair_dual(float (&ca)[16], float (&cb)[16], const PairJob& J, const TmaLayout& L,
+                                          unsigned sb, const float* Hs, const PairFrag& F, int f0) {
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    uint32_t av[2][4][4];
+    {
+      float s4[2][4][4];
+#pragma unroll
+      for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s4[z][u][0] = s4[z][u][1] = s4[z][u][2] = s4[z][u][3] = 0.f;
+      for (int e = F.e0, e2 = f0; e < F.e1; ++e, ++e2) {
+        const unsigned ao = sb + (unsigned)hh * L.half + (unsigned)J.s_ent[e][0] * L.cblk + F.loffA;
+        const float* hpa = Hs + J.s_ent[e][1] * PR_CH + hh * 32 + 2 * F.tq;
+        const float* hpb = Hs + J.s_ent[e2][1] * PR_CH + hh * 32 + 2 * F.tq;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          uint32_t v[4];
+          ldsm_x4(ao + F.poffA[u], v);
+          const float2 ha = *reinterpret_cast<const float2*>(hpa + 8 * u);
+          const float2 hb = *reinterpret_cast<const float2*>(hpb + 8 * u);
+          s4[0][u][0] = fmaf(__uint_as_float(v[0]), ha.x, s4[0][u][0]);
+          s4[0][u][1] = fmaf(__uint_as_float(v[1]), ha.x, s4[0][u][1]);
+          s4[0][u][2] = fmaf(__uint_as_float(v[2]), ha.y, s4[0][u][2]);
+          s4[0][u][3] = fmaf(__uint_as_float(v[3]), ha.y, s4[0][u][3]);
+          s4[1][u][0] = fmaf(__uint_as_float(v[0]), hb.x, s4[1][u][0]);
+          s4[1][u][1] = fmaf(__uint_as_float(v[1]), hb.x, s4[1][u][1]);
+          s4[1][u][2] = fmaf(__uint_as_float(v[2]), hb.y, s4[1][u][2]);
+          s4[1][u][3] = fmaf(__uint_as_float(v[3]), hb.y, s4[1][u][3]);
+        }
+      }
+#pragma unroll
+      for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) av[z][u][e] = __float_as_uint(s4[z][u][e]);
+    }
+    const unsigned fh = sb + (unsigned)hh * L.half + F.yoff;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      uint32_t bv[2][4];
+#pragma unroll
+      for (int i = 0; i < NT / 2; ++i) ldsm_x4(fh + F.loffB[i] + F.poffB[kk], bv[i]);
+      uint32_t bh[4][2], bl[4][2];
+#pragma unroll
+      for (int i = 0; i < NT / 2; ++i)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
+#pragma unroll
+      for (int z = 0; z < 2; ++z) {
+        float* c = z ? cb : ca;
+        uint32_t ah[4], al[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_tf32(av[z][kk][e], ah[e], al[e]);
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
+#pragma unroll
+        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
+      }
+    }
+  }
+}
+
 // MH 16-row tiles (b1) and NT 8-column tiles (b2) per term: (2, 4) covers 32 bins; launches over
 // few bins (blocked unions, small bin sets) take (1, 2) for 16 bins or (1, 1) for 8, so that
 // their MMAs and staged bytes shrink with the bins.
-template <int NTHR, int MH, int NT, int NST>
+template <int NTHR, int MH, int NT, int NST, bool DUAL = false>
 __global__ void __launch_bounds__(NTHR, 1)
     k_pair_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const TmaLayout L,
                double* partials, int* err) {
@@ -689,16 +763,20 @@ __global__ void __launch_bounds__(NTHR, 1)
     }
   };
 
-  float2* slot = reinterpret_cast<float2*>(partials) + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * 16;
+  constexpr int NTM = DUAL ? 2 : 1;  // terms per warp
+  float2* slot =
+      reinterpret_cast<float2*>(partials) + (((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32 + lane) * (16 * NTM);
 #pragma unroll
-  for (int q = 0; q < 16; ++q) slot[q] = make_float2(0.f, 0.f);
+  for (int q = 0; q < 16 * NTM; ++q) slot[q] = make_float2(0.f, 0.f);
   // per chunk the MMA accumulators start from zero (the tensor core's accumulation stays at the
   // size of one chunk's products); chunk sums go to FP32 running sums over at most PR_FLUSH
   // chunks (1024 cells), which are added round robin with Kahan compensation to the lane's
   // (sum, compensation) slots
-  float run[16];
+  float run[NTM][16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) run[q] = 0.f;
+  for (int z = 0; z < NTM; ++z)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) run[z][q] = 0.f;
 
   // ldmatrix rows of this lane: matrix j = lane/8, row r = lane%8 of that matrix; every
   // fragment row is congruent to r mod 8, so its swizzled piece is (piece ^ r).
@@ -737,7 +815,9 @@ __global__ void __launch_bounds__(NTHR, 1)
     // slot it % 16 is flushed at the end of this chunk; load it now so that the L2 round
     // trip overlaps the chunk's work
     const int fg = it & 15;
-    float2 pre = slot[fg];
+    float2 pre[NTM];
+#pragma unroll
+    for (int z = 0; z < NTM; ++z) pre[z] = slot[16 * z + fg];
     if (!mbar_wait_bounded(bar0 + 8u * st, NST == 2 ? ((unsigned)it >> 1) & 1u : (unsigned)(it / NST) & 1u)) {
       s_abort[it & 1] = 1;
       atomicExch(err, 1);
@@ -781,40 +861,49 @@ __global__ void __launch_bounds__(NTHR, 1)
       issue(nx, NST == 2 ? (st ^ 1) : (it + NST - 1) % NST);
     }
     // (2) this warp's 16 x 32 block of its term over its cell half (or both halves)
-    float c[16];
+    float c[NTM][16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) c[q] = 0.f;
+    for (int z = 0; z < NTM; ++z)
+#pragma unroll
+      for (int q = 0; q < 16; ++q) c[z][q] = 0.f;
     const PairFrag F{loffA, {loffB[0], loffB[1]}, {poffA[0], poffA[1], poffA[2], poffA[3]},
                      {poffB[0], poffB[1], poffB[2], poffB[3]}, xoff, yoff, e0, e1, tq, xb};
-    if (hc == 2)
-      pair_halves<NT, 2>(c, J, L, base + sbo, 0, Hs, F);
+    if constexpr (DUAL)
+      pair_dual<NT>(c[0], c[NTM - 1], J, L, base + sbo, Hs, F, J.s_off[J.term[t + 1].xslot]);
+    else if (hc == 2)
+      pair_halves<NT, 2>(c[0], J, L, base + sbo, 0, Hs, F);
     else
-      pair_halves<NT, 1>(c, J, L, base + sbo, hc, Hs, F);
+      pair_halves<NT, 1>(c[0], J, L, base + sbo, hc, Hs, F);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) run[q] += c[q];
+    for (int z = 0; z < NTM; ++z)
+#pragma unroll
+      for (int q = 0; q < 16; ++q) run[z][q] += c[z][q];
     // round-robin flush: each FP32 running sum covers at most 16 chunks (1024 cells); fg is
     // warp-uniform, so the switch is one indexed branch
-    {
+#pragma unroll
+    for (int z = 0; z < NTM; ++z) {
       float x = 0.f;
       switch (fg) {
-#define BISP_TAKE(q) \
-  case q:            \
-    x = run[q];      \
-    run[q] = 0.f;    \
+#define BISP_TAKE(q)  \
+  case q:             \
+    x = run[z][q];    \
+    run[z][q] = 0.f;  \
     break;
         BISP_TAKE(0) BISP_TAKE(1) BISP_TAKE(2) BISP_TAKE(3) BISP_TAKE(4) BISP_TAKE(5) BISP_TAKE(6) BISP_TAKE(7)
         BISP_TAKE(8) BISP_TAKE(9) BISP_TAKE(10) BISP_TAKE(11) BISP_TAKE(12) BISP_TAKE(13) BISP_TAKE(14) BISP_TAKE(15)
 #undef BISP_TAKE
       }
-      kahan_add(pre, x);
-      slot[fg] = pre;
+      kahan_add(pre[z], x);
+      slot[16 * z + fg] = pre[z];
     }
   }
   const bool aborted = it < (nchunk - (int64_t)blockIdx.x + gridDim.x - 1) / gridDim.x;  // left at a break
   // the running sums not flushed since their last turn
   if (!aborted) {
 #pragma unroll
-    for (int q = 0; q < 16; ++q) kahan_add(slot[q], run[q]);
+    for (int z = 0; z < NTM; ++z)
+#pragma unroll
+      for (int q = 0; q < 16; ++q) kahan_add(slot[16 * z + q], run[z][q]);
   }
   // after an abort the copies of the failed chunk and of the chunks staged ahead may still be in
   // flight: wait for them (bounded) before the CTA's shared memory is released
@@ -1164,6 +1253,34 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* warps) {
   // splits while that work is more than 15 % above the mean and the warps stay within 12 (the
   // 384-thread instance).  BISP_PAIR_KSPLIT=1 or 2 forces one warp over both halves or one per
   // half for every term (2 while the warps fit the launch).
+  // two-term warps (pair_dual) when every term sits next to a partner and pairing brings a
+  // launch that would exceed the 384-thread instance back into it (the unit-shell launch's two G
+  // sets: 20 warps -> 10); BISP_PAIR_DUAL=0 never, 1 whenever the terms pair
+  {
+    const char* ed = getenv("BISP_PAIR_DUAL");
+    const int fd = ed ? atoi(ed) : -1;
+    bool adj = mh == 2 && j.nterm % 2 == 0 && fd != 0;
+    for (int u = 0; adj && 2 * u < j.nterm; ++u) adj = pairable(j, 2 * u, 2 * u + 1);
+    if (adj && (j.nterm / 2) * mh <= 12 && (fd == 1 || j.nterm * mh > 12)) {
+      const int w = (j.nterm / 2) * mh;
+      for (int u = 0; 2 * u < j.nterm; ++u) {
+        for (int z = 0; z < 2; ++z) {
+          L->tfirst[2 * u + z] = (unsigned char)(u * mh);
+          L->tsplit[2 * u + z] = 1;
+          L->tsub[2 * u + z] = (unsigned char)z;
+        }
+        for (int mi = 0; mi < mh; ++mi) {
+          L->wterm[u * mh + mi] = (unsigned char)(2 * u);
+          L->whalf[u * mh + mi] = 2;
+          L->wrow[u * mh + mi] = (unsigned char)mi;
+        }
+      }
+      L->ntm = 2;
+      *warps = w;
+      return true;
+    }
+  }
+  L->ntm = 1;
   const char* eks = getenv("BISP_PAIR_KSPLIT");
   const int force = eks ? atoi(eks) : 0;
   int split[64];
@@ -1199,6 +1316,7 @@ static bool tma_layout(const PairJob& j, TmaLayout* L, int* warps) {
   for (int t = 0; t < j.nterm; ++t) {
     L->tfirst[t] = (unsigned char)k;
     L->tsplit[t] = (unsigned char)split[t];
+    L->tsub[t] = 0;
     for (int h = 0; h < split[t]; ++h)
       for (int mi = 0; mi < mh; ++mi, ++k) {
         L->wterm[k] = (unsigned char)t;
@@ -1324,6 +1442,50 @@ static void heavy_first(PairJob& j) {
   for (int e = 0; e < j.out_ent_off[j.nout]; ++e) j.out_ent_term[e] = inv[src.out_ent_term[e]];
 }
 
+// Terms a and b can share a warp (pair_dual): both built on X only, the same bare Y, the same
+// orientation and the same components on their built sides (in order); only the H rows differ.
+static bool pairable(const PairJob& j, int a, int b) {
+  const PairTermDesc &A = j.term[a], &B = j.term[b];
+  if (A.xslot < 0 || B.xslot < 0 || A.yslot >= 0 || B.yslot >= 0 || A.ydir != B.ydir || A.tr != B.tr) return false;
+  const int na = j.s_off[A.xslot + 1] - j.s_off[A.xslot], nb = j.s_off[B.xslot + 1] - j.s_off[B.xslot];
+  if (na != nb) return false;
+  for (int e = 0; e < na; ++e)
+    if (j.s_ent[j.s_off[A.xslot] + e][0] != j.s_ent[j.s_off[B.xslot] + e][0]) return false;
+  return true;
+}
+
+// Reorders the terms so that every term sits next to a partner (terms 2u, 2u + 1 pairable),
+// keeping the order of the first of each pair; false (job unchanged) unless every term has one.
+static bool dual_order(PairJob& j) {
+  if (j.nterm % 2) return false;
+  int partner[64];
+  for (int t = 0; t < j.nterm; ++t) partner[t] = -1;
+  for (int a = 0; a < j.nterm; ++a) {
+    if (partner[a] >= 0) continue;
+    for (int b = a + 1; b < j.nterm; ++b)
+      if (partner[b] < 0 && pairable(j, a, b)) {
+        partner[a] = b;
+        partner[b] = a;
+        break;
+      }
+    if (partner[a] < 0) return false;
+  }
+  int perm[64], inv[64], n = 0;
+  for (int a = 0; a < j.nterm; ++a)
+    if (a < partner[a]) {
+      perm[n++] = a;
+      perm[n++] = partner[a];
+    }
+  const PairJob src = j;
+  for (int k = 0; k < j.nterm; ++k) {
+    j.term[k] = src.term[perm[k]];
+    j.term_out[k] = src.term_out[perm[k]];
+    inv[perm[k]] = k;
+  }
+  for (int e = 0; e < j.out_ent_off[j.nout]; ++e) j.out_ent_term[e] = inv[src.out_ent_term[e]];
+  return true;
+}
+
 static PairJob normalised(const PairJob& j) {
   PairJob jt = j;
   for (int t = 0; t < jt.nterm; ++t) {
@@ -1428,7 +1590,7 @@ size_t pair_scratch_bytes(const PairJob& job) {
 // final reduction for k_pair_tma (slots are compensated FP32 pairs (s, e), sum s - e): bin
 // (b1, b2) of term t (after the transpose (b1, b2) -> (b2, b1) of terms with T.tr) sits in warps
 // tfirst[t] + ks*mh + b1/16 for ks < tsplit[t], lane (b1%8)*4 + (b2%8)/2, slot
-// (b2/8)*4 + ((b1/8)%2)*2 + b2%2
+// 16 tsub[t] + (b2/8)*4 + ((b1/8)%2)*2 + b2%2 of the lane's 16 ntm slots
 __global__ void k_pair_tc_final(const double* partials, int nblk, int warps, const TmaLayout L, int nb, int nout,
                                 double* out) {
   const PairJob& J = c_pj;
@@ -1445,7 +1607,8 @@ __global__ void k_pair_tc_final(const double* partials, int nblk, int warps, con
     for (int ks = 0; ks < L.tsplit[t]; ++ks) {
       const int w = L.tfirst[t] + ks * L.mh + b1 / 16;
       for (int c = lane; c < nblk; c += 32) {
-        const float2 v = reinterpret_cast<const float2*>(partials)[(((size_t)c * warps + w) * 32 + ln) * 16 + q];
+        const float2 v = reinterpret_cast<const float2*>(
+            partials)[(((size_t)c * warps + w) * 32 + ln) * (16 * L.ntm) + 16 * L.tsub[t] + q];
         s += (double)v.x - (double)v.y;
       }
     }
@@ -1525,10 +1688,12 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
     // order of heavy_first
     jt = normalised(j);
     heavy_first(jt);
+    if (j.nb > 16) dual_order(jt);
   }
   if (pair_use_tc(j) && tma_layout(jt, &L, &warps)) {
     const int nblk = L.nblk;
-    const size_t need = (size_t)nblk * warps * 32 * 16 * sizeof(float2);
+    const size_t need = (size_t)nblk * warps * 32 * 16 * L.ntm * sizeof(float2);
+    if (need + sizeof(int) > scratch_bytes) throw Error{2, "pair reduction scratch too small"};
     int* err = reinterpret_cast<int*>(static_cast<unsigned char*>(scratch) + need);
     BISP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     const CUtensorMap mf = f_map(j.fields, j.Ng, j.ncomp, j.nb, (int)(L.cblk / 128));
@@ -1545,7 +1710,10 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
     // launches of at most 12 warps take the instance bounded at 384 threads (more registers per
     // thread for the unrolled k steps)
     const bool small = warps <= 12;
-    if (L.nst == 3) {
+    if (L.ntm == 2) {
+      if (L.nst == 3) launch(k_pair_tma<384, 2, 4, 3, true>);
+      else launch(k_pair_tma<384, 2, 4, 2, true>);
+    } else if (L.nst == 3) {
       if (L.mh == 2) small ? launch(k_pair_tma<384, 2, 4, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 3>);
       else if (L.nt == 2) small ? launch(k_pair_tma<384, 1, 2, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 3>);
       else small ? launch(k_pair_tma<384, 1, 1, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 1, 3>);
