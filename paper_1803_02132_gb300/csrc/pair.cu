@@ -561,6 +561,29 @@ __device__ __forceinline__ void kahan_add(float2& v, float x) {
 __constant__ PairJob c_pj;
 static std::mutex g_pj_mu;
 
+// The last 8-column tile when it holds a single bin (n_b = 8 (NT - 1) + 1, the 25-bin workload):
+// that column is formed with FP32 FMAs instead of three MMAs on a tile 7/8 padding.  Lanes
+// g = lane/4 = 0 hold column 0 of the tile in the B fragment (k = tq and tq + 4); every lane takes
+// them by shuffle and adds its A fragment's rows g, g + 8 over its k pair; the four lanes tq of
+// a row are summed per chunk (tail_close), so the lane tq = 0 holds the column, in the slots of
+// the tile's column 0.
+__device__ __forceinline__ void tail_col(float (&t)[2], const uint32_t (&a)[4], uint32_t b0, uint32_t b1, int tq) {
+  const float y0 = __uint_as_float(__shfl_sync(0xffffffffu, b0, tq));
+  const float y1 = __uint_as_float(__shfl_sync(0xffffffffu, b1, tq));
+  t[0] = fmaf(__uint_as_float(a[0]), y0, fmaf(__uint_as_float(a[2]), y1, t[0]));
+  t[1] = fmaf(__uint_as_float(a[1]), y0, fmaf(__uint_as_float(a[3]), y1, t[1]));
+}
+__device__ __forceinline__ void tail_close(float* c, float (&t)[2]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float v = t[h];
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    c[2 * h] = (threadIdx.x & 3) == 0 ? v : 0.f;  // (row g, col 0) and (row g + 8, col 0)
+    c[2 * h + 1] = 0.f;
+  }
+}
+
 // A warp's fragment addressing: ldmatrix row offsets and swizzled pieces, its term's sides
 struct PairFrag {
   unsigned loffA, loffB[2], poffA[4], poffB[4];
@@ -574,9 +597,11 @@ struct PairFrag {
 // c.  The built sides of all NH halves and four k steps are formed in one pass over the side's
 // entries (one table read and address per entry; the shared-memory loads are independent), then
 // every k step loads and splits the bare side and issues its 3 NT MMAs.
-template <int NT, int NH>
+template <int NT, int NH, bool TAIL1 = false>
 __device__ __forceinline__ void pair_halves(float (&c)[16], const PairJob& J, const TmaLayout& L, unsigned sb,
                                             int h0, const float* Hs, const PairFrag& F) {
+  constexpr int NM = TAIL1 ? NT - 1 : NT;  // column tiles on the tensor cores
+  float tl[2] = {0.f, 0.f};
   uint32_t av[NH][4][4];
   if (F.xb) {
     // built side sum_(c,h) F_c(b, x) H_h(x) for this lane's fragment cells
@@ -633,29 +658,34 @@ __device__ __forceinline__ void pair_halves(float (&c)[16], const PairJob& J, co
 #pragma unroll
         for (int i = 0; i < NT / 2; ++i)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
+          for (int e = 0; e < 4; ++e)
+            if (2 * i + (e >> 1) < NM) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
       } else {
         split_tf32(bv[0][0], bh[0][0], bl[0][0]);
         split_tf32(bv[0][1], bh[0][1], bl[0][1]);
       }
+      if constexpr (TAIL1) tail_col(tl, av[hh][kk], bv[NT / 2 - 1][2], bv[NT / 2 - 1][3], F.tq);
       // small products first, pass-major so that consecutive MMAs are independent
 #pragma unroll
-      for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
+      for (int ni = 0; ni < NM; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
 #pragma unroll
-      for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
+      for (int ni = 0; ni < NM; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
 #pragma unroll
-      for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
+      for (int ni = 0; ni < NM; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
     }
   }
+  if constexpr (TAIL1) tail_close(c + 4 * (NT - 1), tl);
 }
 
 // Two terms in one warp: terms t and t + 1 with the same bare Y side and the same components
 // on their built X sides, which differ only in the H rows (the two G sets of a launch).  Per
 // cell half the two built sides share every ldmatrix load; per k step the bare side's fragments
 // are loaded and split once for both terms' 24 MMAs.
-template <int NT>
+template <int NT, bool TAIL1 = false>
 __device__ __forceinline__ void pair_dual(float (&ca)[16], float (&cb)[16], const PairJob& J, const TmaLayout& L,
                                           unsigned sb, const float* Hs, const PairFrag& F, int f0) {
+  constexpr int NM = TAIL1 ? NT - 1 : NT;  // column tiles on the tensor cores
+  float tl[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
   for (int hh = 0; hh < 2; ++hh) {
     uint32_t av[2][4][4];
@@ -702,28 +732,34 @@ __device__ __forceinline__ void pair_dual(float (&ca)[16], float (&cb)[16], cons
 #pragma unroll
       for (int i = 0; i < NT / 2; ++i)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
+        for (int e = 0; e < 4; ++e)
+          if (2 * i + (e >> 1) < NM) split_tf32(bv[i][e], bh[2 * i + (e >> 1)][e & 1], bl[2 * i + (e >> 1)][e & 1]);
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
         float* c = z ? cb : ca;
         uint32_t ah[4], al[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) split_tf32(av[z][kk][e], ah[e], al[e]);
+        if constexpr (TAIL1) tail_col(tl[z], av[z][kk], bv[NT / 2 - 1][2], bv[NT / 2 - 1][3], F.tq);
 #pragma unroll
-        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
+        for (int ni = 0; ni < NM; ++ni) mma_tf32(c + ni * 4, al, bh[ni]);
 #pragma unroll
-        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
+        for (int ni = 0; ni < NM; ++ni) mma_tf32(c + ni * 4, ah, bl[ni]);
 #pragma unroll
-        for (int ni = 0; ni < NT; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
+        for (int ni = 0; ni < NM; ++ni) mma_tf32(c + ni * 4, ah, bh[ni]);
       }
     }
+  }
+  if constexpr (TAIL1) {
+    tail_close(ca + 4 * (NT - 1), tl[0]);
+    tail_close(cb + 4 * (NT - 1), tl[1]);
   }
 }
 
 // MH 16-row tiles (b1) and NT 8-column tiles (b2) per term: (2, 4) covers 32 bins; launches over
 // few bins (blocked unions, small bin sets) take (1, 2) for 16 bins or (1, 1) for 8, so that
 // their MMAs and staged bytes shrink with the bins.
-template <int NTHR, int MH, int NT, int NST, bool DUAL = false>
+template <int NTHR, int MH, int NT, int NST, bool DUAL = false, bool TAIL1 = false>
 __global__ void __launch_bounds__(NTHR, 1)
     k_pair_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmG, const TmaLayout L,
                double* partials, int* err) {
@@ -869,11 +905,11 @@ __global__ void __launch_bounds__(NTHR, 1)
     const PairFrag F{loffA, {loffB[0], loffB[1]}, {poffA[0], poffA[1], poffA[2], poffA[3]},
                      {poffB[0], poffB[1], poffB[2], poffB[3]}, xoff, yoff, e0, e1, tq, xb};
     if constexpr (DUAL)
-      pair_dual<NT>(c[0], c[NTM - 1], J, L, base + sbo, Hs, F, J.s_off[J.term[t + 1].xslot]);
+      pair_dual<NT, TAIL1>(c[0], c[NTM - 1], J, L, base + sbo, Hs, F, J.s_off[J.term[t + 1].xslot]);
     else if (hc == 2)
-      pair_halves<NT, 2>(c[0], J, L, base + sbo, 0, Hs, F);
+      pair_halves<NT, 2, TAIL1>(c[0], J, L, base + sbo, 0, Hs, F);
     else
-      pair_halves<NT, 1>(c[0], J, L, base + sbo, hc, Hs, F);
+      pair_halves<NT, 1, TAIL1>(c[0], J, L, base + sbo, hc, Hs, F);
 #pragma unroll
     for (int z = 0; z < NTM; ++z)
 #pragma unroll
@@ -1710,9 +1746,15 @@ void pair_reduce(const PairJob& job, double* out_dev, void* scratch, size_t scra
     // launches of at most 12 warps take the instance bounded at 384 threads (more registers per
     // thread for the unrolled k steps)
     const bool small = warps <= 12;
+    // 25 bins: the last column tile holds one bin (FP32 FMAs for it); BISP_PAIR_TAIL=0 keeps it
+    // on the tensor cores
+    const char* etl = getenv("BISP_PAIR_TAIL");
+    const bool tail = L.mh == 2 && L.nt == 4 && j.nb == 25 && small && !(etl && atoi(etl) == 0);
     if (L.ntm == 2) {
-      if (L.nst == 3) launch(k_pair_tma<384, 2, 4, 3, true>);
-      else launch(k_pair_tma<384, 2, 4, 2, true>);
+      if (tail) L.nst == 3 ? launch(k_pair_tma<384, 2, 4, 3, true, true>) : launch(k_pair_tma<384, 2, 4, 2, true, true>);
+      else L.nst == 3 ? launch(k_pair_tma<384, 2, 4, 3, true>) : launch(k_pair_tma<384, 2, 4, 2, true>);
+    } else if (tail) {
+      L.nst == 3 ? launch(k_pair_tma<384, 2, 4, 3, false, true>) : launch(k_pair_tma<384, 2, 4, 2, false, true>);
     } else if (L.nst == 3) {
       if (L.mh == 2) small ? launch(k_pair_tma<384, 2, 4, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 2, 4, 3>);
       else if (L.nt == 2) small ? launch(k_pair_tma<384, 1, 2, 3>) : launch(k_pair_tma<32 * TMA_MAXWARP, 1, 2, 3>);

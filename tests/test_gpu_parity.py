@@ -531,17 +531,21 @@ def test_estimator_parity_high_multipoles(los, monkeypatch):
 _SHAPE_REF = {}
 
 
-@pytest.mark.parametrize("ksplit,ells,dual", [("0", None, "-1"), ("1", None, "-1"), ("2", None, "-1"),
-                                             ("0", None, "0"), ("1", [(0, 0, 0)], "-1"), ("2", [(0, 0, 0)], "-1")])
-def test_tma_contraction_launch_shapes(ksplit, ells, dual, monkeypatch):
+@pytest.mark.parametrize("ksplit,ells,dual,tail", [("0", None, "-1", "1"), ("1", None, "-1", "1"),
+                                                  ("2", None, "-1", "1"), ("0", None, "0", "1"),
+                                                  ("0", None, "-1", "0"), ("1", [(0, 0, 0)], "-1", "1"),
+                                                  ("2", [(0, 0, 0)], "-1", "1")])
+def test_tma_contraction_launch_shapes(ksplit, ells, dual, tail, monkeypatch):
     """The TMA contraction at 25 bins, the headline workload's tile shape (two 16-row by four
     8-column tiles per term), on a small survey with window: the cell halves of a chunk split by
     the balancing rule, on one warp or on two (BISP_PAIR_KSPLIT), for the survey's five terms (two
     staged chunks) and for B000 alone (one term, three staged chunks); the unit-shell launch's
     ten terms (two G sets) in two-term warps by default and one term per warp with
-    BISP_PAIR_DUAL=0; against the oracle."""
+    BISP_PAIR_DUAL=0; the 25th bin's column by FP32 FMAs by default and on the tensor cores with
+    BISP_PAIR_TAIL=0; against the oracle."""
     monkeypatch.setenv("BISP_PAIR_KSPLIT", ksplit)
     monkeypatch.setenv("BISP_PAIR_DUAL", dual)
+    monkeypatch.setenv("BISP_PAIR_TAIL", tail)
     monkeypatch.delenv("BISP_BLOCK_BINS", raising=False)
     c = CASES["survey_local"]
     N, L = c["N"], c["L"]
