@@ -164,3 +164,36 @@ def test_survey512_sampled_pairs_against_oracle():
             scale = np.abs(out[key][im]).max()
             if abs(ref) > 0.01 * scale:
                 assert abs(got - ref) <= TOL * abs(ref), (rec["ells"], b1, b2, key, got, ref)
+
+
+def test_box1024_blocked_fp32_against_fp64_form(monkeypatch):
+    """The 1024^3 box workload (2000 Mpc/h, 1.2e8 particles, TSC + interlacing, B000, B202,
+    B112, B222) at its full mesh and catalogue, in its blocked launch configuration (bins held in
+    blocks, one contraction per block union), on its first four bins: the fused FP32 path against
+    the plain FP64 form (FP64 inverse transforms and one FP64 mesh sum per bin pair and 3j term)
+    on the same assignment.  Holds the 1024^3 instantiations of the pruned inverse passes and the
+    few-bin contraction shapes to the FP64 transforms and mesh sums."""
+    w = dict(bench.WORKLOADS["box1024"])
+    w["edges"] = w["edges"][:5]
+    gal, _ = bench.make_inputs(w, seed=1002)
+    xyz = _dev(gal["xyz"])
+    outs = {}
+    for prec in ("fp32", "fp64"):
+        if prec == "fp32":
+            monkeypatch.setenv("BISP_BLOCK_BINS", "2")
+            monkeypatch.delenv("BISP_FP64_BLOCK_BINS", raising=False)
+        else:
+            monkeypatch.delenv("BISP_BLOCK_BINS", raising=False)
+            monkeypatch.setenv("BISP_FP64_BLOCK_BINS", "1")
+        with _plan_for(w, precision=prec) as plan:
+            plan.assign(bisp.DATA, xyz)
+            outs[prec] = plan.measure()
+            assert plan.info()["pair_kernel"] == (1 if prec == "fp32" else 3)
+    assert np.array_equal(outs["fp32"]["nmodes"], outs["fp64"]["nmodes"])
+    for key in ("B", "shot"):
+        for im, mult in enumerate(w["ells"]):
+            ref = outs["fp64"][key][im]
+            got = outs["fp32"][key][im]
+            m = np.abs(ref) > 0.01 * np.abs(ref).max()
+            err = np.max(np.abs(got[m] - ref[m]) / np.abs(ref[m]))
+            assert err <= TOL, (key, mult, err)
