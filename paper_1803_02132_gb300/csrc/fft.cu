@@ -96,12 +96,19 @@ __global__ void __launch_bounds__(Geo<N>::TS) k_fwd_y(float2* data, const float2
 // ------------------------------------------------------------------------------------
 // forward x pass + interlacing + deconvolution, written over mesh0.
 //   D = [ (D0 + e^{-i pi (nx+ny+nz)/N} D1) / 2 ] / W(k)   (ILV)   or   D0 / W(k)
-// winv[j] = 1 / sinc(pi n_j / N)^p for the signed frequency of index j.
+// winv[j] = 1 / sinc(pi n_j / N)^p for the signed frequency of index j.  LB lines per CTA: with
+// interlacing two meshes' lines sit in shared memory, so the pass takes half the strided passes'
+// lines per CTA (more CTAs per SM).
 // ------------------------------------------------------------------------------------
 template <int N, int ILV>
-__global__ void __launch_bounds__(Geo<N>::TS) k_fwd_x(float2* m0, const float2* m1, const float2* __restrict__ tw,
-                                                      const float* __restrict__ winv) {
-  constexpr int NH = N / 2, LB = Geo<N>::LB;
+struct FwdX {
+  static constexpr int LB = ILV && Geo<N>::LB > 8 ? Geo<N>::LB / 2 : Geo<N>::LB;
+  static constexpr int TS = LB * N / 8;
+};
+template <int N, int ILV>
+__global__ void __launch_bounds__(FwdX<N, ILV>::TS) k_fwd_x(float2* m0, const float2* m1, const float2* __restrict__ tw,
+                                                           const float* __restrict__ winv) {
+  constexpr int NH = N / 2, LB = FwdX<N, ILV>::LB;
   extern __shared__ float2 sm[];  // dynamic: (1 + ILV) * N * LB
   float2* s0 = sm;
   float2* s1 = sm + N * LB;
@@ -162,14 +169,18 @@ static void fwd_impl(float* mesh0, float* mesh1, int count, int mas, const float
     k_fwd_y<N><<<gy, G::TS, s1, s>>>(reinterpret_cast<float2*>(mesh1), tw);
     BISP_CHECK_LAUNCH();
   }
-  const size_t sh = (mesh1 ? 2 : 1) * (size_t)N * G::LB * sizeof(float2);
   if (mesh1) {
+    using X = FwdX<N, 1>;
+    const size_t sh = 2 * (size_t)N * X::LB * sizeof(float2);
     smem_attr(k_fwd_x<N, 1>, sh);
-    k_fwd_x<N, 1><<<gy, G::TS, sh, s>>>(reinterpret_cast<float2*>(mesh0), reinterpret_cast<const float2*>(mesh1),
-                                          tw, winv);
+    k_fwd_x<N, 1><<<dim3(G::NH / X::LB, N, count), X::TS, sh, s>>>(
+        reinterpret_cast<float2*>(mesh0), reinterpret_cast<const float2*>(mesh1), tw, winv);
   } else {
+    using X = FwdX<N, 0>;
+    const size_t sh = (size_t)N * X::LB * sizeof(float2);
     smem_attr(k_fwd_x<N, 0>, sh);
-    k_fwd_x<N, 0><<<gy, G::TS, sh, s>>>(reinterpret_cast<float2*>(mesh0), nullptr, tw, winv);
+    k_fwd_x<N, 0><<<dim3(G::NH / X::LB, N, count), X::TS, sh, s>>>(reinterpret_cast<float2*>(mesh0), nullptr, tw,
+                                                                   winv);
   }
   BISP_CHECK_LAUNCH();
   if (launches) *launches += mesh1 ? 5 : 3;
