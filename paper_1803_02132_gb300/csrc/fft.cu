@@ -278,13 +278,20 @@ __host__ __device__ __forceinline__ InvGeo inv_geo(int N, int P, int LB) {
   return g;
 }
 
+// lines per CTA of the first inverse pass: half the strided passes' (the prune extent stays a
+// multiple of Geo<N>::LB, so of LX)
 template <int N>
-__global__ void __launch_bounds__(Geo<N>::TS) k_inv_x(const __grid_constant__ InvBatch B, float2* t1all,
-                                                      const float2* __restrict__ tw) {
-  constexpr int NH = N / 2, LB = Geo<N>::LB, TS = Geo<N>::TS;
+struct InvX {
+  static constexpr int LX = Geo<N>::LB > 8 ? Geo<N>::LB / 2 : Geo<N>::LB;
+  static constexpr int TS = LX * N / 8;
+};
+template <int N>
+__global__ void __launch_bounds__(InvX<N>::TS, InvX<N>::TS <= 512 ? 2 : 1) k_inv_x(const __grid_constant__ InvBatch B, float2* t1all,
+                                                       const float2* __restrict__ tw) {
+  constexpr int NH = N / 2, LB = InvX<N>::LX, TS = InvX<N>::TS;
   constexpr int EPT = N * LB / TS;  // elements per thread
   extern __shared__ float2 s[];
-  const InvGeo g = inv_geo(N, B.P, LB);
+  const InvGeo g = inv_geo(N, B.P, Geo<N>::LB);
   const int nz0 = blockIdx.x * LB, iy = blockIdx.y;
   const int sy = iy - g.P;
   const int jy = sy & (N - 1);
@@ -632,10 +639,10 @@ static void inv_impl(const InvBatch& b, const float2* tw, void* scratch, cudaStr
   float2* t1 = reinterpret_cast<float2*>(scratch);
   float2* t2 = t1 + (size_t)b.nf * g.t1;
   using RL = RegL<N>;
-  const size_t s1 = (size_t)N * G::LB * sizeof(float2);
+  const size_t s1 = (size_t)N * InvX<N>::LX * sizeof(float2);
   smem_attr(k_inv_x<N>, s1);
   smem_attr(k_inv_y_reg<N>, RL::SMEM);
-  k_inv_x<N><<<dim3(g.Pz / G::LB, g.ny), G::TS, s1, s>>>(b, t1, tw);
+  k_inv_x<N><<<dim3(g.Pz / InvX<N>::LX, g.ny), InvX<N>::TS, s1, s>>>(b, t1, tw);
   BISP_CHECK_LAUNCH();
   k_inv_y_reg<N><<<dim3(g.Pz / G::LB, N, b.nf), RL::THREADS, RL::SMEM, s>>>(b, t1, t2, tw);
   BISP_CHECK_LAUNCH();
