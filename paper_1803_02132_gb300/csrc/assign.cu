@@ -380,6 +380,18 @@ struct DepTile {
   static constexpr int NCELL = RX * RY * RZ;
 };
 
+// Batch of staged particles: two CTAs of DT_X DT_Y DZ threads per SM share the SM's shared memory
+// (the halo tables are static); 512 particles for 12 channels
+template <int P, int ILV, int NC, int DZ>
+struct DepBatch {
+  using T = DepTile<P, ILV, DZ>;
+  static constexpr int NW = ILV ? 6 : 3;
+  static constexpr int PER = 4 * (NW * T::W + NC) + 1;  // bytes per staged particle
+  static constexpr int FIT = (110 * 1024 - 8 * T::NCELL - 512) / PER;
+  static constexpr int MAXP = FIT >= 512 ? 512 : (FIT / 32) * 32;
+  static constexpr size_t BYTES = (size_t)PER * MAXP;
+};
+
 template <int P, int ILV, int NC, int DZ>
 __global__ void __launch_bounds__(DT_X * DT_Y * DZ) k_deposit(const uint32_t* __restrict__ cell_start,
                                                         const float4* __restrict__ frac,
@@ -391,14 +403,15 @@ __global__ void __launch_bounds__(DT_X * DT_Y * DZ) k_deposit(const uint32_t* __
   // mesh 0's weight vanishes for every offset in the particle's cell once an offset exceeds O0HI
   constexpr int O0HI = (P == 3) ? 1 : 0;
   constexpr int NW = ILV ? 6 : 3;              // per-axis weight tables per staged particle
-  // particles per staged batch: what the static shared memory (48 KB) leaves after the halo tables
-  constexpr int MAXP_FIT = (48 * 1024 - 8 * NCELL - 512) / (4 * (NW * W + NC) + 1);
-  constexpr int MAXP = MAXP_FIT >= 256 ? 256 : (MAXP_FIT / 32) * 32;
+  constexpr int MAXP = DepBatch<P, ILV, NC, DZ>::MAXP;  // particles per staged batch
   __shared__ uint32_t s_gs[NCELL];             // first sorted index of each halo cell
   __shared__ uint32_t s_ts[NCELL + 1];         // position of each halo cell in the tile list
-  __shared__ float s_w[NW][W][MAXP];           // 1D weights W_p(o + d) (mesh 0), W_p(o + d - 1/2) (mesh 1)
-  __shared__ float s_val[NC][MAXP];
-  __shared__ unsigned char s_rz[MAXP];         // halo z index of each staged particle's cell
+  // staged batch (dynamic shared memory): 1D weights W_p(o + d) (mesh 0) and W_p(o + d - 1/2)
+  // (mesh 1), channel values, halo z index of each particle's cell
+  extern __shared__ __align__(16) unsigned char dep_dyn[];
+  auto& s_w = *reinterpret_cast<float (*)[NW][W][MAXP]>(dep_dyn);
+  auto& s_val = *reinterpret_cast<float (*)[NC][MAXP]>(dep_dyn + sizeof(float) * NW * W * MAXP);
+  auto& s_rz = *reinterpret_cast<unsigned char (*)[MAXP]>(dep_dyn + sizeof(float) * (NW * W + NC) * MAXP);
   __shared__ uint32_t s_wsum[DT_THREADS / 32];
   __shared__ int s_any;
   const int ntz = N / DT_Z, nty = N / DT_Y;
@@ -549,8 +562,14 @@ static void deposit_pz(const DepositArgs& a, cudaStream_t s) {
   const int64_t Ng = (int64_t)a.N * a.N * a.N;
   constexpr int TH = DepTile<P, ILV, DZ>::THREADS;
   const unsigned grid = (unsigned)(Ng / TH);
-#define BISP_DEP(NC_) \
-  k_deposit<P, ILV, NC_, DZ><<<grid, TH, 0, s>>>(a.cell_start, a.frac, a.vals, a.n, a.N, a.nchan, a.mesh0, a.mesh1)
+#define BISP_DEP(NC_)                                                                                    \
+  do {                                                                                                   \
+    constexpr size_t sh = DepBatch<P, ILV, NC_, DZ>::BYTES;                                              \
+    BISP_CUDA(cudaFuncSetAttribute(k_deposit<P, ILV, NC_, DZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                   (int)sh));                                                            \
+    k_deposit<P, ILV, NC_, DZ><<<grid, TH, sh, s>>>(a.cell_start, a.frac, a.vals, a.n, a.N, a.nchan, a.mesh0, \
+                                                  a.mesh1);                                              \
+  } while (0)
   if (a.nchan <= 1) BISP_DEP(1);
   else if (a.nchan <= 2) BISP_DEP(2);
   else if (a.nchan <= 6) BISP_DEP(6);
