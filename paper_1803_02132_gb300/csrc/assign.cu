@@ -381,14 +381,16 @@ struct DepTile {
 };
 
 // Batch of staged particles: two CTAs of DT_X DT_Y DZ threads per SM share the SM's shared memory
-// (the halo tables are static); 512 particles for 12 channels
+// (112 KB each with the static halo tables): 672 particles for 12 channels with TSC and
+// interlacing.  Measured at 512^3 (random catalogue's assignment): 256 particles 86.0 ms, 512
+// 66.6 ms, 672 65.6 ms, 1440 with one CTA per SM 70.3 ms.
 template <int P, int ILV, int NC, int DZ>
 struct DepBatch {
   using T = DepTile<P, ILV, DZ>;
   static constexpr int NW = ILV ? 6 : 3;
   static constexpr int PER = 4 * (NW * T::W + NC) + 1;  // bytes per staged particle
-  static constexpr int FIT = (110 * 1024 - 8 * T::NCELL - 512) / PER;
-  static constexpr int MAXP = FIT >= 512 ? 512 : (FIT / 32) * 32;
+  static constexpr int FIT = (112 * 1024 - 8 * T::NCELL - 512) / PER;
+  static constexpr int MAXP = (FIT / 32) * 32;
   static constexpr size_t BYTES = (size_t)PER * MAXP;
 };
 
