@@ -319,6 +319,18 @@ enum { BISP_DBG_SPECTRUM = 0, BISP_DBG_MESH = 1 };
 bisp_status bisp_debug_fetch(const bisp_plan* plan, int what, int which, int index,
                              void* host_out, size_t bytes);
 
+/* Device bounds checks (no paper passage: a debugging aid).  The library built with
+ * -DBISP_CHECKED (paper_1803_02132_gb300/build.py, checked=True: libbisp_checked.so) tests the
+ * indexes of its main kernels' global and shared-memory accesses (deposit, particle gather,
+ * shell sums, the three inverse passes, the contraction's tables) against the buffers they
+ * address; a failed check skips the access and, if no failure is recorded yet, records
+ * (site << 32) | (1 << 31) | (low 31 bits of the offending index) in a device word.  Nothing traps.
+ * word (host, non-NULL) receives that word, 0 when every check passed since it was last
+ * cleared; reset != 0 clears it afterwards.  The call synchronises the device.
+ * Errors: BISP_EINVAL for NULL word; BISP_EUNSUPPORTED from the release build (word set to 0);
+ * BISP_ECUDA if the copy fails. */
+bisp_status bisp_check_word(uint64_t* word, int reset);
+
 #ifdef __cplusplus
 }
 #endif

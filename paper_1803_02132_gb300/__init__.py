@@ -50,11 +50,12 @@ class _Info(C.Structure):
                 ("pair_launches", C.c_int), ("pair_kernel", C.c_int), ("zpass_groups", C.c_int)]
 
 
-def _load():
-    if not os.path.exists(_LIB_PATH):
+def _load(path=None, checked=False):
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
         from . import build as _b
-        _b.build()
-    lib = C.CDLL(_LIB_PATH)
+        path = _b.build(checked=checked)
+    lib = C.CDLL(path)
     vp, dp = C.c_void_p, C.POINTER(C.c_double)
     lib.bisp_plan_create.argtypes = [C.POINTER(vp), C.POINTER(_Params), vp]
     lib.bisp_assign.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int64, C.c_int]
@@ -65,6 +66,7 @@ def _load():
     lib.bisp_plan_query.argtypes = [vp, C.POINTER(_Info)]
     lib.bisp_cell_order.argtypes = [C.c_int, C.c_double, C.c_int, vp, C.c_int64, vp, vp, vp]
     lib.bisp_debug_fetch.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, C.c_size_t]
+    lib.bisp_check_word.argtypes = [C.POINTER(C.c_uint64), C.c_int]
     lib.bisp_cell_order_noalloc.argtypes = [C.c_int, C.c_double, C.c_int, vp, C.c_int64, vp, vp, vp]
     lib.bisp_covariance.argtypes = [dp, C.c_int, C.c_int, dp, dp, dp]
     lib.bisp_covariance_factors.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
@@ -79,7 +81,7 @@ def _load():
     for f in ("bisp_plan_create", "bisp_assign", "bisp_measure", "bisp_measure_batch", "bisp_plan_destroy",
               "bisp_plan_query", "bisp_cell_order", "bisp_debug_fetch", "bisp_cell_order_noalloc",
               "bisp_covariance", "bisp_covariance_factors", "bisp_chi2", "bisp_wigner9j", "bisp_masked_zeta",
-              "bisp_zeta_to_bk", "bisp_bk_to_zeta", "bisp_tree_multipoles"):
+              "bisp_zeta_to_bk", "bisp_bk_to_zeta", "bisp_tree_multipoles", "bisp_check_word"):
         getattr(lib, f).restype = C.c_int
     return lib
 
@@ -93,6 +95,30 @@ def lib():
     if _lib is None:
         _lib = _load()
     return _lib
+
+
+def use_checked_library():
+    """Switch this process to libbisp_checked.so (built on first use: the same kernels with device
+    bounds checks, see bisp_check_word in include/bisp.h); returns the previous library handle,
+    which use_library() restores."""
+    global _lib
+    prev = _lib
+    _lib = _load(os.path.join(_HERE, "libbisp_checked.so"), checked=True)
+    return prev
+
+
+def use_library(handle):
+    """Make a library handle returned by use_checked_library() the current one again."""
+    global _lib
+    _lib = handle
+
+
+def check_word(reset=False):
+    """The checked library's device check word (0: every check passed); BispError from the release
+    library (BISP_EUNSUPPORTED)."""
+    w = C.c_uint64(0)
+    _check(lib().bisp_check_word(C.byref(w), 1 if reset else 0))
+    return int(w.value)
 
 
 def header_functions():

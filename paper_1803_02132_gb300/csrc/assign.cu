@@ -25,6 +25,8 @@ int prep_blocks(int64_t n) {
 // so launches from different plans, streams or host threads never share it.
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ PrepArgs a) {
   constexpr int NSMAX = 34;
+  // test of the check mechanism: the check fails without touching memory
+  if (a.selftest && blockIdx.x == 0 && threadIdx.x == 0) BISP_DCHECK(false, 99, 0);
   double acc[NSMAX];
 #pragma unroll
   for (int q = 0; q < NSMAX; ++q) acc[q] = 0.0;
@@ -328,6 +330,7 @@ __global__ void k_gather_particles(const uint32_t* perm, int64_t n, const float4
                                    int nchan, float4* frac_out, float* vals_out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t p = perm[i];
+    if (!BISP_DCHECK(p < (uint64_t)n, 1, p)) continue;
     frac_out[i] = frac_in[p];
     for (int c = 0; c < nchan; ++c) vals_out[(size_t)c * n + i] = vals_in[(size_t)c * n + p];
   }
@@ -432,7 +435,8 @@ __global__ void __launch_bounds__(DT_X * DT_Y * DZ) k_deposit(const uint32_t* __
     const uint32_t rowkey = (hx * (uint32_t)N + hy) * (uint32_t)N;
     uint32_t cnt = 0;
     if (!zwrap) {
-      cnt = cell_start[rowkey + (uint32_t)(z0 + DT_Z - 1 + OHI) + 1] - cell_start[rowkey + (uint32_t)(z0 + OLO)];
+      if (BISP_DCHECK(rowkey + (uint64_t)(z0 + DT_Z - 1 + OHI) + 1 <= (uint64_t)Ng && z0 + OLO >= 0, 2, rowkey))
+        cnt = cell_start[rowkey + (uint32_t)(z0 + DT_Z - 1 + OHI) + 1] - cell_start[rowkey + (uint32_t)(z0 + OLO)];
     } else {
       for (int rz = 0; rz < RZ; ++rz) {
         const uint32_t k = rowkey + ((uint32_t)(z0 + OLO + rz) & msk);
@@ -459,6 +463,7 @@ __global__ void __launch_bounds__(DT_X * DT_Y * DZ) k_deposit(const uint32_t* __
         const uint32_t hx = (uint32_t)(x0 + OLO + rx) & msk, hy = (uint32_t)(y0 + OLO + ry) & msk;
         const uint32_t hz = (uint32_t)(z0 + OLO + rz) & msk;
         const uint32_t k = (hx * (uint32_t)N + hy) * (uint32_t)N + hz;
+        if (!BISP_DCHECK(k < (uint64_t)Ng, 3, k)) continue;
         const uint32_t g0 = cell_start[k];
         s_gs[c] = g0;
         cnt[j] = cell_start[k + 1] - g0;
@@ -500,6 +505,7 @@ __global__ void __launch_bounds__(DT_X * DT_Y * DZ) k_deposit(const uint32_t* __
           else hi = mid - 1;
         }
         const uint32_t g = s_gs[lo] + (q - s_ts[lo]);
+        if (!BISP_DCHECK(g < (uint64_t)n && q - b0 < (uint32_t)MAXP, 4, g)) continue;
         const float4 d = frac[g];
         s_rz[q - b0] = (unsigned char)(lo % RZ);
         // 1D weights of this particle for every offset o (distance particle - node = o + d)

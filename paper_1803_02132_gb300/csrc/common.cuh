@@ -9,6 +9,22 @@
 
 namespace bisp {
 
+// Checked build (compiled with -DBISP_CHECKED, relocatable device code): BISP_DCHECK(cond, site)
+// is the condition itself, and a false condition records (site << 32) | (low 32 bits of the
+// value passed as `what`) in the device word g_bisp_check unless an earlier failure is recorded;
+// the caller skips the guarded access.  The release build compiles every check to `true`.  The
+// host reads and clears the word with bisp_check_word().
+#ifdef BISP_CHECKED
+extern __device__ unsigned long long g_bisp_check;
+__device__ __forceinline__ bool bisp_dcheck(bool ok, unsigned site, unsigned long long what) {
+  if (!ok) atomicCAS(&g_bisp_check, 0ull, ((unsigned long long)site << 32) | (what & 0xffffffffull) | 1ull << 31);
+  return ok;
+}
+#define BISP_DCHECK(cond, site, what) ::bisp::bisp_dcheck((cond), (site), (unsigned long long)(what))
+#else
+#define BISP_DCHECK(cond, site, what) true
+#endif
+
 // Twiddles: kernels take `tw`, a device table of e^{-2 pi i j / BISP_TWN}, j < BISP_TWN,
 // rounded to FP32 from FP64 values computed on the host.
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }

@@ -386,7 +386,8 @@ __global__ void __launch_bounds__(InvX<N>::TS, InvX<N>::TS <= 512 ? 2 : 1) k_inv
     float2* t1 = t1all + (size_t)f * g.t1;
     for (int i = threadIdx.x; i < N * LB; i += blockDim.x) {
       const int l = i % LB, e = i / LB;
-      t1[((size_t)e * g.ny + iy) * g.Pz + nz0 + l] = s[i];
+      const size_t o = ((size_t)e * g.ny + iy) * g.Pz + nz0 + l;
+      if (BISP_DCHECK(o < g.t1 && iy < g.ny, 20, o)) t1[o] = s[i];
     }
     __syncthreads();
   }
@@ -455,6 +456,9 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const __grid_constant__ InvBa
   const int GROUPS = Bt.zgroups;  // row groups per CTA (a power of two; tuned by the plan)
   const unsigned tile_bytes = (unsigned)(ROWS * g.Pz * sizeof(float2));
   const float2* src0 = t2all + (size_t)f * g.t2 + (size_t)blockIdx.x * GROUPS * ROWS * g.Pz;
+  // every row group of this CTA lies inside field f's T2 block
+  const bool src_ok = BISP_DCHECK(((size_t)blockIdx.x + 1) * GROUPS * ROWS * g.Pz <= g.t2, 24, blockIdx.x);
+  if (!src_ok) return;
   const unsigned bar0 = fft_su32(bars);
   __shared__ int s_abort;
   if (threadIdx.x == 0) {
@@ -514,6 +518,7 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const __grid_constant__ InvBa
     if (s_abort) break;  // uniform: set before the barrier; nothing is stored after a timeout
     // stage 2: thread a handles kb = a + A r, r < B / A, an A-point DFT over a' each
     float* out = Bt.f[f].out + row * N;
+    const bool row_ok = BISP_DCHECK((size_t)row < (size_t)N * N, 23, row);
 #pragma unroll
     for (int r = 0; r < B / A; ++r) {
       const int kb = a + A * r;
@@ -524,7 +529,7 @@ __global__ void __launch_bounds__(256) k_inv_z_reg(const __grid_constant__ InvBa
 #pragma unroll
       for (int ka = 0; ka < A; ++ka) {
         const int m = kb + B * ka;
-        reinterpret_cast<float2*>(out)[m] = u[ka];
+        if (row_ok) reinterpret_cast<float2*>(out)[m] = u[ka];
       }
     }
   }
@@ -606,13 +611,17 @@ __global__ void __launch_bounds__(RegL<N>::THREADS) k_inv_y_reg(const __grid_con
   for (int b = 0; b < B; ++b) {
     const int n = a + A * b;
     const int sy = sgn_idx(n, N);
-    v[b] = (sy >= -g.P && sy <= g.P) ? t1[(size_t)(sy + g.P) * g.Pz] : make_float2(0.f, 0.f);
+    const bool in = sy >= -g.P && sy <= g.P &&
+                    BISP_DCHECK((size_t)x * g.ny * g.Pz + (size_t)(sy + g.P) * g.Pz + nz0 + l < g.t1, 21, x);
+    v[b] = in ? t1[(size_t)(sy + g.P) * g.Pz] : make_float2(0.f, 0.f);
   }
   __syncthreads();  // twiddle table ready
   regl_stage1<N, +1>(v, s, wtab, l, a);
   __syncthreads();
   float2* t2 = t2all + (size_t)f * g.t2 + (size_t)x * N * g.Pz + nz0 + l;
-  regl_finish<N, +1>(s, l, a, [&](int m, float2 u) { t2[(size_t)m * g.Pz] = u; });
+  regl_finish<N, +1>(s, l, a, [&](int m, float2 u) {
+    if (BISP_DCHECK((size_t)x * N * g.Pz + (size_t)m * g.Pz + nz0 + l < g.t2, 22, m)) t2[(size_t)m * g.Pz] = u;
+  });
 }
 
 int inverse_zgroups(int N, int requested) {

@@ -69,6 +69,7 @@ struct PrepArgs {
   double* partials;    // [blocks][nsum]  sums: w, then w^3 * Re/Im y* for each D channel
   int nsum;
   int* bad;            // count of non-finite / out-of-box positions
+  int selftest;        // checked build: record one failed check (site 99) with no other effect
 };
 
 // launches (defined in assign.cu)

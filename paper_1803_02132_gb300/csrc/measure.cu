@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(ZS_THREADS) k_zsum(const __grid_constant__ Zsu
     const int sx = (int)(code & 1023u) - 512, sy = (int)((code >> 10) & 1023u) - 512, nz = (int)(code >> 20);
     const int jx = sx & (N - 1), jy = sy & (N - 1);
     const size_t gi = ((size_t)jx * N + jy) * NH + nz;
+    if (!BISP_DCHECK(nz < NH && i >= 0, 10, gi)) continue;
     const float2 xr = A.XR[gi];
     const float2 xi = A.XI ? A.XI[gi] : make_float2(0.f, 0.f);
     const float2 nr = A.NR[gi];
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(256) k_gather_neg(const float* __restrict__ fi
     const uint32_t o = offs[i];
     const int sx = 512 - (int)(o & 1023u), sy = 512 - (int)((o >> 10) & 1023u), sz = 512 - (int)((o >> 20) & 1023u);
     const size_t cell = ((size_t)(sx & (N - 1)) * N + (size_t)(sy & (N - 1))) * N + (size_t)(sz & (N - 1));
+    if (!BISP_DCHECK(cell < (size_t)Ng, 11, cell)) continue;
     for (int c = 0; c < nf; ++c) out[i * nf + c] = fields[c * Ng + cell];
   }
 }

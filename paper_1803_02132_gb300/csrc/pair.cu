@@ -834,6 +834,22 @@ __global__ void __launch_bounds__(NTHR, 1)
   const bool xb = T.xslot >= 0;
   const int e0 = xb ? J.s_off[T.xslot] : 0, e1 = xb ? J.s_off[T.xslot + 1] : 0;
   const unsigned xoff = xb ? 0u : (unsigned)T.xdir * L.cblk, yoff = (unsigned)T.ydir * L.cblk;
+#ifdef BISP_CHECKED
+  // every shared-memory row this warp's term addresses lies in the staged blocks and H buffers
+  if (lane == 0) {
+    BISP_DCHECK(T.ydir >= 0 && T.ydir < L.ncomp && (xb || (T.xdir >= 0 && T.xdir < L.ncomp)), 30, t);
+    const int tl = DUAL ? t + 1 : t;
+    for (int u = t; u <= tl; ++u) {
+      const PairTermDesc& U = J.term[u];
+      if (U.xslot < 0) continue;
+      for (int e = J.s_off[U.xslot]; e < J.s_off[U.xslot + 1]; ++e)
+        BISP_DCHECK(J.s_ent[e][0] >= 0 && J.s_ent[e][0] < L.ncomp && J.s_ent[e][1] >= 0 && J.s_ent[e][1] < J.nh, 31,
+                    e);
+    }
+    if (warp == 0)
+      for (int e = 0; e < J.h_off[J.nh]; ++e) BISP_DCHECK(J.h_ent[e].g < L.gbox, 32, e);
+  }
+#endif
 
   // NST - 1 chunks staged ahead; chunk index it uses stage it % NST, phase (it / NST) & 1.
   // One barrier per chunk: once every thread has passed the barrier of chunk it, every warp

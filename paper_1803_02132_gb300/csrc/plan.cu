@@ -877,6 +877,12 @@ void do_assign(bisp_plan* P, int which, const float* xyz, const float* w, const 
   a.partials = partp;
   a.nsum = nsum;
   a.bad = badp;
+#ifdef BISP_CHECKED
+  {
+    const char* e = getenv("BISP_CHECK_SELFTEST");
+    a.selftest = e && atoi(e) == 1;
+  }
+#endif
   if (n > 0) {
     launch_prep(a, s);
     ++launches;
@@ -1961,6 +1967,11 @@ bisp_status guarded(F&& f) {
 // =====================================================================================
 // C ABI
 // =====================================================================================
+#ifdef BISP_CHECKED
+namespace bisp {
+__device__ unsigned long long g_bisp_check = 0;  // first failed device check (checked build)
+}
+#endif
 extern "C" {
 
 bisp_status bisp_plan_create(bisp_plan** out, const bisp_params* p, void* stream) {
@@ -2180,6 +2191,30 @@ bisp_status bisp_cell_order(int nmesh, double box_len, int mas, const float* xyz
     BISP_CUDA(cudaStreamSynchronize(s));
     for (DBuf* d : {&keys, &idx, &frac, &part, &bad, &scr, &ynd}) d->release(&tb);
   });
+}
+
+bisp_status bisp_check_word(uint64_t* word, int reset) {
+  if (!word) {
+    g_err = "NULL argument";
+    return BISP_EINVAL;
+  }
+#ifdef BISP_CHECKED
+  return guarded([&] {
+    unsigned long long w = 0;
+    BISP_CUDA(cudaDeviceSynchronize());
+    BISP_CUDA(cudaMemcpyFromSymbol(&w, bisp::g_bisp_check, sizeof(w)));
+    if (reset) {
+      const unsigned long long z = 0;
+      BISP_CUDA(cudaMemcpyToSymbol(bisp::g_bisp_check, &z, sizeof(z)));
+    }
+    *word = (uint64_t)w;
+  });
+#else
+  (void)reset;
+  *word = 0;
+  g_err = "device bounds checks are compiled only into the checked build";
+  return BISP_EUNSUPPORTED;
+#endif
 }
 
 bisp_status bisp_debug_fetch(const bisp_plan* P, int what, int which, int index, void* host_out, size_t bytes) {

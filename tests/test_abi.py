@@ -68,3 +68,25 @@ def test_new_plan_options_are_validated_without_the_gpu():
     with pytest.raises(bisp.BispError) as e:
         bisp.Plan(nmesh=64, box_len=1000.0, k_edges=[0.01, 0.02], ells=[(0, 0, 0)], precision=7)
     assert e.value.status == bisp.BISP_EINVAL
+
+
+def test_checked_build_compiles():
+    """The kernels with device bounds checks (-DBISP_CHECKED, relocatable device code) compile for
+    sm_103a: the translation units that carry checks (object files discarded)."""
+    import concurrent.futures as cf
+    import shutil
+    import subprocess
+
+    from paper_1803_02132_gb300 import build as B
+
+    if not shutil.which(B.nvcc()) and not os.path.exists(B.nvcc()):
+        pytest.skip("nvcc not available")
+
+    def one(src):
+        cmd = [B.nvcc(), *B.ARCH, *B.FLAGS, "-DBISP_CHECKED", "-rdc=true", "-c", os.path.join(B.CSRC, src),
+               "-o", os.devnull]
+        return src, subprocess.run(cmd, capture_output=True, text=True)
+
+    with cf.ThreadPoolExecutor(max_workers=5) as ex:
+        for src, r in ex.map(one, ["assign.cu", "fft.cu", "measure.cu", "pair.cu", "plan.cu"]):
+            assert r.returncode == 0, f"{src}: {r.stderr[-2000:]}"
