@@ -209,6 +209,9 @@ def run_gpu(args, w, rank, world):
     # FP64 comparison line leaves it out (its device time already runs to tens of seconds)
     ms_e2e = 0.0
     if not f64 and not args.no_e2e:
+        # one untimed step with host buffers first: the plan grows its arena once for the staged
+        # host inputs, as the device leg's warm-up steps did for theirs
+        step(dev_inputs=False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
