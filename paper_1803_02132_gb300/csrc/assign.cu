@@ -25,8 +25,10 @@ int prep_blocks(int64_t n) {
 // so launches from different plans, streams or host threads never share it.
 __global__ void __launch_bounds__(PREP_THREADS) k_prep(const __grid_constant__ PrepArgs a) {
   constexpr int NSMAX = 34;
+#ifdef BISP_CHECKED
   // test of the check mechanism: the check fails without touching memory
   if (a.selftest && blockIdx.x == 0 && threadIdx.x == 0) BISP_DCHECK(false, 99, 0);
+#endif
   double acc[NSMAX];
 #pragma unroll
   for (int q = 0; q < NSMAX; ++q) acc[q] = 0.0;
@@ -386,12 +388,13 @@ struct DepTile {
 // Batch of staged particles: two CTAs of DT_X DT_Y DZ threads per SM share the SM's shared memory
 // (112 KB each with the static halo tables): 672 particles for 12 channels with TSC and
 // interlacing.  Measured at 512^3 (random catalogue's assignment): 256 particles 86.0 ms, 512
-// 66.6 ms, 672 65.6 ms, 1440 with one CTA per SM 70.3 ms.
+// 66.6 ms, 672 65.6 ms, 1440 with one CTA per SM 70.3 ms; mesh 0 keeps only the offsets where
+// its weights can be non-zero (3 of 4 per axis for TSC with interlacing): 736 particles, 64.7 ms.
 template <int P, int ILV, int NC, int DZ>
 struct DepBatch {
   using T = DepTile<P, ILV, DZ>;
-  static constexpr int NW = ILV ? 6 : 3;
-  static constexpr int PER = 4 * (NW * T::W + NC) + 1;  // bytes per staged particle
+  static constexpr int W0 = (P == 3 ? 1 : 0) - T::OLO + 1;  // mesh 0's non-zero offsets per axis
+  static constexpr int PER = 4 * (3 * W0 + (ILV ? 3 * T::W : 0) + NC) + 1;  // bytes per staged particle
   static constexpr int FIT = (112 * 1024 - 8 * T::NCELL - 512) / PER;
   static constexpr int MAXP = (FIT / 32) * 32;
   static constexpr size_t BYTES = (size_t)PER * MAXP;
@@ -407,16 +410,21 @@ __global__ void __launch_bounds__(DT_X * DT_Y * DZ) k_deposit(const uint32_t* __
   constexpr int OLO = T::OLO, OHI = T::OHI, W = T::W, RY = T::RY, RZ = T::RZ, NCELL = T::NCELL;
   // mesh 0's weight vanishes for every offset in the particle's cell once an offset exceeds O0HI
   constexpr int O0HI = (P == 3) ? 1 : 0;
-  constexpr int NW = ILV ? 6 : 3;              // per-axis weight tables per staged particle
+  constexpr int W0 = DepBatch<P, ILV, NC, DZ>::W0;       // mesh 0's offsets OLO..O0HI
+  constexpr int W1 = ILV ? W : 1;
   constexpr int MAXP = DepBatch<P, ILV, NC, DZ>::MAXP;  // particles per staged batch
   __shared__ uint32_t s_gs[NCELL];             // first sorted index of each halo cell
   __shared__ uint32_t s_ts[NCELL + 1];         // position of each halo cell in the tile list
-  // staged batch (dynamic shared memory): 1D weights W_p(o + d) (mesh 0) and W_p(o + d - 1/2)
-  // (mesh 1), channel values, halo z index of each particle's cell
+  // staged batch (dynamic shared memory): per axis the 1D weights W_p(o + d) of mesh 0 (offsets
+  // OLO..O0HI, where they can be non-zero) and W_p(o + d - 1/2) of mesh 1, channel values, halo z
+  // index of each particle's cell
+  constexpr size_t SW1 = ILV ? 3 * W : 0;
   extern __shared__ __align__(16) unsigned char dep_dyn[];
-  auto& s_w = *reinterpret_cast<float (*)[NW][W][MAXP]>(dep_dyn);
-  auto& s_val = *reinterpret_cast<float (*)[NC][MAXP]>(dep_dyn + sizeof(float) * NW * W * MAXP);
-  auto& s_rz = *reinterpret_cast<unsigned char (*)[MAXP]>(dep_dyn + sizeof(float) * (NW * W + NC) * MAXP);
+  auto& s_w0 = *reinterpret_cast<float (*)[3][W0][MAXP]>(dep_dyn);
+  auto& s_w1 = *reinterpret_cast<float (*)[3][W1][MAXP]>(dep_dyn + sizeof(float) * 3 * W0 * MAXP);
+  auto& s_val = *reinterpret_cast<float (*)[NC][MAXP]>(dep_dyn + sizeof(float) * (3 * W0 + SW1) * MAXP);
+  auto& s_rz =
+      *reinterpret_cast<unsigned char (*)[MAXP]>(dep_dyn + sizeof(float) * (3 * W0 + SW1 + NC) * MAXP);
   __shared__ uint32_t s_wsum[DT_THREADS / 32];
   __shared__ int s_any;
   const int ntz = N / DT_Z, nty = N / DT_Y;
@@ -512,13 +520,15 @@ __global__ void __launch_bounds__(DT_X * DT_Y * DZ) k_deposit(const uint32_t* __
 #pragma unroll
         for (int o = OLO; o <= OHI; ++o) {
           const float tx_ = (float)o + d.x, ty_ = (float)o + d.y, tz_ = (float)o + d.z;
-          s_w[0][o - OLO][q - b0] = wker<P>(tx_);
-          s_w[1][o - OLO][q - b0] = wker<P>(ty_);
-          s_w[2][o - OLO][q - b0] = wker<P>(tz_);
+          if (o <= O0HI) {
+            s_w0[0][o - OLO][q - b0] = wker<P>(tx_);
+            s_w0[1][o - OLO][q - b0] = wker<P>(ty_);
+            s_w0[2][o - OLO][q - b0] = wker<P>(tz_);
+          }
           if (ILV) {
-            s_w[NW - 3][o - OLO][q - b0] = wker<P>(tx_ - 0.5f);
-            s_w[NW - 2][o - OLO][q - b0] = wker<P>(ty_ - 0.5f);
-            s_w[NW - 1][o - OLO][q - b0] = wker<P>(tz_ - 0.5f);
+            s_w1[0][o - OLO][q - b0] = wker<P>(tx_ - 0.5f);
+            s_w1[1][o - OLO][q - b0] = wker<P>(ty_ - 0.5f);
+            s_w1[2][o - OLO][q - b0] = wker<P>(tz_ - 0.5f);
           }
         }
 #pragma unroll
@@ -541,8 +551,8 @@ __global__ void __launch_bounds__(DT_X * DT_Y * DZ) k_deposit(const uint32_t* __
             const int zo = (int)s_rz[i] - lz;  // oz - OLO
             const bool m0 = mxy && zo + OLO <= O0HI;
             float w0 = 0.f, w1 = 0.f;
-            if (m0) w0 = s_w[0][ox - OLO][i] * s_w[1][oy - OLO][i] * s_w[2][zo][i];
-            if (ILV) w1 = s_w[NW - 3][ox - OLO][i] * s_w[NW - 2][oy - OLO][i] * s_w[NW - 1][zo][i];
+            if (m0) w0 = s_w0[0][ox - OLO][i] * s_w0[1][oy - OLO][i] * s_w0[2][zo][i];
+            if (ILV) w1 = s_w1[0][ox - OLO][i] * s_w1[1][oy - OLO][i] * s_w1[2][zo][i];
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
               if (k < nchan) {
