@@ -386,7 +386,7 @@ struct DepTile {
 };
 
 // Batch of staged particles: two CTAs of DT_X DT_Y DZ threads per SM share the SM's shared memory
-// (112 KB each with the static halo tables): 672 particles for 12 channels with TSC and
+// (112 KB each with the static halo tables): 736 particles for 12 channels with TSC and
 // interlacing.  Measured at 512^3 (random catalogue's assignment): 256 particles 86.0 ms, 512
 // 66.6 ms, 672 65.6 ms, 1440 with one CTA per SM 70.3 ms; mesh 0 keeps only the offsets where
 // its weights can be non-zero (3 of 4 per axis for TSC with interlacing): 736 particles, 64.7 ms.
