@@ -193,8 +193,9 @@ def run_gpu(args, w, rank, world):
     pair_launches = 0
     pair_bytes = 0.0
     launches = 0
+    last = None
     for _ in range(args.steps):
-        step()
+        last = step()
         inf = plan.info()
         ms_pair.append(inf["ms_pair"])
         pair_launches += inf["pair_launches"]
@@ -257,6 +258,7 @@ def run_gpu(args, w, rank, world):
                      "traffic": None if f64 else pair_traffic(pair_bytes / max(pair_launches, 1)),
                      "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
                      else "of fallback 6800 GB/s"},
+        "parity": None if f64 else sampled_parity(w, 1002 + rank, last),
         "stages_ms": {"assign_data": info["ms_assign_data"], "assign_randoms": info["ms_assign_randoms"],
                       "measure": info["ms_measure"], "pair": info["ms_pair"]},
         "clocks": clk,
@@ -404,6 +406,39 @@ def config_of(name, w, world):
             "l2": "inputs larger than L2 (meshes and fields of 0.5 GB each)" if w["N"] >= 256
             else "working set of a few hundred MB (no flush)",
             "parallelism": f"replicas x{world}"}
+
+
+def sampled_parity(w, seed, res):
+    """Errors of one measurement `res` against the stored FP64 oracle values at the sampled bin
+    pairs of tests/golden/survey512_sampled_pairs.json (written by the oracle alone, read here as
+    data), when the workload and its seed are the ones stored: per output the max error relative
+    to the value and relative to its multipole's largest |value|, and whether every value is within
+    the bound of the 512^3 parity test.  None for any other workload."""
+    path = os.path.join(ROOT, "tests", "golden", "survey512_sampled_pairs.json")
+    try:
+        gold = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    gw = gold["workload"]
+    same = (gw.get("seed") == seed and gw["N"] == w["N"] and gw["L"] == w["L"] and gw["n_gal"] == w.get("n_gal")
+            and gw["n_ran"] == w.get("n_ran") and gw["P0"] == w["P0"] and np.allclose(gw["edges"], w["edges"])
+            and [tuple(e) for e in gw["ells"]] == [tuple(e) for e in w["ells"]])
+    if not same:
+        return None
+    rel, rel_scale, ok = {}, {}, True
+    for key in ("B", "shot", "window", "window_shot"):
+        r = s = 0.0
+        for rec in gold["values"]:
+            im = [tuple(e) for e in w["ells"]].index(tuple(rec["ells"]))
+            ref, got = rec[key], float(res[key][im, rec["b1"], rec["b2"]])
+            scale = float(np.abs(res[key][im]).max())
+            r = max(r, abs(got - ref) / abs(ref) if ref else 0.0)
+            s = max(s, abs(got - ref) / scale if scale else 0.0)
+            ok = ok and abs(got - ref) <= max(1e-4 * abs(ref), 1e-6 * scale)
+        rel[key], rel_scale[key] = r, s
+    return {"pairs": len(gold["values"]), "max_rel_err": rel, "max_err_over_multipole_max": rel_scale,
+            "pass": ok, "bound": "1e-4 of the value or 1e-6 of its multipole's largest |value|",
+            "against": "FP64 oracle at sampled bin pairs (tests/golden/survey512_sampled_pairs.json)"}
 
 
 def pair_traffic(alg_bytes_per_launch):

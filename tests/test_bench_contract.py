@@ -33,3 +33,27 @@ def test_reference_arm_prints_one_json_line():
               "cpu_baseline", "e2e"):
         assert k in out, k
     assert out["impl"] == "reference" and out["value"] > 0 and out["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_sampled_parity_reads_the_stored_oracle_values():
+    """bench.sampled_parity against a result that holds the stored FP64 oracle values at the
+    sampled pairs: zero error; scaled by 1 + 3e-5: that relative error; another workload: None."""
+    import numpy as np
+
+    w = bench.WORKLOADS["survey512"]
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "survey512_sampled_pairs.json")))
+    nb = len(w["edges"]) - 1
+    res = {k: np.zeros((len(w["ells"]), nb, nb)) for k in ("B", "shot", "window", "window_shot")}
+    for rec in gold["values"]:
+        im = [tuple(e) for e in w["ells"]].index(tuple(rec["ells"]))
+        for k in res:
+            res[k][im, rec["b1"], rec["b2"]] = rec[k]
+    out = bench.sampled_parity(w, gold["workload"]["seed"], res)
+    assert out["pairs"] == len(gold["values"]) and max(out["max_rel_err"].values()) == 0.0 and out["pass"]
+    scaled = {k: v * (1 + 3e-5) for k, v in res.items()}
+    out = bench.sampled_parity(w, gold["workload"]["seed"], scaled)
+    assert all(abs(e - 3e-5) < 1e-9 for e in out["max_rel_err"].values()) and out["pass"]
+    out = bench.sampled_parity(w, gold["workload"]["seed"], {k: v * (1 + 3e-4) for k, v in res.items()})
+    assert not out["pass"]
+    assert bench.sampled_parity(bench.WORKLOADS["box256"], 1002, res) is None
+    assert bench.sampled_parity(w, 7, res) is None
