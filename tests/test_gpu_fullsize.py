@@ -49,8 +49,9 @@ def test_box256_sampled_pairs_against_oracle():
         for b1, b2 in pairs:
             ref = raw[b1, b2] - shot[b1, b2]
             assert abs(out["shot"][im, b1, b2] - shot[b1, b2]) <= TOL * abs(shot[b1, b2]), (mult, b1, b2)
-            if abs(ref) > 0.01 * scale:
-                assert abs(out["B"][im, b1, b2] - ref) <= TOL * abs(ref), (mult, b1, b2, out["B"][im, b1, b2], ref)
+            # 1e-4 of the value, or 1e-5 of the multipole's largest |value| for bins in cancellation
+            assert abs(out["B"][im, b1, b2] - ref) <= max(TOL * abs(ref), 1e-5 * scale), (
+                mult, b1, b2, out["B"][im, b1, b2], ref, scale)
 
 
 def _direct_dft(mesh, n_vecs, N):
@@ -197,3 +198,5 @@ def test_box1024_blocked_fp32_against_fp64_form(monkeypatch):
             m = np.abs(ref) > 0.01 * np.abs(ref).max()
             err = np.max(np.abs(got[m] - ref[m]) / np.abs(ref[m]))
             assert err <= TOL, (key, mult, err)
+            # every other bin within 1e-5 of the multipole's largest |value|
+            assert np.all(np.abs(got - ref) <= np.maximum(TOL * np.abs(ref), 1e-5 * np.abs(ref).max())), (key, mult)
