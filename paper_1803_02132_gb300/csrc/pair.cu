@@ -2,13 +2,18 @@
 // of the real expansion:  out[o][b1][b2] = sum_x sum_{t in o} X_t(x; b1) Y_t(x; b2), where
 // each side is either one filtered component field F_c(x; b) ("bare") or a small
 // combination sum_(c,h) F_c(x; b) H_h(x) with H_h = sum_g coef G_g ("built").
-//  * k_pair_tma: bins <= 32.  TMA tensor-map loads (128-byte swizzle, mbarrier completion)
-//    stage 64-cell chunks of every field in shared memory; built sides are formed there;
-//    each warp multiplies its term's X and Y tiles with mma.sync m16n8k8 TF32 in three
-//    passes (v = hi + lo split, X_hi Y_hi + X_hi Y_lo + X_lo Y_hi: FP32-class products).
+//  * k_pair_tma (default): bins <= 32.  TMA tensor-map loads (128-byte swizzle, mbarrier
+//    completion) stage 64-cell chunks of every field in shared memory, one barrier per chunk;
+//    the H rows are formed once per chunk, built sides directly in MMA fragment registers; each
+//    warp multiplies its term's X and Y tiles with mma.sync m16n8k8 TF32 in three passes
+//    (v = hi + lo split, X_hi Y_hi + X_hi Y_lo + X_lo Y_hi: FP32-class products).  Warp tables
+//    from the host balance the terms (cell halves split for the heaviest, two-term warps for
+//    terms that differ only in their H rows); at 25 bins the 25th column is formed by FMA.
+//  * k_pair_umma (opt-in): the same contraction on tcgen05 with TMEM accumulators.
 //  * k_pair: any bin count up to 40, FP32 FMA register tiles (fallback).
-// Both keep FP32 partial sums over at most 1024 cells and FP64 above that; per-CTA partials
-// are reduced in a fixed order, so results are bit-reproducible.
+// Chunk sums go to FP32 running sums over at most 1024 cells, then to compensated FP32 (TMA,
+// tcgen05) or FP64 (FMA) slots; the slots are reduced in FP64 in a fixed order, so results are
+// bit-reproducible.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
