@@ -297,11 +297,11 @@ bisp_status bisp_cell_order(int nmesh, double box_len, int mas, const float* xyz
  *     GPU that loads the library holds it until the process exits.
  *   - n > BISP_NOALLOC_MAX_PARTICLES returns BISP_EINVAL and names the limit.
  *   - The first call on a device resolves the array's device address with that device
- *     current and keeps it for the life of the process; make that first call before any
- *     stream capture on that device.  After cudaDeviceReset the kept address is stale: do
- *     not call this entry point again in that process.
+ *     current and keeps it for the life of the process.  After cudaDeviceReset the kept
+ *     address is stale: do not call this entry point again in that process.
  *   - The call copies a small table from host memory, reads back an error counter and
- *     synchronises `stream` before it returns.
+ *     synchronises `stream` before it returns, so it cannot be recorded into a CUDA graph:
+ *     do not call it while `stream` (or any stream of the device) is being captured.
  *   - All calls share the one array: calls whose GPU work overlaps (on different streams or
  *     host threads) race and corrupt each other's results.  Serialise them.
  *   - The call allocates nothing (no cudaMalloc, cudaFree or allocating library routine). */
